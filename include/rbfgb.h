@@ -1,0 +1,168 @@
+/*
+ * rbfgb.h -- C ABI of the GB300 RBF terrain library (librbfgb.so).
+ *
+ * The library evaluates the radial-basis-function terrain model of
+ * Sec. III-A, f(x; w) = sum_i w_i phi(||x - c_i||) (Eq. RBF_fml), with its
+ * gradient, runs the recursive ridge update of the weights restricted to the
+ * active rows (Sec. III-C, Eq. H_update, Eq. kf_w_update,
+ * Eq. active_rows_weights_update, Eq. H_inverse_update), selects centers
+ * adaptively (Sec. III-A), and computes the soft-constraint cost of
+ * Sec. IV-C (Eq. residual_manifold_left_wheel, Eq. manifold_derivative) with
+ * its gradients.
+ *
+ * Conventions (every entry point):
+ *  - Array arguments are DEVICE pointers on the context's GPU, owned by the
+ *    caller, unless the comment says "host".  The context owns only its
+ *    internal state (centers, weights, the covariance store and workspaces).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered and asynchronous, except where a comment says the call
+ *    synchronizes (calls that return a data-dependent size to the host).
+ *  - Errors are returned as a status and never trapped on the device; the
+ *    message of the last failure on the calling thread is rbf_last_error().
+ *    A failed call leaves the context in the state it had before the call
+ *    unless the comment says otherwise.
+ *  - Empty inputs (n = 0, Q = 0) are valid no-ops.
+ *  - Points are float32 (x, y, z) triples, row-major n x 3; queries are
+ *    float32 (x, y) pairs, Q x 2; centers and weights are float64.
+ *  - One context must not be used from two host threads at the same time.
+ */
+#ifndef RBFGB_H
+#define RBFGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbf_ctx rbf_ctx;
+
+typedef enum {
+  RBF_OK = 0,
+  RBF_EINVAL = -1,    /* bad argument (null pointer, negative size, bad config) */
+  RBF_ENOMEM = -2,    /* device allocation failed */
+  RBF_ECUDA = -3,     /* a CUDA runtime call failed */
+  RBF_ENOTSPD = -4,   /* a Cholesky pivot was not positive */
+  RBF_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+  RBF_ESTATE = -6,    /* call not valid in the current state (e.g. no centers) */
+  RBF_ERANGE = -7     /* an output buffer is too small */
+} rbf_status;
+
+enum { RBF_KERNEL_WENDLAND = 0, RBF_KERNEL_GAUSSIAN = 1 };
+enum { RBF_UPDATE_FP64 = 0, RBF_UPDATE_MIXED = 1 };
+enum { RBF_LOSS_HUBER = 0, RBF_LOSS_L2 = 1 };
+
+/* Parameters of a terrain model.  All lengths in metres. */
+typedef struct rbf_config {
+  int32_t kernel;           /* RBF_KERNEL_WENDLAND: phi = (1-r/rho)_+^4 (4 r/rho + 1);
+                               RBF_KERNEL_GAUSSIAN: phi = exp(-r^2 / 2 sigma^2) (Eq. RBF_def) */
+  int32_t update_precision; /* RBF_UPDATE_FP64: every step of rbf_update in FP64;
+                               RBF_UPDATE_MIXED: factorizations on the tensor cores,
+                               FP64 accumulation and FP64 iterative refinement */
+  double rho;               /* Wendland support radius */
+  double sigma;             /* Gaussian bandwidth sigma */
+  double cutoff_mult;       /* Gaussian truncation: evaluation uses cutoff_mult*sigma,
+                               the regression rows cutoff_mult*sqrt(sigma^2+noise^2) */
+  double lambda;            /* ridge weight lambda (Sec. III-B); prior covariance I/lambda */
+  int32_t loss;             /* soft-constraint loss: RBF_LOSS_HUBER or RBF_LOSS_L2 */
+  int32_t min_count;        /* center selection: accept a candidate iff count >= min_count */
+  double huber_delta;       /* Huber threshold delta */
+  double lambda_m;          /* weight of the L2 loss (the paper's lambda_M) */
+  double wheel_offset;      /* r in Eq. residual_manifold_left_wheel */
+  double mesh_x0, mesh_y0;  /* candidate mesh of rbf_build_centers: candidate (i, j) sits at */
+  double mesh_h;            /*   (mesh_x0 + (i + 0.5) mesh_h, mesh_y0 + (j + 0.5) mesh_h) */
+  int32_t mesh_nx, mesh_ny; /*   0 <= i < mesh_nx, 0 <= j < mesh_ny, row-major (j outer) */
+  double r_kd;              /* center selection radius (Sec. III-A) */
+} rbf_config;
+
+/* Create a context on the current CUDA device.  Validates cfg (positive radii,
+ * lambda > 0, known enums).  No centers yet. */
+rbf_status rbf_create(const rbf_config* cfg, rbf_ctx** out);
+
+/* Free every device buffer of the context.  Synchronizes the device. */
+rbf_status rbf_destroy(rbf_ctx* ctx);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* rbf_last_error(void);
+
+/* Install M centers (cxy: M x 2 float64).  Resets the weights to the prior
+ * w = 0 and the covariance to P = I / lambda, and rebuilds the center hash
+ * grid (a counting sort of the centers by cell).  Synchronizes. */
+rbf_status rbf_set_centers(rbf_ctx* ctx, const double* cxy, int64_t M, void* stream);
+
+/* Adaptive center selection (Sec. III-A): count the points (pts: n x 3, x and
+ * y used) within r_kd of every candidate of the configured mesh, with the
+ * float32 distance test d2 < r_kd^2, and install the candidates whose count is
+ * >= min_count, in ascending row-major order, as the centers (as
+ * rbf_set_centers does).  counts (optional, may be NULL): mesh_nx*mesh_ny int32
+ * per-candidate counts.  *M_out = number of accepted centers.  Synchronizes. */
+rbf_status rbf_build_centers(rbf_ctx* ctx, const float* pts, int64_t n, int32_t* counts,
+                             int64_t* M_out, void* stream);
+
+/* Number of installed centers (host). */
+rbf_status rbf_num_centers(rbf_ctx* ctx, int64_t* M_out);
+
+/* Copy the centers (M x 2 float64) / weights (M float64) to device buffers. */
+rbf_status rbf_get_centers(rbf_ctx* ctx, double* cxy, void* stream);
+rbf_status rbf_get_weights(rbf_ctx* ctx, double* w, void* stream);
+
+/* Overwrite the weights (M float64) without touching the covariance. */
+rbf_status rbf_set_weights(rbf_ctx* ctx, const double* w, void* stream);
+
+/* One recursive ridge update (Sec. III-C) with the n points of one frame,
+ * expressed in the world frame (pts: n x 3 float32).  noise = sigma_eps of
+ * Sec. III-B (enters the Gaussian regression rows; unused for Wendland).
+ * Active rows A = sorted union of the points' neighbour lists
+ * (Eq. mfk_m_approx); only w_A and the covariance block P[A, A] change and
+ * P[A, not A] becomes 0 (block-diagonal form of Eq. H_inverse_update).
+ * Synchronizes once (to read the size of A).  RBF_ENOTSPD if a factorization
+ * meets a non-positive pivot; the state is then left unchanged. */
+rbf_status rbf_update(rbf_ctx* ctx, const float* pts, int64_t n, double noise, void* stream);
+
+/* h(q) and grad h(q) at Q query points (q: Q x 2 float32; h: Q float32;
+ * grad: Q x 2 float32, may be NULL).  Eq. RBF_fml and Eq. manidolf_grad_detail,
+ * summed over the centers within the support (Wendland) or within
+ * cutoff_mult*sigma (Gaussian), in float32. */
+rbf_status rbf_eval(rbf_ctx* ctx, const float* q, int64_t Q, float* h, float* grad, void* stream);
+
+/* Soft-constraint cost (Sec. IV-C) over n body-frame points (pts: n x 3
+ * float32) under the pose R (host, 3x3 row-major float64), t (host, 3 float64):
+ * q_i = R p_i + t, r_i = q_z - wheel_offset - f(q_xy),
+ * cost = sum Huber_delta(r_i)  (or lambda_m sum r_i^2 for RBF_LOSS_L2),
+ * grad6 = d cost / d [theta, t] with R <- R Exp(theta), t <- t + dt
+ * (Eq. manifold_derivative, Eq. manifold_grad_2).
+ * cost: 1 float64 (device); grad6: 6 float64 (device); resid: n float32
+ * (device, optional, may be NULL).  Reductions are deterministic. */
+rbf_status rbf_soft_cost(rbf_ctx* ctx, const double* R, const double* t, const float* pts,
+                         int64_t n, double* cost, double* grad6, float* resid, void* stream);
+
+/* Backward of gout * cost: gradients with respect to the weights (dw: M
+ * float32), the centers (dc: M x 2 float32) and the pose (dpose6: 6 float64).
+ * gout: device pointer to one float64 (NULL means 1).  Any of dw, dc, dpose6
+ * may be NULL.  Center-major gather: deterministic, no atomics. */
+rbf_status rbf_soft_cost_backward(rbf_ctx* ctx, const double* R, const double* t,
+                                  const float* pts, int64_t n, const double* gout,
+                                  float* dw, float* dc, double* dpose6, void* stream);
+
+/* Covariance entries P[ids, ids] (ids: host, k int32 center ids; Pk: device,
+ * k x k float64 row-major).  Synchronizes. */
+rbf_status rbf_get_cov(rbf_ctx* ctx, const int32_t* ids, int64_t k, double* Pk, void* stream);
+
+/* Active rows of the last update: A (device, capacity cap int32), *a_out =
+ * their number (host).  RBF_ERANGE if cap < a.  Synchronizes. */
+rbf_status rbf_get_active(rbf_ctx* ctx, int32_t* A, int64_t cap, int64_t* a_out, void* stream);
+
+/* Neighbour lists of n points under the regression-row radius for the given
+ * noise (rho for Wendland), with the float32 rule d2 < r^2, ids ascending:
+ * row_ptr (device, n+1 int64), col (device, capacity cap int32).
+ * *nnz_out = total entries (host).  RBF_ERANGE if cap < nnz (row_ptr is still
+ * written).  Synchronizes. */
+rbf_status rbf_get_neighbors(rbf_ctx* ctx, const float* pts, int64_t n, double noise,
+                             int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz_out,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBFGB_H */

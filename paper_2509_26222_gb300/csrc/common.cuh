@@ -1,0 +1,204 @@
+// Internal declarations shared by the translation units of librbfgb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rbfgb.h"
+
+namespace rbf {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+rbf_status fail(rbf_status st, const char* fmt, ...);
+rbf_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define RBF_CUDA(call)                                                         \
+  do {                                                                         \
+    cudaError_t _e = (call);                                                   \
+    if (_e != cudaSuccess) return ::rbf::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define RBF_TRY(expr)                   \
+  do {                                  \
+    rbf_status _s = (expr);             \
+    if (_s != RBF_OK) return _s;        \
+  } while (0)
+
+// Device-side status words (one int per context): kernels record a failure by
+// atomically OR-ing a flag; the host reads the word at the next sync point.
+enum DevFlag : int {
+  DEV_NOT_SPD = 1,
+  DEV_TIMEOUT = 2,
+  DEV_BAD_INDEX = 4,
+};
+
+// ---------------------------------------------------------------------------
+// Grow-only device buffer
+// ---------------------------------------------------------------------------
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+  rbf_status ensure(size_t nbytes);
+  void release();
+};
+
+// ---------------------------------------------------------------------------
+// Hash grid of centers (counting sort by cell, ids ascending within a cell)
+// ---------------------------------------------------------------------------
+struct Grid {
+  float x0, y0;     // lower-left corner of cell (0, 0)
+  float cs, inv_cs; // cell size and its reciprocal
+  int nx, ny;       // number of cells
+};
+
+struct Lattice {
+  bool on = false;  // every center sits on (x0 + (i + 0.5) h, y0 + (j + 0.5) h)
+  double x0, y0, h;
+  int nx, ny;
+};
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct Ctx {
+  rbf_config cfg;
+  int device = 0;
+  int64_t M = 0;
+
+  Buf c64;           // M x 2 float64 centers
+  Buf w;             // M float64 weights
+  Grid grid{};
+  Lattice lat{};
+  Buf cell_start;    // int32 (nx*ny + 1)
+  Buf sorted_id;     // int32 M  (slot -> center id)
+  Buf sorted_xyw;    // float4 M (x, y, w, 0) in slot order, float32
+  Buf wlat;          // float32 lattice weights (lat.ny x lat.nx), 0 where no center
+
+  // recursive update state: the active block is held in information form
+  int64_t a = 0;     // size of the current active block
+  Buf A;             // int32 M   active ids (ascending)
+  Buf g2l;           // int32 M   center id -> local index in A, -1 if not active
+  Buf H;             // float64 a x a   information matrix of the active block
+  Buf L;             // float64 a x a   its Cholesky factor (lower)
+  int64_t ldH = 0;   // leading dimension of H and L
+  Buf Pg;            // float64 M x M covariance of the centers outside the block
+  bool pg_on = false;
+
+  // device status word + epoch counter for flag-based waits
+  Buf dflag;         // int32[4]
+  Buf sync_flags;    // int32 flags for sync-free triangular solves
+  uint32_t epoch = 0;
+
+  // scratch buffers, addressed by slot (slots 48.. are used by the scans)
+  static constexpr int NSLOT = 64;
+  Buf ws[NSLOT];
+  Buf& scratch(int i) { return ws[i < NSLOT ? i : NSLOT - 1]; }
+
+  // host pinned staging for small readbacks
+  int64_t* host_small = nullptr;
+};
+
+rbf_status check_ctx(rbf_ctx* c, bool need_centers);
+
+// float32 / float64 radii for the neighbour rule
+double assembly_radius(const rbf_config& cfg, double noise);
+double eval_radius(const rbf_config& cfg);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+// Neighbour rule: dx, dy, d2 each rounded once to float32, no contraction.
+__device__ __forceinline__ float d2_rn(float qx, float qy, float cx, float cy) {
+  float dx = __fsub_rn(qx, cx);
+  float dy = __fsub_rn(qy, cy);
+  return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+// Candidate cells of the row band j of the grid for a disc of radius rc (in
+// cell units) around (fx, fy) (cell units): returns false if the band misses.
+__device__ __forceinline__ bool row_range(const Grid& g, float fx, float fy, float rc, int j,
+                                          int& ilo, int& ihi) {
+  float gap = fmaxf(0.f, fmaxf((float)j - fy, fy - (float)(j + 1)));
+  float hw2 = rc * rc - gap * gap;
+  if (hw2 < -1e-3f) return false;
+  float hw = sqrtf(fmaxf(hw2, 0.f)) + 2e-3f;
+  float lo = floorf(fx - hw), hi = floorf(fx + hw);
+  lo = fmaxf(lo, 0.f);
+  hi = fminf(hi, (float)(g.nx - 1));
+  if (!(lo <= hi)) return false;
+  ilo = (int)lo;
+  ihi = (int)hi;
+  return true;
+}
+
+__device__ __forceinline__ bool rows_range(const Grid& g, float fy, float rc, int& jlo, int& jhi) {
+  float lo = floorf(fy - rc - 2e-3f), hi = floorf(fy + rc + 2e-3f);
+  lo = fmaxf(lo, 0.f);
+  hi = fminf(hi, (float)(g.ny - 1));
+  if (!(lo <= hi)) return false;
+  jlo = (int)lo;
+  jhi = (int)hi;
+  return true;
+}
+
+// Regression row m(x) in float64 (Sec. III-B): Wendland phi(r), or the
+// Gaussian moment row (s^2/st^2) exp(-r^2 / 2 st^2).
+__device__ __forceinline__ double row_value(int kernel, double r2, double inv_rho,
+                                            double g_scale, double g_inv2s2) {
+  if (kernel == RBF_KERNEL_WENDLAND) {
+    double s = sqrt(r2) * inv_rho;
+    double t = fmax(1.0 - s, 0.0);
+    double t2 = t * t;
+    return t2 * t2 * (4.0 * s + 1.0);
+  }
+  return g_scale * exp(-r2 * g_inv2s2);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers implemented in the .cu files
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 counts -> int64 offsets (n + 1 entries, out[n] = total)
+rbf_status scan_i32_to_i64(Ctx* c, const int32_t* in, int64_t* out, int64_t n,
+                           cudaStream_t s, int scratch_slot);
+// exclusive scan of int32 -> int32 (n + 1 entries)
+rbf_status scan_i32(Ctx* c, const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
+                    int scratch_slot);
+
+rbf_status build_center_grid(Ctx* c, cudaStream_t s);
+rbf_status refresh_center_weights(Ctx* c, cudaStream_t s);
+rbf_status install_centers(Ctx* c, const double* cxy_dev, int64_t M, cudaStream_t s);
+rbf_status reset_update_state(Ctx* c);
+
+// neighbour lists (point-major CSR, ids ascending) under radius r
+rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride_floats, double radius,
+                          Buf& row_ptr, Buf& col, int64_t* nnz, cudaStream_t s);
+
+rbf_status read_dev_flag(Ctx* c, cudaStream_t s, int* flag);
+
+// dense FP64 / mixed-precision linear algebra (dense.cu)
+rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfactor,
+                       bool mixed, cudaStream_t s);
+rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B, int64_t m,
+                      int64_t ldb, bool transpose, cudaStream_t s);
+rbf_status gemm_f64(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                    const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                    double* Cm, int64_t ldc, cudaStream_t s);
+rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,
+                         const double* b, double* r, cudaStream_t s);
+
+}  // namespace rbf
+
+struct rbf_ctx {
+  rbf::Ctx impl;
+};
+
+namespace rbf {
+inline Ctx* C(rbf_ctx* c) { return &c->impl; }
+}  // namespace rbf

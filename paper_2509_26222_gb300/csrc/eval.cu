@@ -1,0 +1,490 @@
+// Evaluation of the terrain model and the soft-constraint cost.
+//
+//  * rbf_eval: h(q) = sum_j w_j phi(||q - c_j||) and grad h (Eq. RBF_fml,
+//    Eq. manidolf_grad_detail with the sign of reading G5), float32, one
+//    thread per query, candidates from the center hash grid (rows of cells
+//    cut to the disc of the support radius).
+//  * rbf_soft_cost: q_i = R p_i + t, r_i = q_z - wheel_offset - h(q_xy)
+//    (Eq. residual_manifold_left_wheel), Huber or L2 cost, pose gradient
+//    through Eq. manifold_derivative and Eq. manifold_grad_2 (right
+//    perturbation), per-block float64 partial sums reduced in a fixed order.
+//  * rbf_soft_cost_backward: weight and center gradients by a center-major
+//    gather over a counting sort of the transformed points (deterministic).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace rbf {
+
+struct EvalParams {
+  Grid g;
+  float r2;       // squared support radius (float32)
+  float rc;       // support radius in cell units
+  float inv_rho;  // Wendland: 1 / rho
+  float inv2s2;   // Gaussian: 1 / (2 sigma^2)
+  float gscale;   // Wendland: -20 / rho^2; Gaussian: -1 / sigma^2
+};
+
+static EvalParams make_eval_params(const Ctx* c) {
+  EvalParams P;
+  P.g = c->grid;
+  double r = eval_radius(c->cfg);
+  float r32 = (float)r;
+  P.r2 = r32 * r32;
+  P.rc = (float)(r / (double)c->grid.cs);
+  P.inv_rho = (float)(1.0 / c->cfg.rho);
+  P.inv2s2 = (float)(1.0 / (2.0 * c->cfg.sigma * c->cfg.sigma));
+  P.gscale = c->cfg.kernel == RBF_KERNEL_WENDLAND
+                 ? (float)(-20.0 / (c->cfg.rho * c->cfg.rho))
+                 : (float)(-1.0 / (c->cfg.sigma * c->cfg.sigma));
+  return P;
+}
+
+// Visit every candidate slot of the hash grid whose cell meets the disc of
+// radius rc (cell units) around the point (x, y).
+template <class F>
+__device__ __forceinline__ void for_each_candidate(const Grid& g, const int32_t* __restrict__ cell_start,
+                                                   float x, float y, float rc, F&& f) {
+  float fx = (x - g.x0) * g.inv_cs, fy = (y - g.y0) * g.inv_cs;
+  int jlo, jhi;
+  if (!rows_range(g, fy, rc, jlo, jhi)) return;
+  for (int j = jlo; j <= jhi; ++j) {
+    int ilo, ihi;
+    if (!row_range(g, fx, fy, rc, j, ilo, ihi)) continue;
+    int s0 = __ldg(cell_start + j * g.nx + ilo);
+    int s1 = __ldg(cell_start + j * g.nx + ihi + 1);
+    for (int s = s0; s < s1; ++s) f(s);
+  }
+}
+
+template <int KERNEL>
+__device__ __forceinline__ void eval_one(const EvalParams& P, const int32_t* __restrict__ cell_start,
+                                         const float4* __restrict__ xyw, float qx, float qy,
+                                         float& h, float& gx, float& gy) {
+  float ah = 0.f, ax = 0.f, ay = 0.f;
+  for_each_candidate(P.g, cell_start, qx, qy, P.rc, [&](int s) {
+    float4 c = __ldg(xyw + s);
+    float dx = qx - c.x, dy = qy - c.y;
+    float d2 = fmaf(dx, dx, dy * dy);
+    if (d2 < P.r2) {
+      if (KERNEL == RBF_KERNEL_WENDLAND) {
+        float sd = sqrtf(d2) * P.inv_rho;
+        float t = fmaxf(1.f - sd, 0.f);
+        float cw = c.z * (t * t * t);
+        ah = fmaf(cw, t * fmaf(4.f, sd, 1.f), ah);
+        ax = fmaf(cw, dx, ax);
+        ay = fmaf(cw, dy, ay);
+      } else {
+        float e = c.z * __expf(-d2 * P.inv2s2);
+        ah += e;
+        ax = fmaf(e, dx, ax);
+        ay = fmaf(e, dy, ay);
+      }
+    }
+  });
+  h = ah;
+  gx = ax * P.gscale;
+  gy = ay * P.gscale;
+}
+
+template <int KERNEL>
+__global__ void __launch_bounds__(256) k_eval(EvalParams P, const int32_t* __restrict__ cell_start,
+                                              const float4* __restrict__ xyw,
+                                              const float2* __restrict__ q, int64_t Q,
+                                              float* __restrict__ h, float2* __restrict__ grad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float2 p = q[i];
+    float hh, gx, gy;
+    if (isfinite(p.x) && isfinite(p.y)) {
+      eval_one<KERNEL>(P, cell_start, xyw, p.x, p.y, hh, gx, gy);
+    } else {
+      hh = gx = gy = __int_as_float(0x7fc00000);
+    }
+    h[i] = hh;
+    if (grad) grad[i] = make_float2(gx, gy);
+  }
+}
+
+static int num_sms(int dev) {
+  static int cached[64] = {0};
+  if (dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 148;
+  }
+  return cached[dev];
+}
+
+static unsigned grid_for(int64_t n, int threads, int dev, int per_sm) {
+  int64_t want = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms(dev) * per_sm;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (unsigned)want;
+}
+
+// ---------------------------------------------------------------------------
+// Soft-constraint cost
+// ---------------------------------------------------------------------------
+struct Pose {
+  float R[9];
+  float t[3];
+};
+
+struct CostParams {
+  int loss;
+  float delta, lam_m, off;
+};
+
+// Residual, loss, psi = d loss / d r and the pose Jacobian row of one point.
+template <int KERNEL>
+__device__ __forceinline__ void point_terms(const EvalParams& P, const int32_t* __restrict__ cell_start,
+                                            const float4* __restrict__ xyw, const Pose& T,
+                                            const CostParams& CP, const float* __restrict__ pts,
+                                            int64_t i, float& qx, float& qy, float& r, float& loss,
+                                            float& psi, float J[6]) {
+  float px = pts[3 * i], py = pts[3 * i + 1], pz = pts[3 * i + 2];
+  qx = fmaf(T.R[0], px, fmaf(T.R[1], py, fmaf(T.R[2], pz, T.t[0])));
+  qy = fmaf(T.R[3], px, fmaf(T.R[4], py, fmaf(T.R[5], pz, T.t[1])));
+  float qz = fmaf(T.R[6], px, fmaf(T.R[7], py, fmaf(T.R[8], pz, T.t[2])));
+  float h, hx, hy;
+  eval_one<KERNEL>(P, cell_start, xyw, qx, qy, h, hx, hy);
+  r = qz - CP.off - h;
+  if (CP.loss == RBF_LOSS_HUBER) {
+    float a = fabsf(r);
+    loss = a <= CP.delta ? 0.5f * r * r : CP.delta * (a - 0.5f * CP.delta);
+    psi = fminf(fmaxf(r, -CP.delta), CP.delta);
+  } else {
+    loss = CP.lam_m * r * r;
+    psi = 2.f * CP.lam_m * r;
+  }
+  // dr/dq = a = (-hx, -hy, 1); dr/dtheta = p x (R^T a); dr/dt = a
+  float ax = -hx, ay = -hy, az = 1.f;
+  float bx = T.R[0] * ax + T.R[3] * ay + T.R[6] * az;
+  float by = T.R[1] * ax + T.R[4] * ay + T.R[7] * az;
+  float bz = T.R[2] * ax + T.R[5] * ay + T.R[8] * az;
+  J[0] = py * bz - pz * by;
+  J[1] = pz * bx - px * bz;
+  J[2] = px * by - py * bx;
+  J[3] = ax;
+  J[4] = ay;
+  J[5] = az;
+}
+
+constexpr int SC_THREADS = 256;
+
+template <int KERNEL>
+__global__ void __launch_bounds__(SC_THREADS) k_soft_cost(EvalParams P, const int32_t* __restrict__ cell_start,
+                                                          const float4* __restrict__ xyw, Pose T,
+                                                          CostParams CP, const float* __restrict__ pts,
+                                                          int64_t n, float* __restrict__ resid,
+                                                          double* __restrict__ partials) {
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float qx, qy, r, loss, psi, J[6];
+    point_terms<KERNEL>(P, cell_start, xyw, T, CP, pts, i, qx, qy, r, loss, psi, J);
+    if (resid) resid[i] = r;
+    acc[0] += (double)loss;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k + 1] += (double)(psi * J[k]);
+  }
+  __shared__ double red[SC_THREADS / 32][7];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double v = 0;
+    for (int w = 0; w < SC_THREADS / 32; ++w) v += red[w][threadIdx.x];
+    partials[blockIdx.x * 8 + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblk,
+                                  const double* __restrict__ gout, double* __restrict__ cost,
+                                  double* __restrict__ grad6) {
+  int k = threadIdx.x;
+  if (k >= 7) return;
+  double v = 0;
+  for (int b = 0; b < nblk; ++b) v += partials[b * 8 + k];
+  double g = gout ? *gout : 1.0;
+  v *= g;
+  if (k == 0) {
+    if (cost) *cost = v;
+  } else if (grad6) {
+    grad6[k - 1] = v;
+  }
+}
+
+static rbf_status load_pose(const double* R, const double* t, Pose* T) {
+  if (!R || !t) return fail(RBF_EINVAL, "null pose");
+  for (int k = 0; k < 9; ++k) {
+    if (!isfinite(R[k])) return fail(RBF_EINVAL, "non-finite rotation");
+    T->R[k] = (float)R[k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (!isfinite(t[k])) return fail(RBF_EINVAL, "non-finite translation");
+    T->t[k] = (float)t[k];
+  }
+  return RBF_OK;
+}
+
+static CostParams cost_params(const rbf_config& cfg) {
+  CostParams CP;
+  CP.loss = cfg.loss;
+  CP.delta = (float)cfg.huber_delta;
+  CP.lam_m = (float)cfg.lambda_m;
+  CP.off = (float)cfg.wheel_offset;
+  return CP;
+}
+
+static rbf_status soft_cost_forward(Ctx* x, const Pose& T, const float* pts, int64_t n,
+                                    const double* gout, double* cost, double* grad6, float* resid,
+                                    cudaStream_t s) {
+  EvalParams P = make_eval_params(x);
+  CostParams CP = cost_params(x->cfg);
+  unsigned nb = grid_for(n, SC_THREADS, x->device, 4);
+  Buf& part = x->scratch(20);
+  RBF_TRY(part.ensure((size_t)nb * 8 * sizeof(double)));
+  if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
+    k_soft_cost<RBF_KERNEL_WENDLAND><<<nb, SC_THREADS, 0, s>>>(
+        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid,
+        part.as<double>());
+  else
+    k_soft_cost<RBF_KERNEL_GAUSSIAN><<<nb, SC_THREADS, 0, s>>>(
+        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid,
+        part.as<double>());
+  RBF_CUDA(cudaGetLastError());
+  k_reduce_partials<<<1, 32, 0, s>>>(part.as<double>(), (int)nb, gout, cost, grad6);
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Backward: per point (qx, qy, psi), counting sort of the points by cell of
+// the center grid, then one thread per center gathers its in-support points.
+// ---------------------------------------------------------------------------
+template <int KERNEL>
+__global__ void __launch_bounds__(256) k_bwd_points(EvalParams P, const int32_t* __restrict__ cell_start,
+                                                    const float4* __restrict__ xyw, Pose T, CostParams CP,
+                                                    const float* __restrict__ pts, int64_t n,
+                                                    const double* __restrict__ gout,
+                                                    float4* __restrict__ qpsi, int32_t* __restrict__ pcell,
+                                                    int32_t* __restrict__ pcount) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float qx, qy, r, loss, psi, J[6];
+  point_terms<KERNEL>(P, cell_start, xyw, T, CP, pts, i, qx, qy, r, loss, psi, J);
+  float g = gout ? (float)*gout : 1.f;
+  qpsi[i] = make_float4(qx, qy, psi * g, 0.f);
+  int ix = (int)floorf((qx - P.g.x0) * P.g.inv_cs);
+  int iy = (int)floorf((qy - P.g.y0) * P.g.inv_cs);
+  // points outside the grid's cell range still gather correctly when clamped:
+  // the per-center search covers the clamped border cells.
+  bool fin = isfinite(qx) && isfinite(qy);
+  ix = min(max(ix, 0), P.g.nx - 1);
+  iy = min(max(iy, 0), P.g.ny - 1);
+  int cc = fin ? iy * P.g.nx + ix : -1;
+  pcell[i] = cc;
+  if (cc >= 0) atomicAdd(&pcount[cc], 1);
+}
+
+__global__ void k_bwd_fill(const int32_t* __restrict__ pcell, int64_t n, const int32_t* __restrict__ start,
+                           int32_t* __restrict__ fill, int32_t* __restrict__ order) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cc = pcell[i];
+  if (cc < 0) return;
+  int pos = start[cc] + atomicAdd(&fill[cc], 1);
+  order[pos] = (int32_t)i;
+}
+
+__global__ void k_bwd_sort(const int32_t* __restrict__ start, int ncell, int32_t* __restrict__ ids) {
+  int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cidx >= ncell) return;
+  int a = start[cidx], b = start[cidx + 1];
+  for (int i = a + 1; i < b; ++i) {
+    int v = ids[i];
+    int k = i - 1;
+    while (k >= a && ids[k] > v) {
+      ids[k + 1] = ids[k];
+      --k;
+    }
+    ids[k + 1] = v;
+  }
+}
+
+// The point cells are clamped to the grid, so a point beyond the border sits
+// in a border cell; widen the search at the border to the whole row/column
+// band by letting the clamped cell range cover it (the disc test is exact).
+template <int KERNEL>
+__global__ void __launch_bounds__(256) k_bwd_centers(EvalParams P, const float4* __restrict__ xyw,
+                                                     const int32_t* __restrict__ sorted_id, int64_t M,
+                                                     const int32_t* __restrict__ pstart,
+                                                     const int32_t* __restrict__ order,
+                                                     const float4* __restrict__ qpsi,
+                                                     float* __restrict__ dw, float2* __restrict__ dc) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  float4 c = xyw[s];
+  int j = sorted_id[s];
+  float aw = 0.f, ax = 0.f, ay = 0.f;
+  const Grid& g = P.g;
+  float fx = (c.x - g.x0) * g.inv_cs, fy = (c.y - g.y0) * g.inv_cs;
+  int jlo = (int)floorf(fy - P.rc - 2e-3f), jhi = (int)floorf(fy + P.rc + 2e-3f);
+  int ilo = (int)floorf(fx - P.rc - 2e-3f), ihi = (int)floorf(fx + P.rc + 2e-3f);
+  // border cells hold every clamped point beyond the border
+  jlo = max(jlo, 0);
+  ilo = max(ilo, 0);
+  jhi = min(jhi, g.ny - 1);
+  ihi = min(ihi, g.nx - 1);
+  for (int cj = jlo; cj <= jhi; ++cj) {
+    if (cj > jhi) break;
+    int a = pstart[cj * g.nx + ilo], b = pstart[cj * g.nx + ihi + 1];
+    for (int k = a; k < b; ++k) {
+      float4 q = __ldg(qpsi + __ldg(order + k));
+      float dx = q.x - c.x, dy = q.y - c.y;
+      float d2 = fmaf(dx, dx, dy * dy);
+      if (d2 < P.r2) {
+        float ph, gc;
+        if (KERNEL == RBF_KERNEL_WENDLAND) {
+          float sd = sqrtf(d2) * P.inv_rho;
+          float t = fmaxf(1.f - sd, 0.f);
+          float t3 = t * t * t;
+          ph = t3 * t * fmaf(4.f, sd, 1.f);
+          gc = P.gscale * t3;
+        } else {
+          ph = __expf(-d2 * P.inv2s2);
+          gc = P.gscale * ph;
+        }
+        aw = fmaf(q.z, ph, aw);
+        float pg = q.z * gc;
+        ax = fmaf(pg, dx, ax);
+        ay = fmaf(pg, dy, ay);
+      }
+    }
+  }
+  if (dw) dw[j] = -aw;
+  if (dc) dc[j] = make_float2(c.z * ax, c.z * ay);
+}
+
+}  // namespace rbf
+
+using namespace rbf;
+
+extern "C" rbf_status rbf_eval(rbf_ctx* c, const float* q, int64_t Q, float* h, float* grad,
+                               void* stream) {
+  RBF_TRY(check_ctx(c, true));
+  if (Q < 0) return fail(RBF_EINVAL, "negative Q");
+  if (Q == 0) return RBF_OK;
+  if (!q || !h) return fail(RBF_EINVAL, "null query or output pointer");
+  if (((uintptr_t)q & 7) || ((uintptr_t)grad & 7))
+    return fail(RBF_EINVAL, "q and grad must be 8-byte aligned");
+  Ctx* x = C(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  EvalParams P = make_eval_params(x);
+  unsigned nb = grid_for(Q, 256, x->device, 8);
+  if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
+    k_eval<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
+                                                   x->sorted_xyw.as<float4>(), (const float2*)q, Q,
+                                                   h, (float2*)grad);
+  else
+    k_eval<RBF_KERNEL_GAUSSIAN><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
+                                                   x->sorted_xyw.as<float4>(), (const float2*)q, Q,
+                                                   h, (float2*)grad);
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}
+
+extern "C" rbf_status rbf_soft_cost(rbf_ctx* c, const double* R, const double* t, const float* pts,
+                                    int64_t n, double* cost, double* grad6, float* resid,
+                                    void* stream) {
+  RBF_TRY(check_ctx(c, true));
+  if (n < 0) return fail(RBF_EINVAL, "negative n");
+  if (!cost && !grad6 && !resid) return fail(RBF_EINVAL, "no output requested");
+  if (n > 0 && !pts) return fail(RBF_EINVAL, "null points");
+  Pose T;
+  RBF_TRY(load_pose(R, t, &T));
+  Ctx* x = C(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (cost) RBF_CUDA(cudaMemsetAsync(cost, 0, sizeof(double), s));
+    if (grad6) RBF_CUDA(cudaMemsetAsync(grad6, 0, 6 * sizeof(double), s));
+    return RBF_OK;
+  }
+  return soft_cost_forward(x, T, pts, n, nullptr, cost, grad6, resid, s);
+}
+
+extern "C" rbf_status rbf_soft_cost_backward(rbf_ctx* c, const double* R, const double* t,
+                                             const float* pts, int64_t n, const double* gout,
+                                             float* dw, float* dc, double* dpose6, void* stream) {
+  RBF_TRY(check_ctx(c, true));
+  if (n < 0) return fail(RBF_EINVAL, "negative n");
+  if (n > 0 && !pts) return fail(RBF_EINVAL, "null points");
+  if (((uintptr_t)dc & 7)) return fail(RBF_EINVAL, "dc must be 8-byte aligned");
+  Pose T;
+  RBF_TRY(load_pose(R, t, &T));
+  Ctx* x = C(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t M = x->M;
+  if (n == 0) {
+    if (dw) RBF_CUDA(cudaMemsetAsync(dw, 0, (size_t)M * sizeof(float), s));
+    if (dc) RBF_CUDA(cudaMemsetAsync(dc, 0, (size_t)M * 2 * sizeof(float), s));
+    if (dpose6) RBF_CUDA(cudaMemsetAsync(dpose6, 0, 6 * sizeof(double), s));
+    return RBF_OK;
+  }
+  if (dpose6) RBF_TRY(soft_cost_forward(x, T, pts, n, gout, nullptr, dpose6, nullptr, s));
+  if (!dw && !dc) return RBF_OK;
+  EvalParams P = make_eval_params(x);
+  CostParams CP = cost_params(x->cfg);
+  const Grid& g = x->grid;
+  int ncell = g.nx * g.ny;
+  Buf& qpsi = x->scratch(21);
+  Buf& pcell = x->scratch(22);
+  Buf& pcount = x->scratch(23);
+  Buf& pstart = x->scratch(24);
+  Buf& order = x->scratch(25);
+  RBF_TRY(qpsi.ensure((size_t)n * sizeof(float4)));
+  RBF_TRY(pcell.ensure((size_t)n * sizeof(int32_t)));
+  RBF_TRY(pcount.ensure((size_t)(ncell + 1) * sizeof(int32_t)));
+  RBF_TRY(pstart.ensure((size_t)(ncell + 1) * sizeof(int32_t)));
+  RBF_TRY(order.ensure((size_t)n * sizeof(int32_t)));
+  RBF_CUDA(cudaMemsetAsync(pcount.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
+  unsigned nb = (unsigned)((n + 255) / 256);
+  if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
+    k_bwd_points<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(
+        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, gout,
+        qpsi.as<float4>(), pcell.as<int32_t>(), pcount.as<int32_t>());
+  else
+    k_bwd_points<RBF_KERNEL_GAUSSIAN><<<nb, 256, 0, s>>>(
+        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, gout,
+        qpsi.as<float4>(), pcell.as<int32_t>(), pcount.as<int32_t>());
+  RBF_CUDA(cudaGetLastError());
+  RBF_TRY(scan_i32(x, pcount.as<int32_t>(), pstart.as<int32_t>(), ncell, s, 48));
+  RBF_CUDA(cudaMemsetAsync(pcount.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
+  k_bwd_fill<<<nb, 256, 0, s>>>(pcell.as<int32_t>(), n, pstart.as<int32_t>(), pcount.as<int32_t>(),
+                                order.as<int32_t>());
+  RBF_CUDA(cudaGetLastError());
+  k_bwd_sort<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(pstart.as<int32_t>(), ncell,
+                                                             order.as<int32_t>());
+  RBF_CUDA(cudaGetLastError());
+  unsigned nbc = (unsigned)((M + 255) / 256);
+  if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
+    k_bwd_centers<RBF_KERNEL_WENDLAND><<<nbc, 256, 0, s>>>(
+        P, x->sorted_xyw.as<float4>(), x->sorted_id.as<int32_t>(), M, pstart.as<int32_t>(),
+        order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc);
+  else
+    k_bwd_centers<RBF_KERNEL_GAUSSIAN><<<nbc, 256, 0, s>>>(
+        P, x->sorted_xyw.as<float4>(), x->sorted_id.as<int32_t>(), M, pstart.as<int32_t>(),
+        order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc);
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}

@@ -1,0 +1,808 @@
+// Recursive ridge update of the weights on the active rows (Sec. III-C).
+//
+// Per frame (n points, world frame):
+//  1. neighbour lists: for every point the centers j with d2 < r^2 (float32
+//     rule, ids ascending) -- the nonzero pattern of m~ in Eq. mfk_m_approx;
+//  2. active rows A = sorted union of the lists, local index map;
+//  3. m~ entries in float64 (Wendland phi, or the Gaussian moment row of
+//     Sec. III-B) and the innovation e = z - m~^T w_A (Eq. kf_w_update);
+//  4. the information matrix of the new block,
+//        H' = (P[A, A])^{-1} + m~ m~^T           (Eq. H_update on the block),
+//     where (P[A, A])^{-1} is assembled from the previous block's information
+//     matrix (a Schur complement drops the centers that leave) and the stored
+//     covariance of the centers that enter;
+//  5. H' = L L^T, w_A += H'^{-1} m~ e (Eq. kf_w_update,
+//     Eq. active_rows_weights_update);
+//  6. the covariance of the centers that left is written to the outside store
+//     and their coupling to everything else is zero: the covariance stays
+//     block diagonal as in Eq. H_inverse_update.
+// The covariance of the active block is thus kept in information form; it is
+// the same matrix the Woodbury form of Eq. H_inverse_update produces.
+#include <math.h>
+
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rbf {
+
+// ---------------------------------------------------------------------------
+// Neighbour lists
+// ---------------------------------------------------------------------------
+struct NbrParams {
+  Grid g;
+  float r2;  // fl32(r) * fl32(r), rounded to float32
+  float rc;  // radius in cell units
+};
+
+template <class F>
+__device__ __forceinline__ void for_each_cand(const Grid& g, const int32_t* __restrict__ cell_start,
+                                              float x, float y, float rc, F&& f) {
+  float fx = (x - g.x0) * g.inv_cs, fy = (y - g.y0) * g.inv_cs;
+  int jlo, jhi;
+  if (!rows_range(g, fy, rc, jlo, jhi)) return;
+  for (int j = jlo; j <= jhi; ++j) {
+    int ilo, ihi;
+    if (!row_range(g, fx, fy, rc, j, ilo, ihi)) continue;
+    int s0 = cell_start[j * g.nx + ilo];
+    int s1 = cell_start[j * g.nx + ihi + 1];
+    for (int s = s0; s < s1; ++s) f(s);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nbr_count(NbrParams P, const int32_t* __restrict__ cell_start,
+                                                   const float4* __restrict__ xyw,
+                                                   const float* __restrict__ pts, int stride,
+                                                   int64_t n, int32_t* __restrict__ cnt,
+                                                   int* __restrict__ status) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x = pts[i * stride], y = pts[i * stride + 1];
+  int c = 0;
+  if (isfinite(x) && isfinite(y) && (stride < 3 || isfinite(pts[i * stride + 2]))) {
+    for_each_cand(P.g, cell_start, x, y, P.rc, [&](int s) {
+      float4 cc = xyw[s];
+      if (d2_rn(x, y, cc.x, cc.y) < P.r2) ++c;
+    });
+  } else {
+    atomicOr(status, DEV_BAD_INDEX);
+  }
+  cnt[i] = c;
+}
+
+__global__ void __launch_bounds__(256) k_nbr_fill(NbrParams P, const int32_t* __restrict__ cell_start,
+                                                  const float4* __restrict__ xyw,
+                                                  const int32_t* __restrict__ sorted_id,
+                                                  const float* __restrict__ pts, int stride, int64_t n,
+                                                  const int64_t* __restrict__ row_ptr,
+                                                  int32_t* __restrict__ col) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x = pts[i * stride], y = pts[i * stride + 1];
+  int64_t a = row_ptr[i], b = row_ptr[i + 1];
+  if (a == b) return;
+  int64_t p = a;
+  for_each_cand(P.g, cell_start, x, y, P.rc, [&](int s) {
+    float4 cc = xyw[s];
+    if (d2_rn(x, y, cc.x, cc.y) < P.r2 && p < b) col[p++] = sorted_id[s];
+  });
+  // ascending ids (rows are short)
+  for (int64_t u = a + 1; u < b; ++u) {
+    int32_t v = col[u];
+    int64_t k = u - 1;
+    while (k >= a && col[k] > v) {
+      col[k + 1] = col[k];
+      --k;
+    }
+    col[k + 1] = v;
+  }
+}
+
+rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, double radius,
+                          Buf& row_ptr, Buf& col, int64_t* nnz, cudaStream_t s) {
+  NbrParams P;
+  P.g = c->grid;
+  float r32 = (float)radius;
+  P.r2 = r32 * r32;
+  P.rc = (float)(radius / (double)c->grid.cs);
+  Buf& cnt = c->scratch(10);
+  RBF_TRY(cnt.ensure((size_t)(n + 1) * sizeof(int32_t)));
+  RBF_TRY(row_ptr.ensure((size_t)(n + 1) * sizeof(int64_t)));
+  unsigned nb = (unsigned)((n + 255) / 256);
+  k_nbr_count<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(), pts,
+                                 stride, n, cnt.as<int32_t>(), c->dflag.as<int>());
+  RBF_CUDA(cudaGetLastError());
+  RBF_TRY(scan_i32_to_i64(c, cnt.as<int32_t>(), row_ptr.as<int64_t>(), n, s, 48));
+  RBF_CUDA(cudaMemcpyAsync(c->host_small, row_ptr.as<int64_t>() + n, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s));
+  int flag = 0;
+  RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_BAD_INDEX) return fail(RBF_EINVAL, "a point has a non-finite coordinate");
+  *nnz = c->host_small[0];
+  RBF_TRY(col.ensure((size_t)(*nnz > 0 ? *nnz : 1) * sizeof(int32_t)));
+  if (*nnz > 0) {
+    k_nbr_fill<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(),
+                                  c->sorted_id.as<int32_t>(), pts, stride, n, row_ptr.as<int64_t>(),
+                                  col.as<int32_t>());
+    RBF_CUDA(cudaGetLastError());
+  }
+  return RBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Active set and block bookkeeping
+// ---------------------------------------------------------------------------
+__global__ void k_mark(const int32_t* __restrict__ col, int64_t nnz, int32_t* __restrict__ mark) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) mark[col[k]] = 1;
+}
+
+// A[pos[j]] = j for marked j; g2l[j] = pos[j] or -1
+__global__ void k_compact(const int32_t* __restrict__ mark, const int32_t* __restrict__ pos, int64_t M,
+                          int32_t* __restrict__ A, int32_t* __restrict__ g2l) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  if (mark[j]) {
+    A[pos[j]] = (int32_t)j;
+    g2l[j] = pos[j];
+  } else {
+    g2l[j] = -1;
+  }
+}
+
+// flag[l] = (other_g2l[ids[l]] >= 0) == want_member
+__global__ void k_member_flag(const int32_t* __restrict__ ids, int64_t a, const int32_t* __restrict__ other_g2l,
+                              int want_member, int32_t* __restrict__ flag) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= a) return;
+  int in = other_g2l[ids[l]] >= 0;
+  flag[l] = (in == want_member) ? 1 : 0;
+}
+
+__global__ void k_list_from_flags(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                  int64_t a, int32_t* __restrict__ list) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < a && flag[l]) list[pos[l]] = (int32_t)l;
+}
+
+// ---------------------------------------------------------------------------
+// m~ entries, innovation, transposed (center-major) lists
+// ---------------------------------------------------------------------------
+struct RowParams {
+  int kernel;
+  double inv_rho;
+  double g_scale;   // sigma^2 / st^2
+  double g_inv2s2;  // 1 / (2 st^2)
+};
+
+__global__ void __launch_bounds__(256) k_rowvals(RowParams R, const float* __restrict__ pts, int64_t n,
+                                                 const int64_t* __restrict__ row_ptr,
+                                                 const int32_t* __restrict__ col,
+                                                 const double* __restrict__ c64,
+                                                 const double* __restrict__ w,
+                                                 const int32_t* __restrict__ g2l,
+                                                 double* __restrict__ val, int32_t* __restrict__ lcol,
+                                                 double* __restrict__ e) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = (double)pts[3 * i], y = (double)pts[3 * i + 1], z = (double)pts[3 * i + 2];
+  double acc = 0.0;
+  for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+    int j = col[k];
+    double dx = x - c64[2 * j], dy = y - c64[2 * j + 1];
+    double m = row_value(R.kernel, dx * dx + dy * dy, R.inv_rho, R.g_scale, R.g_inv2s2);
+    val[k] = m;
+    lcol[k] = g2l[j];
+    acc = fma(m, w[j], acc);
+  }
+  e[i] = z - acc;
+}
+
+__global__ void k_tcount(const int32_t* __restrict__ lcol, int64_t nnz, int32_t* __restrict__ tcnt) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) atomicAdd(&tcnt[lcol[k]], 1);
+}
+
+__global__ void k_tfill(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ lcol,
+                        const int64_t* __restrict__ tstart, int32_t* __restrict__ tfill,
+                        int64_t* __restrict__ tk) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+    int l = lcol[k];
+    int64_t p = tstart[l] + atomicAdd(&tfill[l], 1);
+    tk[p] = k;  // entries of one point are in ascending k; points sort by k too
+  }
+}
+
+// order each center's entries by their position k in the point-major list
+// (= by point index, then by center): makes every later sum deterministic
+__global__ void k_tsort(const int64_t* __restrict__ tstart, int64_t a, int64_t* __restrict__ tk) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= a) return;
+  int64_t lo = tstart[l], hi = tstart[l + 1];
+  for (int64_t u = lo + 1; u < hi; ++u) {
+    int64_t v = tk[u];
+    int64_t k = u - 1;
+    while (k >= lo && tk[k] > v) {
+      tk[k + 1] = tk[k];
+      --k;
+    }
+    tk[k + 1] = v;
+  }
+}
+
+// point index of nnz position k (binary search in row_ptr)
+__device__ __forceinline__ int64_t owner_of(const int64_t* __restrict__ row_ptr, int64_t n, int64_t k) {
+  int64_t lo = 0, hi = n;  // row_ptr[lo] <= k < row_ptr[hi]
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (row_ptr[mid] <= k) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One warp per active row l1: H'[l1, :] += sum_i m_{i,l1} m_{i,:} (row of
+// m~ m~^T, accumulated in shared memory in ascending point order) and
+// u[l1] = sum_i m_{i,l1} e_i.
+__global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const int64_t* __restrict__ tstart,
+                                                   const int64_t* __restrict__ tk,
+                                                   const int64_t* __restrict__ row_ptr, int64_t n,
+                                                   const double* __restrict__ val,
+                                                   const int32_t* __restrict__ lcol,
+                                                   const double* __restrict__ e,
+                                                   double* __restrict__ H, double* __restrict__ u) {
+  extern __shared__ double srow[];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* row = srow + (int64_t)wid * a;
+  for (int64_t l1 = (int64_t)blockIdx.x * nw + wid; l1 < a; l1 += (int64_t)gridDim.x * nw) {
+    for (int64_t j = lane; j < a; j += 32) row[j] = 0.0;
+    __syncwarp();
+    double ue = 0.0;
+    for (int64_t p = tstart[l1]; p < tstart[l1 + 1]; ++p) {
+      int64_t k1 = tk[p];
+      int64_t i = owner_of(row_ptr, n, k1);
+      double m1 = val[k1];
+      ue = fma(m1, e[i], ue);
+      int64_t ra = row_ptr[i], rb = row_ptr[i + 1];
+      for (int64_t k2 = ra + lane; k2 < rb; k2 += 32) row[lcol[k2]] = fma(m1, val[k2], row[lcol[k2]]);
+      __syncwarp();
+    }
+    double* Hr = H + l1 * ldh;
+    for (int64_t j = lane; j < a; j += 32) Hr[j] += row[j];
+    if (lane == 0) u[l1] = ue;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block assembly helpers
+// ---------------------------------------------------------------------------
+// T[u][v] = H[perm[u]][perm[v]] (symmetric, full)
+__global__ void k_gather_sym(const double* __restrict__ H, int64_t ldh, const int32_t* __restrict__ perm,
+                             int64_t m, double* __restrict__ T, int64_t ldt) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  int64_t u = e / m, v = e % m;
+  T[u * ldt + v] = H[(int64_t)perm[u] * ldh + perm[v]];
+}
+
+// Hn[pos[u]][pos[v]] = S[u][v] using the lower triangle of S (symmetric)
+__global__ void k_scatter_sym(const double* __restrict__ S, int64_t lds, int64_t m,
+                              const int32_t* __restrict__ pos, double* __restrict__ Hn, int64_t ldn) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  int64_t u = e / m, v = e % m;
+  double x = (v <= u) ? S[u * lds + v] : S[v * lds + u];
+  Hn[(int64_t)pos[u] * ldn + pos[v]] = x;
+}
+
+__global__ void k_scatter_diag(const int32_t* __restrict__ pos, int64_t m, double value,
+                               double* __restrict__ Hn, int64_t ldn) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < m) Hn[(int64_t)pos[u] * ldn + pos[u]] = value;
+}
+
+// B (m x q) = 0 except B[rowpos[c]][c] = 1
+__global__ void k_unit_rhs(double* __restrict__ B, int64_t m, int64_t q, const int32_t* __restrict__ rowpos) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * q) return;
+  int64_t r = e / q, cidx = e % q;
+  B[e] = (rowpos[cidx] == r) ? 1.0 : 0.0;
+}
+
+// gather G[u][v] = Pg[ids[u]][ids[v]]
+__global__ void k_gather_global(const double* __restrict__ Pg, int64_t M, const int32_t* __restrict__ gids,
+                                const int32_t* __restrict__ lpos, int64_t m, double* __restrict__ G) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  int64_t u = e / m, v = e % m;
+  G[e] = Pg[(int64_t)gids[lpos[u]] * M + gids[lpos[v]]];
+}
+
+__global__ void k_identity(double* __restrict__ B, int64_t m) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m * m) B[e] = (e / m == e % m) ? 1.0 : 0.0;
+}
+
+__global__ void k_copy_lower(const double* __restrict__ S, double* __restrict__ D, int64_t m, int64_t ld) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  D[(e / m) * ld + e % m] = S[(e / m) * ld + e % m];
+}
+
+// outside store: zero rows/columns of the leaving ids, then write their block
+__global__ void k_pg_zero(double* __restrict__ Pg, int64_t M, const int32_t* __restrict__ ids,
+                          const int32_t* __restrict__ lpos, int64_t d) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d * M) return;
+  int64_t q = e / M, j = e % M;
+  int64_t g = ids[lpos[q]];
+  Pg[g * M + j] = 0.0;
+  Pg[j * M + g] = 0.0;
+}
+
+__global__ void k_pg_block(double* __restrict__ Pg, int64_t M, const int32_t* __restrict__ ids,
+                           const int32_t* __restrict__ lpos, int64_t d, const double* __restrict__ Pdd) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d * d) return;
+  int64_t u = e / d, v = e % d;
+  Pg[(int64_t)ids[lpos[u]] * M + ids[lpos[v]]] = Pdd[e];
+}
+
+__global__ void k_pg_init(double* __restrict__ Pg, int64_t M, double diag) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < M) Pg[j * M + j] = diag;
+}
+
+__global__ void k_w_add(double* __restrict__ w, const int32_t* __restrict__ A, int64_t a,
+                        const double* __restrict__ delta) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < a) w[A[l]] += delta[l];
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static RowParams row_params(const rbf_config& cfg, double noise) {
+  RowParams R;
+  R.kernel = cfg.kernel;
+  R.inv_rho = 1.0 / cfg.rho;
+  double st2 = cfg.sigma * cfg.sigma + noise * noise;
+  R.g_scale = cfg.sigma * cfg.sigma / st2;
+  R.g_inv2s2 = 1.0 / (2.0 * st2);
+  return R;
+}
+
+// Solve H x = b with the Cholesky factor L (x overwrites b).  In mixed mode
+// the factor is only single-precision accurate, so the solution is refined
+// with float64 residuals r = b - H x until the correction stops shrinking.
+static rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld,
+                             double* b, bool refine, cudaStream_t s) {
+  if (!refine) {
+    RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, false, s));
+    RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, true, s));
+    return RBF_OK;
+  }
+  Buf& rb = c->scratch(31);
+  Buf& xb = c->scratch(32);
+  Buf& bb = c->scratch(33);
+  RBF_TRY(rb.ensure((size_t)a * sizeof(double)));
+  RBF_TRY(xb.ensure((size_t)a * sizeof(double)));
+  RBF_TRY(bb.ensure((size_t)a * sizeof(double)));
+  RBF_CUDA(cudaMemcpyAsync(bb.p, b, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RBF_CUDA(cudaMemcpyAsync(xb.p, b, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RBF_TRY(trsm_lower(c, L, a, ld, xb.as<double>(), 1, 1, false, s));
+  RBF_TRY(trsm_lower(c, L, a, ld, xb.as<double>(), 1, 1, true, s));
+  for (int it = 0; it < 6; ++it) {
+    RBF_TRY(symv_residual(H, a, ld, xb.as<double>(), bb.as<double>(), rb.as<double>(), s));
+    RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, false, s));
+    RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, true, s));
+    k_axpy<<<nblk(a), 256, 0, s>>>(xb.as<double>(), rb.as<double>(), a);
+    RBF_CUDA(cudaGetLastError());
+  }
+  RBF_CUDA(cudaMemcpyAsync(b, xb.p, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return RBF_OK;
+}
+
+// Inverse of an SPD matrix G (m x m, in place): G = L L^T, Z = L^{-1}, G^{-1} = Z^T Z.
+static rbf_status spd_inverse(Ctx* c, double* G, int64_t m, cudaStream_t s, int slot) {
+  Buf& Zb = c->scratch(slot);
+  RBF_TRY(Zb.ensure((size_t)m * m * sizeof(double)));
+  RBF_TRY(potrf_lower(c, G, m, m, m, false, s));
+  k_identity<<<nblk(m * m), 256, 0, s>>>(Zb.as<double>(), m);
+  RBF_CUDA(cudaGetLastError());
+  RBF_TRY(trsm_lower(c, G, m, m, Zb.as<double>(), m, m, false, s));
+  RBF_TRY(gemm_f64(true, false, m, m, m, 1.0, Zb.as<double>(), m, Zb.as<double>(), m, 0.0, G, m, s));
+  return RBF_OK;
+}
+
+}  // namespace rbf
+
+using namespace rbf;
+
+extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, double noise, void* stream) {
+  RBF_TRY(check_ctx(cx, true));
+  if (n < 0) return fail(RBF_EINVAL, "negative n");
+  if (n == 0) return RBF_OK;
+  if (!pts) return fail(RBF_EINVAL, "null points");
+  if (!(noise >= 0) || !isfinite(noise)) return fail(RBF_EINVAL, "noise must be finite and >= 0");
+  Ctx* c = C(cx);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t M = c->M;
+  const bool mixed = c->cfg.update_precision == RBF_UPDATE_MIXED;
+
+  // 1. neighbour lists
+  Buf& row_ptr = c->scratch(0);
+  Buf& col = c->scratch(1);
+  int64_t nnz = 0;
+  RBF_TRY(neighbor_lists(c, pts, n, 3, assembly_radius(c->cfg, noise), row_ptr, col, &nnz, s));
+  if (nnz == 0) return RBF_OK;
+
+  // 2. active set
+  Buf& mark = c->scratch(2);
+  Buf& pos = c->scratch(3);
+  Buf& An = c->scratch(4);
+  Buf& g2ln = c->scratch(5);
+  RBF_TRY(mark.ensure((size_t)M * sizeof(int32_t)));
+  RBF_TRY(pos.ensure((size_t)(M + 1) * sizeof(int32_t)));
+  RBF_TRY(An.ensure((size_t)M * sizeof(int32_t)));
+  RBF_TRY(g2ln.ensure((size_t)M * sizeof(int32_t)));
+  RBF_CUDA(cudaMemsetAsync(mark.p, 0, (size_t)M * sizeof(int32_t), s));
+  k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>());
+  RBF_CUDA(cudaGetLastError());
+  RBF_TRY(scan_i32(c, mark.as<int32_t>(), pos.as<int32_t>(), M, s, 48));
+  k_compact<<<nblk(M), 256, 0, s>>>(mark.as<int32_t>(), pos.as<int32_t>(), M, An.as<int32_t>(),
+                                    g2ln.as<int32_t>());
+  RBF_CUDA(cudaGetLastError());
+
+  // 3. relation to the previous block: S (stay), D (leave), E (enter)
+  const int64_t ap = c->a;
+  Buf& fl = c->scratch(6);
+  Buf& fpos = c->scratch(7);
+  Buf& Dl = c->scratch(8);   // prev-local positions of leaving centers
+  Buf& Sl = c->scratch(9);   // prev-local positions of staying centers
+  Buf& El = c->scratch(11);  // new-local positions of entering centers
+  Buf& Sn = c->scratch(12);  // new-local positions of staying centers
+  int64_t amax = (ap > M ? ap : M);
+  RBF_TRY(fl.ensure((size_t)(amax + 1) * sizeof(int32_t)));
+  RBF_TRY(fpos.ensure((size_t)(amax + 1) * sizeof(int32_t) * 4));
+  RBF_TRY(Dl.ensure((size_t)(amax + 1) * sizeof(int32_t)));
+  RBF_TRY(Sl.ensure((size_t)(amax + 1) * sizeof(int32_t)));
+  RBF_TRY(El.ensure((size_t)(amax + 1) * sizeof(int32_t)));
+  RBF_TRY(Sn.ensure((size_t)(amax + 1) * sizeof(int32_t)));
+  int32_t* fp = fpos.as<int32_t>();
+  int32_t* fpD = fp;                  // scan outputs, (ap+1) or (a+1) each
+  int32_t* fpS = fp + (amax + 1);
+  int32_t* fpE = fp + 2 * (amax + 1);
+  int32_t* fpSn = fp + 3 * (amax + 1);
+  Buf& fl2 = c->scratch(13);
+  RBF_TRY(fl2.ensure((size_t)(amax + 1) * sizeof(int32_t) * 2));
+  int32_t* flD = fl.as<int32_t>();
+  int32_t* flS = fl2.as<int32_t>();
+  int32_t* flE = fl2.as<int32_t>() + (amax + 1);
+  // sizes to the host: a, d, s, e
+  int64_t* hs = c->host_small;
+  RBF_CUDA(cudaMemcpyAsync(hs + 0, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RBF_CUDA(cudaStreamSynchronize(s));
+  const int64_t an = (int64_t)((int32_t*)hs)[0];
+  if (an == 0) return RBF_OK;
+  int64_t d = 0, sN = 0, e = an;
+  if (ap > 0) {
+    k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 0, flD);
+    k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 1, flS);
+    k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 0, flE);
+    RBF_CUDA(cudaGetLastError());
+    RBF_TRY(scan_i32(c, flD, fpD, ap, s, 48));
+    RBF_TRY(scan_i32(c, flS, fpS, ap, s, 48));
+    RBF_TRY(scan_i32(c, flE, fpE, an, s, 48));
+    // staying centers in new-local positions: flag = member of the previous block
+    Buf& flSn = c->scratch(14);
+    RBF_TRY(flSn.ensure((size_t)(an + 1) * sizeof(int32_t)));
+    k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 1,
+                                           flSn.as<int32_t>());
+    RBF_CUDA(cudaGetLastError());
+    RBF_TRY(scan_i32(c, flSn.as<int32_t>(), fpSn, an, s, 48));
+    k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flD, fpD, ap, Dl.as<int32_t>());
+    k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flS, fpS, ap, Sl.as<int32_t>());
+    k_list_from_flags<<<nblk(an), 256, 0, s>>>(flE, fpE, an, El.as<int32_t>());
+    k_list_from_flags<<<nblk(an), 256, 0, s>>>(flSn.as<int32_t>(), fpSn, an, Sn.as<int32_t>());
+    RBF_CUDA(cudaGetLastError());
+    int32_t* h32 = (int32_t*)hs;
+    RBF_CUDA(cudaMemcpyAsync(h32 + 0, fpD + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaMemcpyAsync(h32 + 1, fpS + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaMemcpyAsync(h32 + 2, fpE + an, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    d = h32[0];
+    sN = h32[1];
+    e = h32[2];
+    if (sN + e != an || sN + d != ap) return fail(RBF_ECUDA, "inconsistent active-set bookkeeping");
+  } else {
+    // every new center enters
+    Buf& flSn = c->scratch(14);
+    RBF_TRY(flSn.ensure((size_t)(an + 1) * sizeof(int32_t)));
+    RBF_CUDA(cudaMemsetAsync(flSn.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
+    // El = 0..an-1
+    std::vector<int32_t> iota((size_t)an);
+    for (int64_t l = 0; l < an; ++l) iota[l] = (int32_t)l;
+    RBF_CUDA(cudaMemcpyAsync(El.p, iota.data(), (size_t)an * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // 4. m~ entries, innovation, center-major lists
+  Buf& val = c->scratch(15);
+  Buf& lcol = c->scratch(16);
+  Buf& ev = c->scratch(17);
+  Buf& tcnt = c->scratch(18);
+  Buf& tstart = c->scratch(19);
+  Buf& tk = c->scratch(34);
+  RBF_TRY(val.ensure((size_t)nnz * sizeof(double)));
+  RBF_TRY(lcol.ensure((size_t)nnz * sizeof(int32_t)));
+  RBF_TRY(ev.ensure((size_t)n * sizeof(double)));
+  RBF_TRY(tcnt.ensure((size_t)(an + 1) * sizeof(int32_t)));
+  RBF_TRY(tstart.ensure((size_t)(an + 1) * sizeof(int64_t)));
+  RBF_TRY(tk.ensure((size_t)nnz * sizeof(int64_t)));
+  RowParams RP = row_params(c->cfg, noise);
+  k_rowvals<<<nblk(n), 256, 0, s>>>(RP, pts, n, row_ptr.as<int64_t>(), col.as<int32_t>(),
+                                    c->c64.as<double>(), c->w.as<double>(), g2ln.as<int32_t>(),
+                                    val.as<double>(), lcol.as<int32_t>(), ev.as<double>());
+  RBF_CUDA(cudaGetLastError());
+  RBF_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
+  k_tcount<<<nblk(nnz), 256, 0, s>>>(lcol.as<int32_t>(), nnz, tcnt.as<int32_t>());
+  RBF_CUDA(cudaGetLastError());
+  RBF_TRY(scan_i32_to_i64(c, tcnt.as<int32_t>(), tstart.as<int64_t>(), an, s, 48));
+  RBF_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
+  k_tfill<<<nblk(n), 256, 0, s>>>(row_ptr.as<int64_t>(), n, lcol.as<int32_t>(), tstart.as<int64_t>(),
+                                  tcnt.as<int32_t>(), tk.as<int64_t>());
+  RBF_CUDA(cudaGetLastError());
+  k_tsort<<<nblk(an), 256, 0, s>>>(tstart.as<int64_t>(), an, tk.as<int64_t>());
+  RBF_CUDA(cudaGetLastError());
+
+  // 5. leaving centers: their covariance block and the Schur complement
+  const int64_t ld = an;
+  Buf& Hn = c->scratch(35);
+  Buf& Ln = c->scratch(36);
+  Buf& u = c->scratch(37);
+  RBF_TRY(Hn.ensure((size_t)an * an * sizeof(double)));
+  RBF_TRY(Ln.ensure((size_t)an * an * sizeof(double)));
+  RBF_TRY(u.ensure((size_t)an * sizeof(double)));
+  RBF_CUDA(cudaMemsetAsync(Hn.p, 0, (size_t)an * an * sizeof(double), s));
+  Buf& Pdd = c->scratch(38);
+  if (d > 0) {
+    // Y = L_prev^{-1} E_D, P_DD = Y^T Y
+    Buf& Y = c->scratch(39);
+    RBF_TRY(Y.ensure((size_t)ap * d * sizeof(double)));
+    RBF_TRY(Pdd.ensure((size_t)d * d * sizeof(double)));
+    k_unit_rhs<<<nblk(ap * d), 256, 0, s>>>(Y.as<double>(), ap, d, Dl.as<int32_t>());
+    RBF_CUDA(cudaGetLastError());
+    RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s));
+    RBF_TRY(gemm_f64(true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
+                     Pdd.as<double>(), d, s));
+    if (sN > 0) {
+      // T = H_prev permuted to [D; S]; d steps of Cholesky leave H_S in T[d:, d:]
+      Buf& perm = c->scratch(40);
+      Buf& T = c->scratch(41);
+      RBF_TRY(perm.ensure((size_t)ap * sizeof(int32_t)));
+      RBF_TRY(T.ensure((size_t)ap * ap * sizeof(double)));
+      RBF_CUDA(cudaMemcpyAsync(perm.p, Dl.p, (size_t)d * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      RBF_CUDA(cudaMemcpyAsync(perm.as<int32_t>() + d, Sl.p, (size_t)sN * sizeof(int32_t),
+                               cudaMemcpyDeviceToDevice, s));
+      k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), ap,
+                                                 T.as<double>(), ap);
+      RBF_CUDA(cudaGetLastError());
+      RBF_TRY(potrf_lower(c, T.as<double>(), ap, ap, d, false, s));
+      k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>() + d * ap + d, ap, sN, Sn.as<int32_t>(),
+                                                  Hn.as<double>(), ld);
+      RBF_CUDA(cudaGetLastError());
+    }
+  } else if (sN > 0) {
+    // nobody leaves: the staying block is the previous information matrix
+    Buf& T = c->scratch(41);
+    RBF_TRY(T.ensure((size_t)ap * ap * sizeof(double)));
+    k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), sN,
+                                               T.as<double>(), sN);
+    RBF_CUDA(cudaGetLastError());
+    k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>(), sN, sN, Sn.as<int32_t>(), Hn.as<double>(),
+                                                ld);
+    RBF_CUDA(cudaGetLastError());
+  }
+
+  // 6. entering centers: inverse of their stored covariance block
+  if (e > 0) {
+    if (!c->pg_on) {
+      k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld);
+      RBF_CUDA(cudaGetLastError());
+    } else {
+      Buf& Gb = c->scratch(42);
+      RBF_TRY(Gb.ensure((size_t)e * e * sizeof(double)));
+      k_gather_global<<<nblk(e * e), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
+                                                   El.as<int32_t>(), e, Gb.as<double>());
+      RBF_CUDA(cudaGetLastError());
+      RBF_TRY(spd_inverse(c, Gb.as<double>(), e, s, 43));
+      k_scatter_sym<<<nblk(e * e), 256, 0, s>>>(Gb.as<double>(), e, e, El.as<int32_t>(), Hn.as<double>(),
+                                                ld);
+      RBF_CUDA(cudaGetLastError());
+    }
+  }
+
+  // 7. + m~ m~^T and u = m~ e
+  {
+    int dev_smem = 0;
+    RBF_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    int64_t per_warp = an * (int64_t)sizeof(double);
+    int warps = (int)((int64_t)dev_smem / per_warp);
+    if (warps > 4) warps = 4;
+    if (warps < 1) return fail(RBF_EINVAL, "active block of %lld centers exceeds shared memory", (long long)an);
+    size_t smem = (size_t)warps * per_warp;
+    RBF_CUDA(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned g = nblk(an, warps);
+    k_gram_rows<<<g, warps * 32, smem, s>>>(an, ld, tstart.as<int64_t>(), tk.as<int64_t>(),
+                                             row_ptr.as<int64_t>(), n, val.as<double>(),
+                                             lcol.as<int32_t>(), ev.as<double>(), Hn.as<double>(),
+                                             u.as<double>());
+    RBF_CUDA(cudaGetLastError());
+  }
+
+  // 8. factor H' and solve for the weight increment
+  RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, mixed, s));
+  int flag = 0;
+  RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
+  RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), mixed, s));
+  RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
+
+  // 9. commit
+  k_w_add<<<nblk(an), 256, 0, s>>>(c->w.as<double>(), An.as<int32_t>(), an, u.as<double>());
+  RBF_CUDA(cudaGetLastError());
+  if (d > 0) {
+    if (!c->pg_on) {
+      RBF_TRY(c->Pg.ensure((size_t)M * M * sizeof(double)));
+      RBF_CUDA(cudaMemsetAsync(c->Pg.p, 0, (size_t)M * M * sizeof(double), s));
+      k_pg_init<<<nblk(M), 256, 0, s>>>(c->Pg.as<double>(), M, 1.0 / c->cfg.lambda);
+      RBF_CUDA(cudaGetLastError());
+      c->pg_on = true;
+    }
+    k_pg_zero<<<nblk(d * M), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d);
+    RBF_CUDA(cudaGetLastError());
+    k_pg_block<<<nblk(d * d), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d,
+                                           Pdd.as<double>());
+    RBF_CUDA(cudaGetLastError());
+  }
+  std::swap(c->H, Hn);
+  std::swap(c->L, Ln);
+  std::swap(c->A, An);
+  std::swap(c->g2l, g2ln);
+  c->a = an;
+  c->ldH = ld;
+  RBF_TRY(refresh_center_weights(c, s));
+  return RBF_OK;
+}
+
+extern "C" rbf_status rbf_get_active(rbf_ctx* cx, int32_t* A, int64_t cap, int64_t* a_out, void* stream) {
+  RBF_TRY(check_ctx(cx, true));
+  if (!a_out) return fail(RBF_EINVAL, "null a_out");
+  Ctx* c = C(cx);
+  *a_out = c->a;
+  if (c->a == 0) return RBF_OK;
+  if (!A) return fail(RBF_EINVAL, "null A");
+  if (cap < c->a) return fail(RBF_ERANGE, "capacity %lld < %lld", (long long)cap, (long long)c->a);
+  cudaStream_t s = (cudaStream_t)stream;
+  RBF_CUDA(cudaMemcpyAsync(A, c->A.p, (size_t)c->a * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  RBF_CUDA(cudaStreamSynchronize(s));
+  return RBF_OK;
+}
+
+extern "C" rbf_status rbf_get_neighbors(rbf_ctx* cx, const float* pts, int64_t n, double noise,
+                                        int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz_out,
+                                        void* stream) {
+  RBF_TRY(check_ctx(cx, true));
+  if (n < 0 || !nnz_out || !row_ptr) return fail(RBF_EINVAL, "bad arguments");
+  if (n > 0 && !pts) return fail(RBF_EINVAL, "null points");
+  Ctx* c = C(cx);
+  cudaStream_t s = (cudaStream_t)stream;
+  Buf& rp = c->scratch(0);
+  Buf& cl = c->scratch(1);
+  int64_t nnz = 0;
+  if (n == 0) {
+    RBF_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s));
+    *nnz_out = 0;
+    return RBF_OK;
+  }
+  RBF_TRY(neighbor_lists(c, pts, n, 3, assembly_radius(c->cfg, noise), rp, cl, &nnz, s));
+  *nnz_out = nnz;
+  RBF_CUDA(cudaMemcpyAsync(row_ptr, rp.p, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  if (nnz > cap) {
+    RBF_CUDA(cudaStreamSynchronize(s));
+    return fail(RBF_ERANGE, "capacity %lld < %lld entries", (long long)cap, (long long)nnz);
+  }
+  if (nnz > 0) {
+    if (!col) return fail(RBF_EINVAL, "null col");
+    RBF_CUDA(cudaMemcpyAsync(col, cl.p, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
+  RBF_CUDA(cudaStreamSynchronize(s));
+  return RBF_OK;
+}
+
+// P[ids, ids]: active ids from the factor of the block's information matrix,
+// the others from the outside store (or the prior), zero across the two.
+__global__ void k_cov_assemble(int64_t k, const int32_t* __restrict__ ids, const int32_t* __restrict__ g2l,
+                               const int32_t* __restrict__ rank_in_active, const double* __restrict__ Paa,
+                               int64_t ka, const double* __restrict__ Pg, int64_t M, int pg_on,
+                               double prior, double* __restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  int64_t u = e / k, v = e % k;
+  int iu = ids[u], iv = ids[v];
+  bool au = g2l[iu] >= 0, av = g2l[iv] >= 0;
+  double x = 0.0;
+  if (au && av) {
+    x = Paa[(int64_t)rank_in_active[u] * ka + rank_in_active[v]];
+  } else if (!au && !av) {
+    if (pg_on) x = Pg[(int64_t)iu * M + iv];
+    else x = (iu == iv) ? prior : 0.0;
+  }
+  out[e] = x;
+}
+
+extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, double* Pk, void* stream) {
+  RBF_TRY(check_ctx(cx, true));
+  if (k < 0) return fail(RBF_EINVAL, "negative k");
+  if (k == 0) return RBF_OK;
+  if (!ids || !Pk) return fail(RBF_EINVAL, "null argument");
+  Ctx* c = C(cx);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int64_t u = 0; u < k; ++u)
+    if (ids[u] < 0 || ids[u] >= c->M) return fail(RBF_EINVAL, "id %d out of range", ids[u]);
+  // local indices of the active ids (host copy of g2l)
+  std::vector<int32_t> g2l((size_t)c->M, -1);
+  if (c->a > 0)
+    RBF_CUDA(cudaMemcpyAsync(g2l.data(), c->g2l.p, (size_t)c->M * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RBF_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> rank((size_t)k, -1), lpos;
+  for (int64_t u = 0; u < k; ++u) {
+    int l = c->a > 0 ? g2l[ids[u]] : -1;
+    if (l >= 0) {
+      rank[u] = (int32_t)lpos.size();
+      lpos.push_back(l);
+    }
+  }
+  int64_t ka = (int64_t)lpos.size();
+  Buf& ib = c->scratch(44);
+  Buf& rb = c->scratch(45);
+  Buf& lb = c->scratch(46);
+  Buf& Y = c->scratch(47);
+  Buf& Paa = c->scratch(39);
+  RBF_TRY(ib.ensure((size_t)k * sizeof(int32_t)));
+  RBF_TRY(rb.ensure((size_t)k * sizeof(int32_t)));
+  RBF_CUDA(cudaMemcpyAsync(ib.p, ids, (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  RBF_CUDA(cudaMemcpyAsync(rb.p, rank.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (ka > 0) {
+    RBF_TRY(lb.ensure((size_t)ka * sizeof(int32_t)));
+    RBF_TRY(Y.ensure((size_t)c->a * ka * sizeof(double)));
+    RBF_TRY(Paa.ensure((size_t)ka * ka * sizeof(double)));
+    RBF_CUDA(cudaMemcpyAsync(lb.p, lpos.data(), (size_t)ka * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_unit_rhs<<<nblk(c->a * ka), 256, 0, s>>>(Y.as<double>(), c->a, ka, lb.as<int32_t>());
+    RBF_CUDA(cudaGetLastError());
+    RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s));
+    RBF_TRY(gemm_f64(true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,
+                     Paa.as<double>(), ka, s));
+  }
+  k_cov_assemble<<<nblk(k * k), 256, 0, s>>>(k, ib.as<int32_t>(), c->g2l.as<int32_t>(), rb.as<int32_t>(),
+                                             ka > 0 ? Paa.as<double>() : nullptr, ka,
+                                             c->pg_on ? c->Pg.as<double>() : nullptr, c->M, c->pg_on ? 1 : 0,
+                                             1.0 / c->cfg.lambda, Pk);
+  RBF_CUDA(cudaGetLastError());
+  RBF_CUDA(cudaStreamSynchronize(s));
+  int flag = 0;
+  RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
+  return RBF_OK;
+}
