@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the RBF terrain hot path on one GB300 (or N replicas).
+
+Workload: the LIO staircase sequence -- M = 4,096 centers on a 64 x 64 grid
+at 0.2 m, Wendland C2 support 0.6 m, lambda = 1e-3; every frame is a
+synthetic Mid360-like scan whose 8,000 ground returns (range noise 3 cm) feed
+one recursive ridge update; the soft-constraint cost and h / grad h are then
+evaluated at the same 8,000 points.  One step = one frame:
+
+    rbf_update (neighbour lists, active set, m~ entries, information matrix
+                of the active block, Cholesky, weight increment)
+  + rbf_soft_cost (cost and pose gradient at the frame's points)
+  + rbf_eval (h and grad h at the frame's points)
+
+The headline ``value`` is frames/s with the frame's points already in HBM;
+``e2e`` is the same through host (pinned) buffers with the copies in the
+timed region.  ``eval`` reports rbf_eval throughput on 2^26 uniform random
+queries over the grid.  The L2 cache (126 MB) is flushed between steps by
+writing a 512 MB buffer outside the timed interval.
+
+--impl reference times the FP64 CPU oracle on the same workload on this
+machine's host cores (the paper publishes no code; the oracle is the
+reference implementation of what the path computes).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RBF h+∇h queries/s, update frames/s at M=4096; % HBM/tensor roofline"
+WORKLOAD = ("LIO staircase sequence: M=4096 centers (64x64 @ 0.2 m), Wendland C2 rho=0.6 m, "
+            "lambda=1e-3; per frame 8000 ground returns -> rbf_update + rbf_soft_cost + rbf_eval")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+NOISE = 0.03
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,power.draw",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                s = float(parts[0])
+                mx = max(mx, float(parts[1]))
+                bits = int(parts[2], 16)
+            except ValueError:
+                continue
+            sm.append(s)
+            for b, name in REASON_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def frame_arrays(k):
+    from paper_2509_26222_gb300 import workloads as W
+    ground, sensor, _ = W.config2_frame(k)
+    body = ground - sensor[None, :]
+    return ground.astype(np.float32), body.astype(np.float32), sensor
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2509_26222_gb300 import native as N, workloads as W
+
+    N.load(build_if_missing=True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = N.UPDATE_MIXED if args.precision == "mixed" else N.UPDATE_FP64
+    centers = torch.tensor(W.config2_centers(), device=dev)
+    nfr = args.warmup + args.steps
+    frames = [frame_arrays(k % W.C2_FRAMES) for k in range(2 * nfr)]
+    eye = np.eye(3)
+
+    def make_terrain():
+        T = N.Terrain(rho=0.6, lam=1e-3, update_precision=prec, huber_delta=0.05)
+        T.set_centers(centers)
+        return T
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # ----- device-resident run (headline) -----
+    T = make_terrain()
+    dev_frames = [(torch.tensor(g, device=dev), torch.tensor(b, device=dev), s) for g, b, s in frames[:nfr]]
+    h = torch.empty(8000, device=dev)
+    grad = torch.empty(8000, 2, device=dev)
+    out7 = torch.empty(7, dtype=torch.float64, device=dev)
+
+    def step(fr):
+        g, b, s = fr
+        T.update(g, noise=NOISE)
+        T.soft_cost(eye, s, b, out=out7)
+        T.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
+
+    for k in range(args.warmup):
+        step(dev_frames[k])
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    T.profile(True)
+    T.profile_read(reset=True)
+    l0 = N.launch_count()
+    times = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.warmup, nfr):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(dev_frames[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    launches = N.launch_count() - l0
+    prof = T.profile_read(reset=True)
+    T.profile(False)
+    total_ms = float(sum(times))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    a_last = int(T.active().numel())
+
+    # ----- end to end through host buffers -----
+    T2 = make_terrain()
+    host = [(torch.tensor(g).pin_memory(), torch.tensor(b).pin_memory(), s) for g, b, s in frames[nfr:]]
+    h_host = torch.empty(8000, pin_memory=True)
+    grad_host = torch.empty(8000, 2, pin_memory=True)
+    o_host = torch.empty(7, dtype=torch.float64, pin_memory=True)
+    h2d = d2h = 0
+
+    def e2e_step(fr):
+        nonlocal h2d, d2h
+        g, b, s = fr
+        gd = g.to(dev, non_blocking=True)
+        bd = b.to(dev, non_blocking=True)
+        T2.update(gd, noise=NOISE)
+        T2.soft_cost(eye, s, bd, out=out7)
+        T2.eval(gd[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
+        o_host.copy_(out7, non_blocking=True)
+        h_host[: g.shape[0]].copy_(h[: g.shape[0]], non_blocking=True)
+        grad_host[: g.shape[0]].copy_(grad[: g.shape[0]], non_blocking=True)
+        return g.numel() * 4 + b.numel() * 4, 7 * 8 + g.shape[0] * 12
+
+    for k in range(args.warmup):
+        e2e_step(host[k])
+    torch.cuda.synchronize()
+    e2e_times = []
+    for k in range(args.warmup, nfr):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bi, bo = e2e_step(host[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+        h2d, d2h = bi, bo
+    e2e_ms = float(sum(e2e_times))
+    T2.close()
+
+    # ----- eval throughput on 2^26 random queries -----
+    Q = 1 << args.eval_log2
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    q = (torch.rand(Q, 2, device=dev, generator=gen, dtype=torch.float32) * 12.8 - 6.4).contiguous()
+    hq = torch.empty(Q, device=dev)
+    gq = torch.empty(Q, 2, device=dev)
+    for _ in range(3):
+        T.eval(q, out_h=hq, out_grad=gq)
+    torch.cuda.synchronize()
+    T.profile(True)
+    T.profile_read(reset=True)
+    ev = []
+    for r in range(5):
+        flush.fill_(float(r))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        T.eval(q, out_h=hq, out_grad=gq)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ev.append(e0.elapsed_time(e1))
+    T.profile(False)
+    eval_ms = float(np.median(ev))
+    T.close()
+    return dict(times=times, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, prof=prof,
+                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q)
+
+
+# ---------------------------------------------------------------------------
+# the FP64 CPU oracle on the same workload
+# ---------------------------------------------------------------------------
+def oracle_frames(ks, budget_s=None):
+    from oracle import rbf_oracle as O
+    from paper_2509_26222_gb300 import workloads as W
+    st = O.BlockState(W.config2_centers(), 1e-3, O.WENDLAND, rho=0.6)
+    eye = np.eye(3)
+    times = []
+    t_start = time.perf_counter()
+    for k in ks:
+        g, b, s = frame_arrays(k)
+        g64 = g.astype(np.float64)
+        t0 = time.perf_counter()
+        O.block_update(st, g64, noise=NOISE)
+        O.soft_cost(eye, s, b.astype(np.float64), st.c, st.w, O.WENDLAND, rho=0.6, delta=0.05)
+        O.eval_h(g64[:, :2], st.c, st.w, O.WENDLAND, rho=0.6, chunk=256)
+        times.append(time.perf_counter() - t0)
+        if budget_s is not None and time.perf_counter() - t_start > budget_s:
+            break
+    return times
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    ks = list(range(args.warmup + args.steps))
+    t = oracle_frames(ks)
+    timed = t[args.warmup:]
+    total = float(sum(timed))
+    value = len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws,
+        "steps": len(timed), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle (numpy)"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"frames {args.warmup}..{len(ks) - 1} of the sequence, full frames"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--eval-log2", type=int, default=26)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    r = run_ours(args, ws, rank, local)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    pk, pk_kind = peaks()
+    K = len(r["times"])
+    value = ws * K / (r["total_ms"] * 1e-3)
+    prof = r["prof"]
+    # dominant kernel stage of the step
+    kstages = ["trailing", "panel", "solve", "assembly", "block", "neighbors", "eval", "softcost"]
+    dom = max(kstages, key=lambda s: prof[s][0])
+    ms, work, cnt = prof[dom]
+    roof = None
+    if dom in ("trailing", "panel", "solve") and ms > 0:
+        tf = work / (ms * 1e-3) / 1e12
+        prec_mixed = args.precision == "mixed" and dom == "trailing"
+        peak = pk["bf16_tflops_sustained"] if prec_mixed else FP64_NOMINAL_TFLOPS
+        roof = {"kernel": dom, "bound": "tensor" if prec_mixed else "alu", "achieved": tf, "peak": peak,
+                "unit": "TFLOP/s", "frac": tf / peak, "traffic": None,
+                "peak_kind": ("bf16 sustained, " + pk_kind) if prec_mixed else "FP64 nominal 1.25 TFLOP/s (recipe)",
+                "launches": int(cnt), "ms_per_launch": ms / max(cnt, 1),
+                "flops_per_launch": work / max(cnt, 1)}
+    elif ms > 0:
+        gbs = work / (ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind}
+    eval_qps = r["Q"] / (r["eval_ms"] * 1e-3)
+    eval_gbs = 20.0 * eval_qps / 1e9
+    stage_ms = {s: round(prof[s][0] / K, 4) for s in prof}
+    cpu = None
+    if not args.no_cpu:
+        ct = oracle_frames(range(0, 100), budget_s=args.cpu_budget)
+        cpu = {"value": len(ct) / sum(ct), "unit": "frames/s", "cores": cores(), "kind": "oracle",
+               "sample": f"first {len(ct)} frames of the sequence (full frames), about {args.cpu_budget:.0f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": r["total_ms"] / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+bf16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "update_precision": args.precision, "frames_timed": K,
+                   "active_block_last": r["a_last"], "l2": "flushed between steps (512 MB write)",
+                   "eval_dtype": "f32", "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "e2e": {"value": ws * K / (r["e2e_ms"] * 1e-3), "unit": "frames/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": int(r["launches"]),
+        "roofline": roof,
+        "eval": {"queries_per_s": eval_qps * ws, "Q": r["Q"], "ms": r["eval_ms"],
+                 "roofline": {"bound": "hbm", "achieved": eval_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                              "frac": eval_gbs / pk["hbm_gbs"], "traffic": None,
+                              "bytes_per_query": 20, "peak_kind": pk_kind}},
+        "stage_ms_per_step": stage_ms,
+        "clocks": r["clocks"],
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,31 @@ rbf_status rbf_get_neighbors(rbf_ctx* ctx, const float* pts, int64_t n, double n
                              int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz_out,
                              void* stream);
 
+/* Stage timing.  While enabled, every call records CUDA events on its own
+ * stream around each stage below and adds the stage's algorithmic work
+ * (floating-point operations, or bytes for the memory-bound stages).
+ * rbf_profile_read synchronizes, returns the accumulated milliseconds,
+ * work and number of timed intervals per stage (arrays of RBF_NSTAGE) and
+ * optionally resets them.  Tracing is host bookkeeping only: it changes no
+ * result. */
+enum {
+  RBF_STAGE_NEIGHBORS = 0,  /* neighbour lists + active set (bytes: 12 per point) */
+  RBF_STAGE_ASSEMBLY = 1,   /* m~ entries, innovation, m~ m~^T rows (flops) */
+  RBF_STAGE_BLOCK = 2,      /* leaving/entering centers: Schur complement, stored blocks */
+  RBF_STAGE_PANEL = 3,      /* Cholesky diagonal tiles + panel solves (flops) */
+  RBF_STAGE_TRAILING = 4,   /* Cholesky trailing updates, one interval per launch (flops) */
+  RBF_STAGE_SOLVE = 5,      /* triangular solves and refinement (flops) */
+  RBF_STAGE_EVAL = 6,       /* rbf_eval (bytes: 8 in + 12 out per query) */
+  RBF_STAGE_SOFTCOST = 7,   /* rbf_soft_cost (bytes: 12 in per point) */
+  RBF_STAGE_BACKWARD = 8,   /* rbf_soft_cost_backward (bytes: 12 in + 12 out) */
+  RBF_NSTAGE = 9
+};
+rbf_status rbf_profile_enable(rbf_ctx* ctx, int on);
+/* Number of CUDA kernels librbfgb.so has launched since it was loaded (all
+ * contexts and threads; host counter, no synchronization). */
+rbf_status rbf_launch_count(int64_t* n);
+rbf_status rbf_profile_read(rbf_ctx* ctx, double* ms, double* work, int64_t* count, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -12,6 +13,9 @@
 namespace rbf {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 rbf_status fail(rbf_status st, const char* fmt, ...) {
   char buf[512];
@@ -35,7 +39,10 @@ rbf_status Buf::ensure(size_t nbytes) {
     p = nullptr;
     bytes = 0;
   }
-  size_t want = nbytes < 256 ? 256 : nbytes;
+  // grow with 25% slack so that sizes that creep up frame by frame do not
+  // reallocate (and synchronize) on every call
+  size_t want = nbytes < 256 ? 256 : nbytes + nbytes / 4;
+  want = (want + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(&p, want);
   if (e != cudaSuccess) {
     p = nullptr;
@@ -146,23 +153,23 @@ template <class Tin, class Tout>
 static rbf_status scan_impl(Ctx* c, const Tin* in, Tout* out, int64_t n, cudaStream_t s,
                             int slot) {
   if (n <= 0) {
-    k_scan_total<Tin, Tout><<<1, 1, 0, s>>>(in, out, 0);
+    { k_scan_total<Tin, Tout><<<1, 1, 0, s>>>(in, out, 0); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     return RBF_OK;
   }
   int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   Buf& sums = c->scratch(slot);
   RBF_TRY(sums.ensure((size_t)(tiles + 1) * sizeof(Tout)));
-  k_scan_tiles<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, sums.as<Tout>());
+  { k_scan_tiles<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, sums.as<Tout>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   if (tiles > 1) {
     Buf& offs = c->scratch(slot + 1);
     RBF_TRY(offs.ensure((size_t)(tiles + 1) * sizeof(Tout)));
     RBF_TRY((scan_impl<Tout, Tout>(c, sums.as<Tout>(), offs.as<Tout>(), tiles, s, slot + 2)));
-    k_scan_add<Tout><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, offs.as<Tout>());
+    { k_scan_add<Tout><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, offs.as<Tout>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
-  k_scan_total<Tin, Tout><<<1, 1, 0, s>>>(in, out, n);
+  { k_scan_total<Tin, Tout><<<1, 1, 0, s>>>(in, out, n); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
@@ -244,15 +251,15 @@ rbf_status refresh_center_weights(Ctx* c, cudaStream_t s) {
   int64_t M = c->M;
   if (M <= 0) return RBF_OK;
   unsigned nb = (unsigned)((M + 255) / 256);
-  k_sorted_xyw<<<nb, 256, 0, s>>>(c->c64.as<double>(), c->w.as<double>(),
-                                  c->sorted_id.as<int32_t>(), M, c->sorted_xyw.as<float4>());
+  { k_sorted_xyw<<<nb, 256, 0, s>>>(c->c64.as<double>(), c->w.as<double>(),
+                                  c->sorted_id.as<int32_t>(), M, c->sorted_xyw.as<float4>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   if (c->lat.on) {
     size_t cells = (size_t)c->lat.nx * c->lat.ny;
     RBF_CUDA(cudaMemsetAsync(c->wlat.p, 0, cells * sizeof(float), s));
-    k_lattice_w<<<nb, 256, 0, s>>>(c->c64.as<double>(), c->w.as<double>(), M, c->lat.x0,
+    { k_lattice_w<<<nb, 256, 0, s>>>(c->c64.as<double>(), c->w.as<double>(), M, c->lat.x0,
                                    c->lat.y0, 1.0 / c->lat.h, c->lat.nx, c->lat.ny,
-                                   c->wlat.as<float>());
+                                   c->wlat.as<float>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   return RBF_OK;
@@ -350,16 +357,16 @@ rbf_status build_center_grid(Ctx* c, cudaStream_t s) {
   RBF_TRY(cnt.ensure((size_t)(ncell + 1) * sizeof(int32_t)));
   RBF_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
   unsigned nb = (unsigned)((M + 255) / 256);
-  k_center_cells<<<nb, 256, 0, s>>>(c->c64.as<double>(), M, g, cell.as<int32_t>(),
-                                    cnt.as<int32_t>());
+  { k_center_cells<<<nb, 256, 0, s>>>(c->c64.as<double>(), M, g, cell.as<int32_t>(),
+                                    cnt.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(c, cnt.as<int32_t>(), c->cell_start.as<int32_t>(), ncell, s, 48));
   RBF_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
-  k_center_fill<<<nb, 256, 0, s>>>(cell.as<int32_t>(), M, c->cell_start.as<int32_t>(),
-                                   cnt.as<int32_t>(), c->sorted_id.as<int32_t>());
+  { k_center_fill<<<nb, 256, 0, s>>>(cell.as<int32_t>(), M, c->cell_start.as<int32_t>(),
+                                   cnt.as<int32_t>(), c->sorted_id.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  k_sort_cells<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(c->cell_start.as<int32_t>(), ncell,
-                                                               c->sorted_id.as<int32_t>());
+  { k_sort_cells<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(c->cell_start.as<int32_t>(), ncell,
+                                                               c->sorted_id.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   if (c->lat.on) RBF_TRY(c->wlat.ensure((size_t)c->lat.nx * c->lat.ny * sizeof(float)));
   return refresh_center_weights(c, s);
@@ -392,9 +399,79 @@ rbf_status install_centers(Ctx* c, const double* cxy, int64_t M, cudaStream_t s)
   return RBF_OK;
 }
 
+static cudaEvent_t take_event(Ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+StageTimer::StageTimer(Ctx* c_, int stage_, cudaStream_t s_, double work_)
+    : c(c_), stage(stage_), s(s_), work(work_) {
+  if (!c->prof) return;
+  a = take_event(c);
+  if (a) cudaEventRecord(a, s);
+}
+
+StageTimer::~StageTimer() {
+  if (!a) return;
+  cudaEvent_t b = take_event(c);
+  if (!b) return;
+  cudaEventRecord(b, s);
+  c->marks.push_back({stage, a, b, work});
+}
+
+static void profile_collect(Ctx* c) {
+  for (auto& m : c->marks) {
+    float ms = 0.f;
+    cudaEventSynchronize(m.b);
+    if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      c->prof_ms[m.stage] += ms;
+      c->prof_work[m.stage] += m.work;
+      c->prof_count[m.stage] += 1;
+    }
+    c->ev_pool.push_back(m.a);
+    c->ev_pool.push_back(m.b);
+  }
+  c->marks.clear();
+}
+
 }  // namespace rbf
 
 using namespace rbf;
+
+extern "C" rbf_status rbf_launch_count(int64_t* n) {
+  if (!n) return fail(RBF_EINVAL, "null output");
+  *n = (int64_t)g_launches.load();
+  return RBF_OK;
+}
+
+extern "C" rbf_status rbf_profile_enable(rbf_ctx* cx, int on) {
+  RBF_TRY(check_ctx(cx, false));
+  C(cx)->prof = on != 0;
+  return RBF_OK;
+}
+
+extern "C" rbf_status rbf_profile_read(rbf_ctx* cx, double* ms, double* work, int64_t* count, int reset) {
+  RBF_TRY(check_ctx(cx, false));
+  Ctx* c = C(cx);
+  profile_collect(c);
+  for (int k = 0; k < RBF_NSTAGE; ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (work) work[k] = c->prof_work[k];
+    if (count) count[k] = c->prof_count[k];
+    if (reset) {
+      c->prof_ms[k] = 0.0;
+      c->prof_work[k] = 0.0;
+      c->prof_count[k] = 0;
+    }
+  }
+  return RBF_OK;
+}
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -454,6 +531,11 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   if (x->host_small) cudaFreeHost(x->host_small);
+  for (auto& m : x->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (cudaEvent_t e : x->ev_pool) cudaEventDestroy(e);
   delete c;
   return RBF_OK;
 }

@@ -126,24 +126,24 @@ extern "C" rbf_status rbf_build_centers(rbf_ctx* cx, const float* pts, int64_t n
   RBF_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(nc + 1) * sizeof(int32_t), s));
   unsigned nbp = (unsigned)((n + 255) / 256), nbc = (unsigned)((nc + 255) / 256);
   if (n > 0) {
-    k_pt_cells<<<nbp, 256, 0, s>>>(pts, n, g, pcell.as<int32_t>(), cnt.as<int32_t>(), c->dflag.as<int>());
+    { k_pt_cells<<<nbp, 256, 0, s>>>(pts, n, g, pcell.as<int32_t>(), cnt.as<int32_t>(), c->dflag.as<int>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   RBF_TRY(scan_i32(c, cnt.as<int32_t>(), start.as<int32_t>(), nc, s, 48));
   RBF_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(nc + 1) * sizeof(int32_t), s));
   if (n > 0) {
-    k_pt_fill<<<nbp, 256, 0, s>>>(pcell.as<int32_t>(), n, start.as<int32_t>(), cnt.as<int32_t>(),
-                                  binned.as<float2>(), pts);
+    { k_pt_fill<<<nbp, 256, 0, s>>>(pcell.as<int32_t>(), n, start.as<int32_t>(), cnt.as<int32_t>(),
+                                  binned.as<float2>(), pts); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   float r32 = (float)cfg.r_kd;
   float r2 = r32 * r32;
   float rc = (float)(cfg.r_kd / cfg.mesh_h);
   int32_t* cnt_out = counts ? counts : cc.as<int32_t>();
-  k_count_cands<<<nbc, 256, 0, s>>>(cfg.mesh_x0, cfg.mesh_y0, cfg.mesh_h, g, r2, rc, start.as<int32_t>(),
-                                    binned.as<float2>(), cnt_out);
+  { k_count_cands<<<nbc, 256, 0, s>>>(cfg.mesh_x0, cfg.mesh_y0, cfg.mesh_h, g, r2, rc, start.as<int32_t>(),
+                                    binned.as<float2>(), cnt_out); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  k_accept<<<nbc, 256, 0, s>>>(cnt_out, nc, cfg.min_count, acc.as<int32_t>());
+  { k_accept<<<nbc, 256, 0, s>>>(cnt_out, nc, cfg.min_count, acc.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(c, acc.as<int32_t>(), pos.as<int32_t>(), nc, s, 48));
   int32_t* h32 = (int32_t*)c->host_small;
@@ -159,8 +159,8 @@ extern "C" rbf_status rbf_build_centers(rbf_ctx* cx, const float* pts, int64_t n
     return RBF_OK;
   }
   RBF_TRY(outc.ensure((size_t)M * 2 * sizeof(double)));
-  k_emit<<<nbc, 256, 0, s>>>(acc.as<int32_t>(), pos.as<int32_t>(), nc, cfg.mesh_nx, cfg.mesh_x0, cfg.mesh_y0,
-                             cfg.mesh_h, outc.as<double>());
+  { k_emit<<<nbc, 256, 0, s>>>(acc.as<int32_t>(), pos.as<int32_t>(), nc, cfg.mesh_nx, cfg.mesh_x0, cfg.mesh_y0,
+                             cfg.mesh_h, outc.as<double>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   // install_centers copies from outc; it uses scratch slots 0-1 and 48+ only
   // after the copy, so outc (slot 7) stays valid.

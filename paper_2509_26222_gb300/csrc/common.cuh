@@ -103,6 +103,30 @@ struct Ctx {
 
   // host pinned staging for small readbacks
   int64_t* host_small = nullptr;
+
+  // stage timing (rbf_profile_enable)
+  bool prof = false;
+  struct Mark {
+    int stage;
+    cudaEvent_t a, b;
+    double work;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[RBF_NSTAGE] = {};
+  double prof_work[RBF_NSTAGE] = {};
+  int64_t prof_count[RBF_NSTAGE] = {};
+};
+
+// Scoped stage interval: records an event pair on stream s when profiling is on.
+struct StageTimer {
+  Ctx* c;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  double work;
+  StageTimer(Ctx* c_, int stage_, cudaStream_t s_, double work_ = 0.0);
+  ~StageTimer();
 };
 
 rbf_status check_ctx(rbf_ctx* c, bool need_centers);
@@ -182,12 +206,21 @@ rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride_floats
 
 rbf_status read_dev_flag(Ctx* c, cudaStream_t s, int* flag);
 
+// number of kernels this library has launched (all contexts, all threads)
+void note_launch();
+inline cudaError_t cooperative_launch(const void* f, dim3 g, dim3 b, void** args, size_t smem,
+                                      cudaStream_t s) {
+  cudaError_t e = cudaLaunchCooperativeKernel(f, g, b, args, smem, s);
+  if (e == cudaSuccess) note_launch();
+  return e;
+}
+
 // dense FP64 / mixed-precision linear algebra (dense.cu)
 rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfactor,
                        bool mixed, cudaStream_t s);
 rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B, int64_t m,
                       int64_t ldb, bool transpose, cudaStream_t s);
-rbf_status gemm_f64(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                     double* Cm, int64_t ldc, cudaStream_t s);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,

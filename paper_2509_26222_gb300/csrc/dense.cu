@@ -29,6 +29,8 @@ constexpr int NB = 32;
 // CTA participate.  T is [32][33].  Returns through T (lower triangle).
 // ---------------------------------------------------------------------------
 __device__ void chol_tile_smem(double (*T)[NB + 1], int kb, int* flag) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  __shared__ double rinv;
   for (int j = 0; j < kb; ++j) {
     if (threadIdx.x == 0) {
       double d = T[j][j];
@@ -36,16 +38,17 @@ __device__ void chol_tile_smem(double (*T)[NB + 1], int kb, int* flag) {
         atomicOr(flag, DEV_NOT_SPD);
         d = 1.0;
       }
-      T[j][j] = sqrt(d);
+      double r = sqrt(d);
+      T[j][j] = r;
+      rinv = 1.0 / r;
     }
     __syncthreads();
-    double piv = T[j][j];
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) T[i][j] /= piv;
+    if (threadIdx.x < 32 && tx > j && tx < kb) T[tx][j] *= rinv;
     __syncthreads();
-    int m = kb - j - 1;  // trailing size
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) T[i][k] -= T[i][j] * T[k][j];
+    if (tx > j) {
+      double tkj = T[tx][j];
+      for (int i = ty; i < kb; i += ny)
+        if (i >= tx) T[i][tx] -= T[i][j] * tkj;
     }
     __syncthreads();
   }
@@ -161,17 +164,21 @@ rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfacto
   for (int64_t k = 0; k < nfactor; k += NB) {
     int kb = (int)((nfactor - k) < NB ? (nfactor - k) : NB);
     int64_t rows = n - k - kb;
-    int rows_per_cta = 64;
+    int rows_per_cta = 16;
     int64_t ctas = rows > 0 ? (rows + rows_per_cta - 1) / rows_per_cta : 1;
-    k_potrf_panel<<<(unsigned)ctas, 256, 0, s>>>(A, lda, n, k, kb, rows_per_cta, dt.as<double>(),
-                                                 flag);
-    RBF_CUDA(cudaGetLastError());
-    k_copy_tile<<<1, 256, 0, s>>>(A, lda, k, kb, dt.as<double>());
-    RBF_CUDA(cudaGetLastError());
+    {
+      StageTimer st(c, RBF_STAGE_PANEL, s, (double)kb * kb * kb / 3.0 + (double)rows * kb * kb);
+      { k_potrf_panel<<<(unsigned)ctas, 256, 0, s>>>(A, lda, n, k, kb, rows_per_cta, dt.as<double>(),
+                                                   flag); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      { k_copy_tile<<<1, 256, 0, s>>>(A, lda, k, kb, dt.as<double>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    }
     if (rows > 0) {
+      StageTimer st(c, RBF_STAGE_TRAILING, s, (double)rows * (double)(rows + 1) * kb);
       int64_t T = (rows + ST - 1) / ST;
       int64_t tiles = T * (T + 1) / 2;
-      k_syrk_trailing<<<(unsigned)tiles, 256, 0, s>>>(A, lda, n, k, kb);
+      { k_syrk_trailing<<<(unsigned)tiles, 256, 0, s>>>(A, lda, n, k, kb); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
   }
@@ -197,31 +204,43 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // Solves op(L) X = B in place for columns [c0, c0 + mc) of B.
 // transpose = false: forward (block rows in order 0..nblk-1)
 // transpose = true : backward with L^T (block rows nblk-1..0)
+// Thread (i, g) = (tid >> 3, tid & 7) owns row i of the block and the
+// coefficient slice [4g, 4g + 4) of every dependency; the slice is loaded
+// before the wait so that its latency overlaps the producer's work.
 __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __restrict__ L, int64_t ldl,
                                                               int64_t n, double* B, int64_t ldb,
                                                               int c0, int mc, bool transpose,
                                                               int* flags, int epoch, int* status) {
-  __shared__ double Lt[NB][NB + 1];
-  __shared__ double Xs[NB][TS_MC + 1];
   __shared__ double acc[NB][TS_MC + 1];
+  __shared__ double Dg[NB][NB + 1];
+  __shared__ double inv_d[NB];
   __shared__ int bail;
+  const int tid = threadIdx.x, ti = tid >> 3, tg = tid & 7;
   int64_t nblk = (n + NB - 1) / NB;
   for (int64_t lk = blockIdx.x; lk < nblk; lk += gridDim.x) {
     int64_t r = transpose ? (nblk - 1 - lk) : lk;
     int64_t r0 = r * NB;
     int rb = (int)((n - r0) < NB ? (n - r0) : NB);
-    for (int e = threadIdx.x; e < NB * TS_MC; e += blockDim.x) {
+    for (int e = tid; e < NB * TS_MC; e += blockDim.x) {
       int i = e / TS_MC, j = e % TS_MC;
       acc[i][j] = (i < rb && j < mc) ? B[(r0 + i) * ldb + c0 + j] : 0.0;
     }
-    if (threadIdx.x == 0) bail = 0;
+    if (tid == 0) bail = 0;
     __syncthreads();
-    // consume every solved block this row depends on, in order
     for (int64_t lc = 0; lc < lk; ++lc) {
       int64_t cb = transpose ? (nblk - 1 - lc) : lc;
       int64_t cc0 = cb * NB;
       int cbs = (int)((n - cc0) < NB ? (n - cc0) : NB);
-      if (threadIdx.x == 0) {
+      double lv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int t = 4 * tg + u;
+        double v = 0.0;
+        if (ti < rb && t < cbs)
+          v = transpose ? L[(cc0 + t) * ldl + r0 + ti] : L[(r0 + ti) * ldl + cc0 + t];
+        lv[u] = v;
+      }
+      if (tid == 0) {
         long long it = 0;
         while (ld_acquire(flags + cb) != epoch) {
           if (++it > TS_SPIN_LIMIT) {
@@ -229,63 +248,55 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __re
             bail = 1;
             break;
           }
-          __nanosleep(64);
+          __nanosleep(20);
         }
       }
       __syncthreads();
       if (bail) break;
-      // coefficient block: forward L[r, cb]; backward L^T[r, cb] = L[cb, r]^T
-      for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        double v = 0.0;
-        if (i < rb && j < cbs)
-          v = transpose ? L[(cc0 + j) * ldl + r0 + i] : L[(r0 + i) * ldl + cc0 + j];
-        Lt[i][j] = v;
+      for (int j = 0; j < mc; ++j) {
+        double pp = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int t = 4 * tg + u;
+          if (t < cbs) pp = fma(lv[u], __ldcg(B + (cc0 + t) * ldb + c0 + j), pp);
+        }
+        pp += __shfl_xor_sync(0xffffffffu, pp, 1);
+        pp += __shfl_xor_sync(0xffffffffu, pp, 2);
+        pp += __shfl_xor_sync(0xffffffffu, pp, 4);
+        if (tg == 0 && ti < rb) acc[ti][j] -= pp;
       }
-      for (int e = threadIdx.x; e < NB * TS_MC; e += blockDim.x) {
-        int i = e / TS_MC, j = e % TS_MC;
-        Xs[i][j] = (i < cbs && j < mc) ? __ldcg(B + (cc0 + i) * ldb + c0 + j) : 0.0;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < NB * TS_MC; e += blockDim.x) {
-        int i = e / TS_MC, j = e % TS_MC;
-        double sacc = 0.0;
-#pragma unroll 8
-        for (int t = 0; t < NB; ++t) sacc = fma(Lt[i][t], Xs[t][j], sacc);
-        acc[i][j] -= sacc;
-      }
-      __syncthreads();
     }
-    // diagonal block: forward substitution with L_rr, or backward with L_rr^T
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    // diagonal block of op(L)
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
       int i = e / NB, j = e % NB;
       double v = 0.0;
       if (i < rb && j < rb) v = transpose ? L[(r0 + j) * ldl + r0 + i] : L[(r0 + i) * ldl + r0 + j];
-      Lt[i][j] = v;  // op(L)_rr[i][j]
+      Dg[i][j] = v;
     }
     __syncthreads();
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (tid < NB) inv_d[tid] = tid < rb ? 1.0 / Dg[tid][tid] : 0.0;
+    __syncthreads();
+    int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     for (int j = wid; j < mc; j += nw) {
-      // lane i holds acc[i][j]
       double b = lane < rb ? acc[lane][j] : 0.0;
       if (!transpose) {
         for (int t = 0; t < rb; ++t) {
-          double xt = __shfl_sync(0xffffffffu, b, t) / Lt[t][t];
+          double xt = __shfl_sync(0xffffffffu, b, t) * inv_d[t];
           if (lane == t) b = xt;
-          else if (lane > t) b -= Lt[lane][t] * xt;
+          else if (lane > t) b -= Dg[lane][t] * xt;
         }
       } else {
         for (int t = rb - 1; t >= 0; --t) {
-          double xt = __shfl_sync(0xffffffffu, b, t) / Lt[t][t];
+          double xt = __shfl_sync(0xffffffffu, b, t) * inv_d[t];
           if (lane == t) b = xt;
-          else if (lane < t) b -= Lt[lane][t] * xt;
+          else if (lane < t) b -= Dg[lane][t] * xt;
         }
       }
       if (lane < rb) B[(r0 + lane) * ldb + c0 + j] = b;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release(flags + r, epoch);
+    if (tid == 0) st_release(flags + r, epoch);
   }
 }
 
@@ -316,7 +327,7 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
     int c0i = (int)c0;
     void* args[] = {(void*)&L, (void*)&ldl, (void*)&n, (void*)&B, (void*)&ldb, (void*)&c0i,
                     (void*)&mc, (void*)&transpose, (void*)&flags, (void*)&epoch, (void*)&status};
-    RBF_CUDA(cudaLaunchCooperativeKernel((const void*)k_trsm_syncfree, dim3((unsigned)grid),
+    RBF_CUDA(cooperative_launch((const void*)k_trsm_syncfree, dim3((unsigned)grid),
                                          dim3(TS_THREADS), args, 0, s));
   }
   return RBF_OK;
@@ -367,12 +378,60 @@ __global__ void __launch_bounds__(256) k_gemm_f64(bool ta, bool tb, int64_t m, i
   }
 }
 
-rbf_status gemm_f64(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+// Partial products over a slice of k (split-K) for small outputs with long k.
+__global__ void __launch_bounds__(256) k_gemm_splitk(bool ta, bool tb, int64_t m, int64_t n, int64_t k,
+                                                     int64_t kchunk, const double* __restrict__ A,
+                                                     int64_t lda, const double* __restrict__ B,
+                                                     int64_t ldb, double* __restrict__ part) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  int64_t i = e / n, j = e % n;
+  int64_t k0 = (int64_t)blockIdx.y * kchunk, k1 = k0 + kchunk < k ? k0 + kchunk : k;
+  double acc = 0.0;
+  for (int64_t t = k0; t < k1; ++t) {
+    double a = ta ? A[t * lda + i] : A[i * lda + t];
+    double b = tb ? B[j * ldb + t] : B[t * ldb + j];
+    acc = fma(a, b, acc);
+  }
+  part[(int64_t)blockIdx.y * m * n + e] = acc;
+}
+
+__global__ void k_gemm_reduce(int64_t m, int64_t n, int nsplit, const double* __restrict__ part, double alpha,
+                              double beta, double* __restrict__ Cm, int64_t ldc) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  double acc = 0.0;
+  for (int q = 0; q < nsplit; ++q) acc += part[(int64_t)q * m * n + e];
+  int64_t i = e / n, j = e % n;
+  double prev = beta != 0.0 ? Cm[i * ldc + j] : 0.0;
+  Cm[i * ldc + j] = alpha * acc + beta * prev;
+}
+
+rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
                     int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc,
                     cudaStream_t s) {
   if (m <= 0 || n <= 0) return RBF_OK;
+  int64_t tiles = ((m + GT - 1) / GT) * ((n + GT - 1) / GT);
+  if (tiles < 64 && k > 512) {
+    int64_t kchunk = 64;
+    int64_t nsplit = (k + kchunk - 1) / kchunk;
+    if (nsplit > 4096) {
+      nsplit = 4096;
+      kchunk = (k + nsplit - 1) / nsplit;
+      nsplit = (k + kchunk - 1) / kchunk;
+    }
+    Buf& part = c->scratch(28);
+    RBF_TRY(part.ensure((size_t)nsplit * m * n * sizeof(double)));
+    dim3 grid((unsigned)((m * n + 255) / 256), (unsigned)nsplit);
+    { k_gemm_splitk<<<grid, 256, 0, s>>>(ta, tb, m, n, k, kchunk, A, lda, B, ldb, part.as<double>()); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    { k_gemm_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, s>>>(m, n, (int)nsplit, part.as<double>(), alpha,
+                                                                 beta, Cm, ldc); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    return RBF_OK;
+  }
   dim3 grid((unsigned)((n + GT - 1) / GT), (unsigned)((m + GT - 1) / GT));
-  k_gemm_f64<<<grid, 256, 0, s>>>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc);
+  { k_gemm_f64<<<grid, 256, 0, s>>>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
@@ -395,7 +454,7 @@ __global__ void __launch_bounds__(256) k_symv_residual(const double* __restrict_
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x, const double* b,
                          double* r, cudaStream_t s) {
   if (n <= 0) return RBF_OK;
-  k_symv_residual<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(H, n, ld, x, b, r);
+  { k_symv_residual<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(H, n, ld, x, b, r); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }

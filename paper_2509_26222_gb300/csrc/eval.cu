@@ -255,15 +255,15 @@ static rbf_status soft_cost_forward(Ctx* x, const Pose& T, const float* pts, int
   Buf& part = x->scratch(20);
   RBF_TRY(part.ensure((size_t)nb * 8 * sizeof(double)));
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
-    k_soft_cost<RBF_KERNEL_WENDLAND><<<nb, SC_THREADS, 0, s>>>(
+    { k_soft_cost<RBF_KERNEL_WENDLAND><<<nb, SC_THREADS, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid,
-        part.as<double>());
+        part.as<double>()); ::rbf::note_launch(); }
   else
-    k_soft_cost<RBF_KERNEL_GAUSSIAN><<<nb, SC_THREADS, 0, s>>>(
+    { k_soft_cost<RBF_KERNEL_GAUSSIAN><<<nb, SC_THREADS, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid,
-        part.as<double>());
+        part.as<double>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  k_reduce_partials<<<1, 32, 0, s>>>(part.as<double>(), (int)nb, gout, cost, grad6);
+  { k_reduce_partials<<<1, 32, 0, s>>>(part.as<double>(), (int)nb, gout, cost, grad6); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
@@ -392,14 +392,15 @@ extern "C" rbf_status rbf_eval(rbf_ctx* c, const float* q, int64_t Q, float* h, 
   cudaStream_t s = (cudaStream_t)stream;
   EvalParams P = make_eval_params(x);
   unsigned nb = grid_for(Q, 256, x->device, 8);
+  StageTimer st(x, RBF_STAGE_EVAL, s, 20.0 * (double)Q);
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
-    k_eval<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
+    { k_eval<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
                                                    x->sorted_xyw.as<float4>(), (const float2*)q, Q,
-                                                   h, (float2*)grad);
+                                                   h, (float2*)grad); ::rbf::note_launch(); }
   else
-    k_eval<RBF_KERNEL_GAUSSIAN><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
+    { k_eval<RBF_KERNEL_GAUSSIAN><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
                                                    x->sorted_xyw.as<float4>(), (const float2*)q, Q,
-                                                   h, (float2*)grad);
+                                                   h, (float2*)grad); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
@@ -420,6 +421,7 @@ extern "C" rbf_status rbf_soft_cost(rbf_ctx* c, const double* R, const double* t
     if (grad6) RBF_CUDA(cudaMemsetAsync(grad6, 0, 6 * sizeof(double), s));
     return RBF_OK;
   }
+  StageTimer st(x, RBF_STAGE_SOFTCOST, s, 12.0 * (double)n);
   return soft_cost_forward(x, T, pts, n, nullptr, cost, grad6, resid, s);
 }
 
@@ -441,6 +443,7 @@ extern "C" rbf_status rbf_soft_cost_backward(rbf_ctx* c, const double* R, const 
     if (dpose6) RBF_CUDA(cudaMemsetAsync(dpose6, 0, 6 * sizeof(double), s));
     return RBF_OK;
   }
+  StageTimer st(x, RBF_STAGE_BACKWARD, s, 24.0 * (double)n);
   if (dpose6) RBF_TRY(soft_cost_forward(x, T, pts, n, gout, nullptr, dpose6, nullptr, s));
   if (!dw && !dc) return RBF_OK;
   EvalParams P = make_eval_params(x);
@@ -460,31 +463,31 @@ extern "C" rbf_status rbf_soft_cost_backward(rbf_ctx* c, const double* R, const 
   RBF_CUDA(cudaMemsetAsync(pcount.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
   unsigned nb = (unsigned)((n + 255) / 256);
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
-    k_bwd_points<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(
+    { k_bwd_points<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, gout,
-        qpsi.as<float4>(), pcell.as<int32_t>(), pcount.as<int32_t>());
+        qpsi.as<float4>(), pcell.as<int32_t>(), pcount.as<int32_t>()); ::rbf::note_launch(); }
   else
-    k_bwd_points<RBF_KERNEL_GAUSSIAN><<<nb, 256, 0, s>>>(
+    { k_bwd_points<RBF_KERNEL_GAUSSIAN><<<nb, 256, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, gout,
-        qpsi.as<float4>(), pcell.as<int32_t>(), pcount.as<int32_t>());
+        qpsi.as<float4>(), pcell.as<int32_t>(), pcount.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(x, pcount.as<int32_t>(), pstart.as<int32_t>(), ncell, s, 48));
   RBF_CUDA(cudaMemsetAsync(pcount.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
-  k_bwd_fill<<<nb, 256, 0, s>>>(pcell.as<int32_t>(), n, pstart.as<int32_t>(), pcount.as<int32_t>(),
-                                order.as<int32_t>());
+  { k_bwd_fill<<<nb, 256, 0, s>>>(pcell.as<int32_t>(), n, pstart.as<int32_t>(), pcount.as<int32_t>(),
+                                order.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  k_bwd_sort<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(pstart.as<int32_t>(), ncell,
-                                                             order.as<int32_t>());
+  { k_bwd_sort<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(pstart.as<int32_t>(), ncell,
+                                                             order.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   unsigned nbc = (unsigned)((M + 255) / 256);
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
-    k_bwd_centers<RBF_KERNEL_WENDLAND><<<nbc, 256, 0, s>>>(
+    { k_bwd_centers<RBF_KERNEL_WENDLAND><<<nbc, 256, 0, s>>>(
         P, x->sorted_xyw.as<float4>(), x->sorted_id.as<int32_t>(), M, pstart.as<int32_t>(),
-        order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc);
+        order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc); ::rbf::note_launch(); }
   else
-    k_bwd_centers<RBF_KERNEL_GAUSSIAN><<<nbc, 256, 0, s>>>(
+    { k_bwd_centers<RBF_KERNEL_GAUSSIAN><<<nbc, 256, 0, s>>>(
         P, x->sorted_xyw.as<float4>(), x->sorted_id.as<int32_t>(), M, pstart.as<int32_t>(),
-        order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc);
+        order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }

@@ -110,8 +110,8 @@ rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, doubl
   RBF_TRY(cnt.ensure((size_t)(n + 1) * sizeof(int32_t)));
   RBF_TRY(row_ptr.ensure((size_t)(n + 1) * sizeof(int64_t)));
   unsigned nb = (unsigned)((n + 255) / 256);
-  k_nbr_count<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(), pts,
-                                 stride, n, cnt.as<int32_t>(), c->dflag.as<int>());
+  { k_nbr_count<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(), pts,
+                                 stride, n, cnt.as<int32_t>(), c->dflag.as<int>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32_to_i64(c, cnt.as<int32_t>(), row_ptr.as<int64_t>(), n, s, 48));
   RBF_CUDA(cudaMemcpyAsync(c->host_small, row_ptr.as<int64_t>() + n, sizeof(int64_t),
@@ -122,9 +122,9 @@ rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, doubl
   *nnz = c->host_small[0];
   RBF_TRY(col.ensure((size_t)(*nnz > 0 ? *nnz : 1) * sizeof(int32_t)));
   if (*nnz > 0) {
-    k_nbr_fill<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(),
+    { k_nbr_fill<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(),
                                   c->sorted_id.as<int32_t>(), pts, stride, n, row_ptr.as<int64_t>(),
-                                  col.as<int32_t>());
+                                  col.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   return RBF_OK;
@@ -212,43 +212,82 @@ __global__ void k_tfill(const int64_t* __restrict__ row_ptr, int64_t n, const in
   for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
     int l = lcol[k];
     int64_t p = tstart[l] + atomicAdd(&tfill[l], 1);
-    tk[p] = k;  // entries of one point are in ascending k; points sort by k too
+    tk[p] = k;  // position in the point-major list: ascending k = ascending point
   }
 }
 
-// order each center's entries by their position k in the point-major list
-// (= by point index, then by center): makes every later sum deterministic
-__global__ void k_tsort(const int64_t* __restrict__ tstart, int64_t a, int64_t* __restrict__ tk) {
-  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= a) return;
-  int64_t lo = tstart[l], hi = tstart[l + 1];
-  for (int64_t u = lo + 1; u < hi; ++u) {
-    int64_t v = tk[u];
-    int64_t k = u - 1;
-    while (k >= lo && tk[k] > v) {
-      tk[k + 1] = tk[k];
-      --k;
-    }
-    tk[k + 1] = v;
-  }
-}
-
-// point index of nnz position k (binary search in row_ptr)
-__device__ __forceinline__ int64_t owner_of(const int64_t* __restrict__ row_ptr, int64_t n, int64_t k) {
-  int64_t lo = 0, hi = n;  // row_ptr[lo] <= k < row_ptr[hi]
+// point index of every center-major entry (after sorting)
+__global__ void k_towner(const int64_t* __restrict__ tk, int64_t nnz, const int64_t* __restrict__ row_ptr,
+                         int64_t n, int32_t* __restrict__ tpt) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  int64_t k = tk[p];
+  int64_t lo = 0, hi = n;  // largest lo with row_ptr[lo] <= k
   while (hi - lo > 1) {
     int64_t mid = (lo + hi) >> 1;
     if (row_ptr[mid] <= k) lo = mid;
     else hi = mid;
   }
-  return lo;
+  tpt[p] = (int32_t)lo;
+}
+
+// order each center's entries by their position k in the point-major list
+// (= by point index): makes every later sum deterministic.  One CTA per
+// center, bitonic sort in shared memory; lists longer than the shared buffer
+// (very dense frames) fall back to an insertion sort by one thread.
+constexpr int TSORT_CAP = 2048;
+__global__ void __launch_bounds__(256) k_tsort(const int64_t* __restrict__ tstart, int64_t a,
+                                               int64_t* __restrict__ tk) {
+  __shared__ int64_t key[TSORT_CAP];
+  int64_t l = blockIdx.x;
+  if (l >= a) return;
+  int64_t lo = tstart[l], hi = tstart[l + 1];
+  int64_t len = hi - lo;
+  if (len <= 1) return;
+  if (len > TSORT_CAP) {
+    if (threadIdx.x == 0) {
+      for (int64_t u = lo + 1; u < hi; ++u) {
+        int64_t v = tk[u];
+        int64_t k = u - 1;
+        while (k >= lo && tk[k] > v) {
+          tk[k + 1] = tk[k];
+          --k;
+        }
+        tk[k + 1] = v;
+      }
+    }
+    return;
+  }
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) key[i] = i < len ? tk[lo + i] : INT64_MAX;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          bool up = (i & k) == 0;
+          int64_t x = key[i], y = key[ixj];
+          if ((x > y) == up) {
+            key[i] = y;
+            key[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += blockDim.x) tk[lo + i] = key[i];
 }
 
 // One warp per active row l1: H'[l1, :] += sum_i m_{i,l1} m_{i,:} (row of
 // m~ m~^T, accumulated in shared memory in ascending point order) and
-// u[l1] = sum_i m_{i,l1} e_i.
+// u[l1] = sum_i m_{i,l1} e_i.  The metadata of 32 entries is fetched by the
+// 32 lanes at once, then the entries are applied one after the other.
 __global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const int64_t* __restrict__ tstart,
                                                    const int64_t* __restrict__ tk,
+                                                   const int32_t* __restrict__ tpt,
                                                    const int64_t* __restrict__ row_ptr, int64_t n,
                                                    const double* __restrict__ val,
                                                    const int32_t* __restrict__ lcol,
@@ -261,15 +300,32 @@ __global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const
     for (int64_t j = lane; j < a; j += 32) row[j] = 0.0;
     __syncwarp();
     double ue = 0.0;
-    for (int64_t p = tstart[l1]; p < tstart[l1 + 1]; ++p) {
-      int64_t k1 = tk[p];
-      int64_t i = owner_of(row_ptr, n, k1);
-      double m1 = val[k1];
-      ue = fma(m1, e[i], ue);
-      int64_t ra = row_ptr[i], rb = row_ptr[i + 1];
-      for (int64_t k2 = ra + lane; k2 < rb; k2 += 32) row[lcol[k2]] = fma(m1, val[k2], row[lcol[k2]]);
-      __syncwarp();
+    int64_t p0 = tstart[l1], p1 = tstart[l1 + 1];
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+      int cnt = (int)((p1 - pb) < 32 ? (p1 - pb) : 32);
+      double m1 = 0.0;
+      int64_t ra = 0, rb = 0;
+      if (lane < cnt) {
+        int64_t k1 = tk[pb + lane];
+        int64_t i = tpt[pb + lane];
+        m1 = val[k1];
+        ue = fma(m1, e[i], ue);
+        ra = row_ptr[i];
+        rb = row_ptr[i + 1];
+      }
+      for (int q = 0; q < cnt; ++q) {
+        double mq = __shfl_sync(0xffffffffu, m1, q);
+        int64_t qa = __shfl_sync(0xffffffffu, ra, q);
+        int64_t qb = __shfl_sync(0xffffffffu, rb, q);
+        for (int64_t k2 = qa + lane; k2 < qb; k2 += 32) {
+          int l2 = lcol[k2];
+          row[l2] = fma(mq, val[k2], row[l2]);
+        }
+        __syncwarp();
+      }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ue += __shfl_xor_sync(0xffffffffu, ue, o);
     double* Hr = H + l1 * ldh;
     for (int64_t j = lane; j < a; j += 32) Hr[j] += row[j];
     if (lane == 0) u[l1] = ue;
@@ -404,7 +460,7 @@ static rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a
     RBF_TRY(symv_residual(H, a, ld, xb.as<double>(), bb.as<double>(), rb.as<double>(), s));
     RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, false, s));
     RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, true, s));
-    k_axpy<<<nblk(a), 256, 0, s>>>(xb.as<double>(), rb.as<double>(), a);
+    { k_axpy<<<nblk(a), 256, 0, s>>>(xb.as<double>(), rb.as<double>(), a); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   RBF_CUDA(cudaMemcpyAsync(b, xb.p, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -416,10 +472,10 @@ static rbf_status spd_inverse(Ctx* c, double* G, int64_t m, cudaStream_t s, int 
   Buf& Zb = c->scratch(slot);
   RBF_TRY(Zb.ensure((size_t)m * m * sizeof(double)));
   RBF_TRY(potrf_lower(c, G, m, m, m, false, s));
-  k_identity<<<nblk(m * m), 256, 0, s>>>(Zb.as<double>(), m);
+  { k_identity<<<nblk(m * m), 256, 0, s>>>(Zb.as<double>(), m); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(trsm_lower(c, G, m, m, Zb.as<double>(), m, m, false, s));
-  RBF_TRY(gemm_f64(true, false, m, m, m, 1.0, Zb.as<double>(), m, Zb.as<double>(), m, 0.0, G, m, s));
+  RBF_TRY(gemm_f64(c, true, false, m, m, m, 1.0, Zb.as<double>(), m, Zb.as<double>(), m, 0.0, G, m, s));
   return RBF_OK;
 }
 
@@ -442,7 +498,10 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   Buf& row_ptr = c->scratch(0);
   Buf& col = c->scratch(1);
   int64_t nnz = 0;
-  RBF_TRY(neighbor_lists(c, pts, n, 3, assembly_radius(c->cfg, noise), row_ptr, col, &nnz, s));
+  {
+    StageTimer st(c, RBF_STAGE_NEIGHBORS, s, 12.0 * (double)n);
+    RBF_TRY(neighbor_lists(c, pts, n, 3, assembly_radius(c->cfg, noise), row_ptr, col, &nnz, s));
+  }
   if (nnz == 0) return RBF_OK;
 
   // 2. active set
@@ -455,11 +514,11 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_TRY(An.ensure((size_t)M * sizeof(int32_t)));
   RBF_TRY(g2ln.ensure((size_t)M * sizeof(int32_t)));
   RBF_CUDA(cudaMemsetAsync(mark.p, 0, (size_t)M * sizeof(int32_t), s));
-  k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>());
+  { k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(c, mark.as<int32_t>(), pos.as<int32_t>(), M, s, 48));
-  k_compact<<<nblk(M), 256, 0, s>>>(mark.as<int32_t>(), pos.as<int32_t>(), M, An.as<int32_t>(),
-                                    g2ln.as<int32_t>());
+  { k_compact<<<nblk(M), 256, 0, s>>>(mark.as<int32_t>(), pos.as<int32_t>(), M, An.as<int32_t>(),
+                                    g2ln.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
 
   // 3. relation to the previous block: S (stay), D (leave), E (enter)
@@ -495,9 +554,9 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   if (an == 0) return RBF_OK;
   int64_t d = 0, sN = 0, e = an;
   if (ap > 0) {
-    k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 0, flD);
-    k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 1, flS);
-    k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 0, flE);
+    { k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 0, flD); ::rbf::note_launch(); }
+    { k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 1, flS); ::rbf::note_launch(); }
+    { k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 0, flE); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     RBF_TRY(scan_i32(c, flD, fpD, ap, s, 48));
     RBF_TRY(scan_i32(c, flS, fpS, ap, s, 48));
@@ -505,14 +564,14 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     // staying centers in new-local positions: flag = member of the previous block
     Buf& flSn = c->scratch(14);
     RBF_TRY(flSn.ensure((size_t)(an + 1) * sizeof(int32_t)));
-    k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 1,
-                                           flSn.as<int32_t>());
+    { k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 1,
+                                           flSn.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     RBF_TRY(scan_i32(c, flSn.as<int32_t>(), fpSn, an, s, 48));
-    k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flD, fpD, ap, Dl.as<int32_t>());
-    k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flS, fpS, ap, Sl.as<int32_t>());
-    k_list_from_flags<<<nblk(an), 256, 0, s>>>(flE, fpE, an, El.as<int32_t>());
-    k_list_from_flags<<<nblk(an), 256, 0, s>>>(flSn.as<int32_t>(), fpSn, an, Sn.as<int32_t>());
+    { k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flD, fpD, ap, Dl.as<int32_t>()); ::rbf::note_launch(); }
+    { k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flS, fpS, ap, Sl.as<int32_t>()); ::rbf::note_launch(); }
+    { k_list_from_flags<<<nblk(an), 256, 0, s>>>(flE, fpE, an, El.as<int32_t>()); ::rbf::note_launch(); }
+    { k_list_from_flags<<<nblk(an), 256, 0, s>>>(flSn.as<int32_t>(), fpSn, an, Sn.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     int32_t* h32 = (int32_t*)hs;
     RBF_CUDA(cudaMemcpyAsync(h32 + 0, fpD + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -536,6 +595,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   }
 
   // 4. m~ entries, innovation, center-major lists
+  StageTimer* st_asm = new StageTimer(c, RBF_STAGE_ASSEMBLY, s, 0.0);
   Buf& val = c->scratch(15);
   Buf& lcol = c->scratch(16);
   Buf& ev = c->scratch(17);
@@ -549,22 +609,28 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_TRY(tstart.ensure((size_t)(an + 1) * sizeof(int64_t)));
   RBF_TRY(tk.ensure((size_t)nnz * sizeof(int64_t)));
   RowParams RP = row_params(c->cfg, noise);
-  k_rowvals<<<nblk(n), 256, 0, s>>>(RP, pts, n, row_ptr.as<int64_t>(), col.as<int32_t>(),
+  { k_rowvals<<<nblk(n), 256, 0, s>>>(RP, pts, n, row_ptr.as<int64_t>(), col.as<int32_t>(),
                                     c->c64.as<double>(), c->w.as<double>(), g2ln.as<int32_t>(),
-                                    val.as<double>(), lcol.as<int32_t>(), ev.as<double>());
+                                    val.as<double>(), lcol.as<int32_t>(), ev.as<double>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
-  k_tcount<<<nblk(nnz), 256, 0, s>>>(lcol.as<int32_t>(), nnz, tcnt.as<int32_t>());
+  { k_tcount<<<nblk(nnz), 256, 0, s>>>(lcol.as<int32_t>(), nnz, tcnt.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32_to_i64(c, tcnt.as<int32_t>(), tstart.as<int64_t>(), an, s, 48));
   RBF_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
-  k_tfill<<<nblk(n), 256, 0, s>>>(row_ptr.as<int64_t>(), n, lcol.as<int32_t>(), tstart.as<int64_t>(),
-                                  tcnt.as<int32_t>(), tk.as<int64_t>());
+  { k_tfill<<<nblk(n), 256, 0, s>>>(row_ptr.as<int64_t>(), n, lcol.as<int32_t>(), tstart.as<int64_t>(),
+                                  tcnt.as<int32_t>(), tk.as<int64_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  k_tsort<<<nblk(an), 256, 0, s>>>(tstart.as<int64_t>(), an, tk.as<int64_t>());
+  { k_tsort<<<(unsigned)an, 256, 0, s>>>(tstart.as<int64_t>(), an, tk.as<int64_t>()); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  Buf& tpt = c->scratch(29);
+  RBF_TRY(tpt.ensure((size_t)nnz * sizeof(int32_t)));
+  { k_towner<<<nblk(nnz), 256, 0, s>>>(tk.as<int64_t>(), nnz, row_ptr.as<int64_t>(), n, tpt.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
 
+  delete st_asm;
   // 5. leaving centers: their covariance block and the Schur complement
+  StageTimer* st_blk = new StageTimer(c, RBF_STAGE_BLOCK, s, 0.0);
   const int64_t ld = an;
   Buf& Hn = c->scratch(35);
   Buf& Ln = c->scratch(36);
@@ -579,10 +645,10 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     Buf& Y = c->scratch(39);
     RBF_TRY(Y.ensure((size_t)ap * d * sizeof(double)));
     RBF_TRY(Pdd.ensure((size_t)d * d * sizeof(double)));
-    k_unit_rhs<<<nblk(ap * d), 256, 0, s>>>(Y.as<double>(), ap, d, Dl.as<int32_t>());
+    { k_unit_rhs<<<nblk(ap * d), 256, 0, s>>>(Y.as<double>(), ap, d, Dl.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s));
-    RBF_TRY(gemm_f64(true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
+    RBF_TRY(gemm_f64(c, true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
                      Pdd.as<double>(), d, s));
     if (sN > 0) {
       // T = H_prev permuted to [D; S]; d steps of Cholesky leave H_S in T[d:, d:]
@@ -593,46 +659,48 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       RBF_CUDA(cudaMemcpyAsync(perm.p, Dl.p, (size_t)d * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
       RBF_CUDA(cudaMemcpyAsync(perm.as<int32_t>() + d, Sl.p, (size_t)sN * sizeof(int32_t),
                                cudaMemcpyDeviceToDevice, s));
-      k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), ap,
-                                                 T.as<double>(), ap);
+      { k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), ap,
+                                                 T.as<double>(), ap); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
       RBF_TRY(potrf_lower(c, T.as<double>(), ap, ap, d, false, s));
-      k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>() + d * ap + d, ap, sN, Sn.as<int32_t>(),
-                                                  Hn.as<double>(), ld);
+      { k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>() + d * ap + d, ap, sN, Sn.as<int32_t>(),
+                                                  Hn.as<double>(), ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
   } else if (sN > 0) {
     // nobody leaves: the staying block is the previous information matrix
     Buf& T = c->scratch(41);
     RBF_TRY(T.ensure((size_t)ap * ap * sizeof(double)));
-    k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), sN,
-                                               T.as<double>(), sN);
+    { k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), sN,
+                                               T.as<double>(), sN); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>(), sN, sN, Sn.as<int32_t>(), Hn.as<double>(),
-                                                ld);
+    { k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>(), sN, sN, Sn.as<int32_t>(), Hn.as<double>(),
+                                                ld); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
 
   // 6. entering centers: inverse of their stored covariance block
   if (e > 0) {
     if (!c->pg_on) {
-      k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld);
+      { k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {
       Buf& Gb = c->scratch(42);
       RBF_TRY(Gb.ensure((size_t)e * e * sizeof(double)));
-      k_gather_global<<<nblk(e * e), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
-                                                   El.as<int32_t>(), e, Gb.as<double>());
+      { k_gather_global<<<nblk(e * e), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
+                                                   El.as<int32_t>(), e, Gb.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
       RBF_TRY(spd_inverse(c, Gb.as<double>(), e, s, 43));
-      k_scatter_sym<<<nblk(e * e), 256, 0, s>>>(Gb.as<double>(), e, e, El.as<int32_t>(), Hn.as<double>(),
-                                                ld);
+      { k_scatter_sym<<<nblk(e * e), 256, 0, s>>>(Gb.as<double>(), e, e, El.as<int32_t>(), Hn.as<double>(),
+                                                ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
   }
 
+  delete st_blk;
   // 7. + m~ m~^T and u = m~ e
   {
+    StageTimer st(c, RBF_STAGE_ASSEMBLY, s, 0.0);
     int dev_smem = 0;
     RBF_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     int64_t per_warp = an * (int64_t)sizeof(double);
@@ -642,10 +710,10 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     size_t smem = (size_t)warps * per_warp;
     RBF_CUDA(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned g = nblk(an, warps);
-    k_gram_rows<<<g, warps * 32, smem, s>>>(an, ld, tstart.as<int64_t>(), tk.as<int64_t>(),
-                                             row_ptr.as<int64_t>(), n, val.as<double>(),
+    { k_gram_rows<<<g, warps * 32, smem, s>>>(an, ld, tstart.as<int64_t>(), tk.as<int64_t>(),
+                                             tpt.as<int32_t>(), row_ptr.as<int64_t>(), n, val.as<double>(),
                                              lcol.as<int32_t>(), ev.as<double>(), Hn.as<double>(),
-                                             u.as<double>());
+                                             u.as<double>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
 
@@ -655,25 +723,28 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   int flag = 0;
   RBF_TRY(read_dev_flag(c, s, &flag));
   if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
-  RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), mixed, s));
+  {
+    StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 14.0 : 2.0) * (double)an * an);
+    RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), mixed, s));
+  }
   RBF_TRY(read_dev_flag(c, s, &flag));
   if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
 
   // 9. commit
-  k_w_add<<<nblk(an), 256, 0, s>>>(c->w.as<double>(), An.as<int32_t>(), an, u.as<double>());
+  { k_w_add<<<nblk(an), 256, 0, s>>>(c->w.as<double>(), An.as<int32_t>(), an, u.as<double>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   if (d > 0) {
     if (!c->pg_on) {
       RBF_TRY(c->Pg.ensure((size_t)M * M * sizeof(double)));
       RBF_CUDA(cudaMemsetAsync(c->Pg.p, 0, (size_t)M * M * sizeof(double), s));
-      k_pg_init<<<nblk(M), 256, 0, s>>>(c->Pg.as<double>(), M, 1.0 / c->cfg.lambda);
+      { k_pg_init<<<nblk(M), 256, 0, s>>>(c->Pg.as<double>(), M, 1.0 / c->cfg.lambda); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
       c->pg_on = true;
     }
-    k_pg_zero<<<nblk(d * M), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d);
+    { k_pg_zero<<<nblk(d * M), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    k_pg_block<<<nblk(d * d), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d,
-                                           Pdd.as<double>());
+    { k_pg_block<<<nblk(d * d), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d,
+                                           Pdd.as<double>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   std::swap(c->H, Hn);
@@ -789,16 +860,16 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
     RBF_TRY(Y.ensure((size_t)c->a * ka * sizeof(double)));
     RBF_TRY(Paa.ensure((size_t)ka * ka * sizeof(double)));
     RBF_CUDA(cudaMemcpyAsync(lb.p, lpos.data(), (size_t)ka * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    k_unit_rhs<<<nblk(c->a * ka), 256, 0, s>>>(Y.as<double>(), c->a, ka, lb.as<int32_t>());
+    { k_unit_rhs<<<nblk(c->a * ka), 256, 0, s>>>(Y.as<double>(), c->a, ka, lb.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s));
-    RBF_TRY(gemm_f64(true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,
+    RBF_TRY(gemm_f64(c, true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,
                      Paa.as<double>(), ka, s));
   }
-  k_cov_assemble<<<nblk(k * k), 256, 0, s>>>(k, ib.as<int32_t>(), c->g2l.as<int32_t>(), rb.as<int32_t>(),
+  { k_cov_assemble<<<nblk(k * k), 256, 0, s>>>(k, ib.as<int32_t>(), c->g2l.as<int32_t>(), rb.as<int32_t>(),
                                              ka > 0 ? Paa.as<double>() : nullptr, ka,
                                              c->pg_on ? c->Pg.as<double>() : nullptr, c->M, c->pg_on ? 1 : 0,
-                                             1.0 / c->cfg.lambda, Pk);
+                                             1.0 / c->cfg.lambda, Pk); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_CUDA(cudaStreamSynchronize(s));
   int flag = 0;

@@ -72,7 +72,19 @@ _SIGS = {
     "rbf_get_cov": [_P, _P, _I64, _P, _P],
     "rbf_get_active": [_P, _P, _I64, ctypes.POINTER(_I64), _P],
     "rbf_get_neighbors": [_P, _P, _I64, _D, _P, _P, _I64, ctypes.POINTER(_I64), _P],
+    "rbf_profile_enable": [_P, ctypes.c_int],
+    "rbf_profile_read": [_P, _P, _P, _P, ctypes.c_int],
+    "rbf_launch_count": [ctypes.POINTER(_I64)],
 }
+
+STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward"]
+
+
+def launch_count() -> int:
+    """Kernels launched by librbfgb.so since it was loaded."""
+    n = ctypes.c_int64()
+    _check(load().rbf_launch_count(ctypes.byref(n)))
+    return n.value
 
 
 def lib_path() -> str:
@@ -236,6 +248,19 @@ class Terrain:
         _check(self.lib.rbf_soft_cost_backward(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], _ptr(g),
                                                _ptr(dw), _ptr(dc), _ptr(dpose), _stream()))
         return dw, dc, dpose
+
+    # -- stage timing -----------------------------------------------------
+    def profile(self, on=True):
+        _check(self.lib.rbf_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """{stage: (ms, work, intervals)} accumulated since the last reset."""
+        k = len(STAGES)
+        ms = (ctypes.c_double * k)()
+        work = (ctypes.c_double * k)()
+        cnt = (ctypes.c_int64 * k)()
+        _check(self.lib.rbf_profile_read(self._h, ms, work, cnt, 1 if reset else 0))
+        return {STAGES[i]: (ms[i], work[i], cnt[i]) for i in range(k)}
 
     # -- inspection -------------------------------------------------------
     def cov(self, ids):
