@@ -136,6 +136,26 @@ rbf_status rbf_eval(rbf_ctx* ctx, const float* q, int64_t Q, float* h, float* gr
 rbf_status rbf_soft_cost(rbf_ctx* ctx, const double* R, const double* t, const float* pts,
                          int64_t n, double* cost, double* grad6, float* resid, void* stream);
 
+/* rbf_soft_cost that allocates nothing, for callers that cannot allocate
+ * device memory while they run: a scan-matching loop with a hard per-frame
+ * deadline (cudaMalloc / cudaFree can synchronize the device and take
+ * milliseconds) or a process that reserves its GPU memory once at start-up.
+ * The paper has no counterpart; the arguments, results and launch are those
+ * of rbf_soft_cost.  Its only scratch, the per-block partial sums, lives in a
+ * fixed device array of 128 KiB (2,048 blocks x 8 float64) that every GPU
+ * which loads the library holds until the process exits.  The launch uses
+ * min(ceil(n / 256), 4 x number of SMs) blocks, so any n is accepted on GPUs
+ * with up to 512 SMs; a launch that would need more blocks returns RBF_ERANGE.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (other streams, other threads, other contexts)
+ * race on it and must be serialized by the caller.  Each call overwrites
+ * every slot it later reads, so nothing of an earlier call leaks into a
+ * result. */
+rbf_status rbf_soft_cost_noalloc(rbf_ctx* ctx, const double* R, const double* t, const float* pts,
+                                 int64_t n, double* cost, double* grad6, float* resid, void* stream);
+
 /* Backward of gout * cost: gradients with respect to the weights (dw: M
  * float32), the centers (dc: M x 2 float32) and the pose (dpose6: 6 float64).
  * gout: device pointer to one float64 (NULL means 1).  Any of dw, dc, dpose6

@@ -12,6 +12,8 @@
 //    gather over a counting sort of the transformed points (deterministic).
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rbf {
@@ -488,6 +490,84 @@ extern "C" rbf_status rbf_soft_cost_backward(rbf_ctx* c, const double* R, const 
     { k_bwd_centers<RBF_KERNEL_GAUSSIAN><<<nbc, 256, 0, s>>>(
         P, x->sorted_xyw.as<float4>(), x->sorted_id.as<int32_t>(), M, pstart.as<int32_t>(),
         order.as<int32_t>(), qpsi.as<float4>(), dw, (float2*)dc); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Soft cost without any allocation.
+//
+// Some callers cannot allocate device memory once they are running: a
+// scan-matching loop with a hard per-frame deadline (cudaMalloc and cudaFree
+// may synchronize the whole device and take milliseconds), or an embedded
+// process that reserves all of its GPU memory at start-up.  For them this
+// variant keeps its scratch -- the per-block partial sums of the cost and the
+// pose gradient -- in a fixed array of this file instead of a buffer the
+// context grows on demand.
+// ---------------------------------------------------------------------------
+namespace rbf {
+
+constexpr int NOALLOC_MAX_BLOCKS = 2048;  // partial sums of at most 2048 blocks: 128 KiB
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS * 8];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[256] = {};
+
+// Device address of the array on device `dev` (the current device).  Host
+// code cannot use the symbol itself: it is only a host-side stand-in.
+static rbf_status noalloc_scratch(int dev, double** out) {
+  if (dev < 0 || dev >= 256) return fail(RBF_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return RBF_OK;
+}
+
+}  // namespace rbf
+
+extern "C" rbf_status rbf_soft_cost_noalloc(rbf_ctx* c, const double* R, const double* t, const float* pts,
+                                            int64_t n, double* cost, double* grad6, float* resid,
+                                            void* stream) {
+  RBF_TRY(check_ctx(c, true));
+  if (n < 0) return fail(RBF_EINVAL, "negative n");
+  if (!cost && !grad6 && !resid) return fail(RBF_EINVAL, "no output requested");
+  if (n > 0 && !pts) return fail(RBF_EINVAL, "null points");
+  Pose T;
+  RBF_TRY(load_pose(R, t, &T));
+  Ctx* x = C(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (cost) RBF_CUDA(cudaMemsetAsync(cost, 0, sizeof(double), s));
+    if (grad6) RBF_CUDA(cudaMemsetAsync(grad6, 0, 6 * sizeof(double), s));
+    return RBF_OK;
+  }
+  unsigned nb = grid_for(n, SC_THREADS, x->device, 4);
+  if (nb > (unsigned)NOALLOC_MAX_BLOCKS)
+    return fail(RBF_ERANGE, "this launch needs %u partial-sum blocks; the static scratch holds %d", nb,
+                NOALLOC_MAX_BLOCKS);
+  double* part = nullptr;
+  RBF_TRY(noalloc_scratch(x->device, &part));
+  EvalParams P = make_eval_params(x);
+  CostParams CP = cost_params(x->cfg);
+  // every block writes all 8 of its partial-sum slots, and the reduction reads
+  // only the nb blocks of this launch: nothing left by an earlier call is used
+  if (x->cfg.kernel == RBF_KERNEL_WENDLAND) {
+    k_soft_cost<RBF_KERNEL_WENDLAND><<<nb, SC_THREADS, 0, s>>>(
+        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid, part);
+    ::rbf::note_launch();
+  } else {
+    k_soft_cost<RBF_KERNEL_GAUSSIAN><<<nb, SC_THREADS, 0, s>>>(
+        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid, part);
+    ::rbf::note_launch();
+  }
+  RBF_CUDA(cudaGetLastError());
+  k_reduce_partials<<<1, 32, 0, s>>>(part, (int)nb, nullptr, cost, grad6);
+  ::rbf::note_launch();
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
