@@ -39,10 +39,14 @@ rbf_status Buf::ensure(size_t nbytes) {
     p = nullptr;
     bytes = 0;
   }
-  // grow with 25% slack so that sizes that creep up frame by frame do not
-  // reallocate (and synchronize) on every call
-  size_t want = nbytes < 256 ? 256 : nbytes + nbytes / 4;
-  want = (want + 255) & ~(size_t)255;
+  // grow to the next power of two (25% slack above 1 GiB) so that sizes that
+  // creep up frame by frame do not reallocate -- and synchronize -- each call
+  size_t want = 256;
+  if (nbytes > ((size_t)1 << 30)) {
+    want = (nbytes + nbytes / 4 + 255) & ~(size_t)255;
+  } else {
+    while (want < nbytes) want <<= 1;
+  }
   cudaError_t e = cudaMalloc(&p, want);
   if (e != cudaSuccess) {
     p = nullptr;
@@ -247,6 +251,17 @@ __global__ void k_lattice_w(const double* __restrict__ c64, const double* __rest
   if (ix >= 0 && ix < nx && iy >= 0 && iy < ny) wl[(int64_t)iy * nx + ix] = (float)w[j];
 }
 
+// W2[j][i] = (Wpad[j][i], Wpad[j][i + 1]) with Wpad = W padded by pad zeros
+__global__ void k_build_w2(const float* __restrict__ W, int nx, int ny, int pad, int pitch, int rows,
+                           float2* __restrict__ W2) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)pitch * rows) return;
+  int j = (int)(e / pitch) - pad, i = (int)(e % pitch) - pad;
+  float a = (j >= 0 && j < ny && i >= 0 && i < nx) ? W[(int64_t)j * nx + i] : 0.f;
+  float b = (j >= 0 && j < ny && i + 1 >= 0 && i + 1 < nx) ? W[(int64_t)j * nx + i + 1] : 0.f;
+  W2[e] = make_float2(a, b);
+}
+
 rbf_status refresh_center_weights(Ctx* c, cudaStream_t s) {
   int64_t M = c->M;
   if (M <= 0) return RBF_OK;
@@ -261,6 +276,13 @@ rbf_status refresh_center_weights(Ctx* c, cudaStream_t s) {
                                    c->lat.y0, 1.0 / c->lat.h, c->lat.nx, c->lat.ny,
                                    c->wlat.as<float>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
+    if (c->lat_rc > 0) {
+      int rc = c->lat_rc, pitch = c->lat.nx + 4 * rc, rows = c->lat.ny + 4 * rc;
+      int64_t tot = (int64_t)pitch * rows;
+      { k_build_w2<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->wlat.as<float>(), c->lat.nx, c->lat.ny, 2 * rc,
+                                                               pitch, rows, c->wlat2.as<float2>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    }
   }
   return RBF_OK;
 }
@@ -368,7 +390,33 @@ rbf_status build_center_grid(Ctx* c, cudaStream_t s) {
   { k_sort_cells<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(c->cell_start.as<int32_t>(), ncell,
                                                                c->sorted_id.as<int32_t>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  if (c->lat.on) RBF_TRY(c->wlat.ensure((size_t)c->lat.nx * c->lat.ny * sizeof(float)));
+  c->lat_rc = 0;
+  if (c->lat.on && c->cfg.kernel == RBF_KERNEL_WENDLAND) {
+    int rc = (int)ceil(c->cfg.rho / c->lat.h - 1e-6);
+    if (rc >= 1 && rc <= 4) c->lat_rc = rc;
+  }
+  if (c->lat.on) {
+    RBF_TRY(c->wlat.ensure((size_t)c->lat.nx * c->lat.ny * sizeof(float)));
+    if (c->lat_rc > 0)
+      RBF_TRY(c->wlat2.ensure((size_t)(c->lat.nx + 4 * c->lat_rc) * (c->lat.ny + 4 * c->lat_rc) * sizeof(float2)));
+    // node coordinates exactly as the float32 copies of the float64 centers
+    std::vector<float> xs((size_t)c->lat.nx), ys((size_t)c->lat.ny);
+    for (int i = 0; i < c->lat.nx; ++i) xs[i] = (float)(c->lat.x0 + ((double)i + 0.5) * c->lat.h);
+    for (int j = 0; j < c->lat.ny; ++j) ys[j] = (float)(c->lat.y0 + ((double)j + 0.5) * c->lat.h);
+    // the lattice origin comes from a center, so take the exact coordinates of
+    // the centers themselves where a row or column holds one
+    for (int64_t k = 0; k < M; ++k) {
+      int ix = (int)floor((hc[2 * k] - c->lat.x0) / c->lat.h);
+      int iy = (int)floor((hc[2 * k + 1] - c->lat.y0) / c->lat.h);
+      if (ix >= 0 && ix < c->lat.nx) xs[ix] = (float)hc[2 * k];
+      if (iy >= 0 && iy < c->lat.ny) ys[iy] = (float)hc[2 * k + 1];
+    }
+    RBF_TRY(c->lat_xs.ensure(xs.size() * sizeof(float)));
+    RBF_TRY(c->lat_ys.ensure(ys.size() * sizeof(float)));
+    RBF_CUDA(cudaMemcpyAsync(c->lat_xs.p, xs.data(), xs.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    RBF_CUDA(cudaMemcpyAsync(c->lat_ys.p, ys.data(), ys.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+  }
   return refresh_center_weights(c, s);
 }
 
@@ -526,8 +574,8 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   if (!c) return RBF_OK;
   Ctx* x = C(c);
   cudaDeviceSynchronize();
-  Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat,
-                 &x->A, &x->g2l, &x->H, &x->L, &x->Pg, &x->dflag, &x->sync_flags};
+  Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2,
+                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Pg, &x->dflag, &x->sync_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   if (x->host_small) cudaFreeHost(x->host_small);

@@ -80,6 +80,9 @@ struct Ctx {
   Buf sorted_id;     // int32 M  (slot -> center id)
   Buf sorted_xyw;    // float4 M (x, y, w, 0) in slot order, float32
   Buf wlat;          // float32 lattice weights (lat.ny x lat.nx), 0 where no center
+  Buf lat_xs, lat_ys; // float32 lattice node coordinates (fl32 of the float64 centers)
+  Buf wlat2;          // padded pairs (W[j][i], W[j][i+1]) for the fixed-window kernel
+  int lat_rc = 0;     // window half-width in nodes (0: kernel not applicable)
 
   // recursive update state: the active block is held in information form
   int64_t a = 0;     // size of the current active block
@@ -88,6 +91,10 @@ struct Ctx {
   Buf H;             // float64 a x a   information matrix of the active block
   Buf L;             // float64 a x a   its Cholesky factor (lower)
   int64_t ldH = 0;   // leading dimension of H and L
+  Buf Lf;            // float32 factor of H (mixed precision), a x a, leading dimension ldw
+  Buf Zd;            // float32 inverses of its 64 x 64 diagonal blocks
+  int64_t ldw = 0;
+  int refine_sweeps = 4;  // float64 refinement sweeps of every mixed-precision solve
   Buf Pg;            // float64 M x M covariance of the centers outside the block
   bool pg_on = false;
 
@@ -223,6 +230,13 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
 rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                     double* Cm, int64_t ldc, cudaStream_t s);
+// mixed precision (mixed.cu)
+rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
+                       cudaStream_t s);
+rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Zd, float* B, int64_t m,
+                  int64_t ldb, bool transpose, cudaStream_t s);
+rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
+                       int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,
                          const double* b, double* r, cudaStream_t s);
 

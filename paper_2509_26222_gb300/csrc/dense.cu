@@ -204,29 +204,56 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // Solves op(L) X = B in place for columns [c0, c0 + mc) of B.
 // transpose = false: forward (block rows in order 0..nblk-1)
 // transpose = true : backward with L^T (block rows nblk-1..0)
-// Thread (i, g) = (tid >> 3, tid & 7) owns row i of the block and the
-// coefficient slice [4g, 4g + 4) of every dependency; the slice is loaded
-// before the wait so that its latency overlaps the producer's work.
+// Before waiting on anything, a CTA inverts the diagonal block of its block
+// row; each dependency is then a 32 x 32 x mc product from a shared-memory
+// copy of the solved block, and the final step is x = D^{-1} acc.
 __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __restrict__ L, int64_t ldl,
                                                               int64_t n, double* B, int64_t ldb,
                                                               int c0, int mc, bool transpose,
                                                               int* flags, int epoch, int* status) {
   __shared__ double acc[NB][TS_MC + 1];
+  __shared__ double Xs[NB][TS_MC + 1];
+  __shared__ double Dinv[NB][NB + 1];
   __shared__ double Dg[NB][NB + 1];
-  __shared__ double inv_d[NB];
   __shared__ int bail;
   const int tid = threadIdx.x, ti = tid >> 3, tg = tid & 7;
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   int64_t nblk = (n + NB - 1) / NB;
   for (int64_t lk = blockIdx.x; lk < nblk; lk += gridDim.x) {
     int64_t r = transpose ? (nblk - 1 - lk) : lk;
     int64_t r0 = r * NB;
     int rb = (int)((n - r0) < NB ? (n - r0) : NB);
+    // diagonal block op(L)_rr (lower for forward, upper for transpose) and its inverse
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      double v = (i == j) ? 1.0 : 0.0;
+      if (i < rb && j < rb) v = transpose ? L[(r0 + j) * ldl + r0 + i] : L[(r0 + i) * ldl + r0 + j];
+      Dg[i][j] = v;
+    }
     for (int e = tid; e < NB * TS_MC; e += blockDim.x) {
       int i = e / TS_MC, j = e % TS_MC;
       acc[i][j] = (i < rb && j < mc) ? B[(r0 + i) * ldb + c0 + j] : 0.0;
     }
     if (tid == 0) bail = 0;
     __syncthreads();
+    // column c of D^{-1}: solve D x = e_c by substitution, lane = row
+    for (int cidx = wid; cidx < NB; cidx += nw) {
+      double b = (lane == cidx) ? 1.0 : 0.0;
+      if (!transpose) {
+        for (int t = 0; t < NB; ++t) {
+          double xt = __shfl_sync(0xffffffffu, b, t) / Dg[t][t];
+          if (lane == t) b = xt;
+          else if (lane > t) b -= Dg[lane][t] * xt;
+        }
+      } else {
+        for (int t = NB - 1; t >= 0; --t) {
+          double xt = __shfl_sync(0xffffffffu, b, t) / Dg[t][t];
+          if (lane == t) b = xt;
+          else if (lane < t) b -= Dg[lane][t] * xt;
+        }
+      }
+      Dinv[lane][cidx] = b;
+    }
     for (int64_t lc = 0; lc < lk; ++lc) {
       int64_t cb = transpose ? (nblk - 1 - lc) : lc;
       int64_t cc0 = cb * NB;
@@ -253,46 +280,32 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __re
       }
       __syncthreads();
       if (bail) break;
+      for (int e = tid; e < NB * mc; e += blockDim.x) {
+        int t = e / mc, j = e % mc;
+        Xs[t][j] = (t < cbs) ? __ldcg(B + (cc0 + t) * ldb + c0 + j) : 0.0;
+      }
+      __syncthreads();
       for (int j = 0; j < mc; ++j) {
         double pp = 0.0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int t = 4 * tg + u;
-          if (t < cbs) pp = fma(lv[u], __ldcg(B + (cc0 + t) * ldb + c0 + j), pp);
-        }
+        for (int u = 0; u < 4; ++u) pp = fma(lv[u], Xs[4 * tg + u][j], pp);
         pp += __shfl_xor_sync(0xffffffffu, pp, 1);
         pp += __shfl_xor_sync(0xffffffffu, pp, 2);
         pp += __shfl_xor_sync(0xffffffffu, pp, 4);
-        if (tg == 0 && ti < rb) acc[ti][j] -= pp;
+        if (tg == 0) acc[ti][j] -= pp;
       }
-    }
-    // diagonal block of op(L)
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      double v = 0.0;
-      if (i < rb && j < rb) v = transpose ? L[(r0 + j) * ldl + r0 + i] : L[(r0 + i) * ldl + r0 + j];
-      Dg[i][j] = v;
+      __syncthreads();
     }
     __syncthreads();
-    if (tid < NB) inv_d[tid] = tid < rb ? 1.0 / Dg[tid][tid] : 0.0;
-    __syncthreads();
-    int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    for (int j = wid; j < mc; j += nw) {
-      double b = lane < rb ? acc[lane][j] : 0.0;
-      if (!transpose) {
-        for (int t = 0; t < rb; ++t) {
-          double xt = __shfl_sync(0xffffffffu, b, t) * inv_d[t];
-          if (lane == t) b = xt;
-          else if (lane > t) b -= Dg[lane][t] * xt;
-        }
-      } else {
-        for (int t = rb - 1; t >= 0; --t) {
-          double xt = __shfl_sync(0xffffffffu, b, t) * inv_d[t];
-          if (lane == t) b = xt;
-          else if (lane < t) b -= Dg[lane][t] * xt;
-        }
-      }
-      if (lane < rb) B[(r0 + lane) * ldb + c0 + j] = b;
+    // x = D^{-1} acc
+    for (int j = 0; j < mc; ++j) {
+      double pp = 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pp = fma(Dinv[ti][4 * tg + u], acc[4 * tg + u][j], pp);
+      pp += __shfl_xor_sync(0xffffffffu, pp, 1);
+      pp += __shfl_xor_sync(0xffffffffu, pp, 2);
+      pp += __shfl_xor_sync(0xffffffffu, pp, 4);
+      if (tg == 0 && ti < rb) B[(r0 + ti) * ldb + c0 + j] = pp;
     }
     __threadfence();
     __syncthreads();

@@ -108,6 +108,273 @@ __global__ void __launch_bounds__(256) k_eval(EvalParams P, const int32_t* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Lattice path: centers on (x0 + (i + 0.5) h, y0 + (j + 0.5) h) with the
+// weights in a dense ny x nx array (0 where the mesh node holds no center).
+// Positions are arithmetic, so a candidate costs one 4-byte weight load; the
+// loop visits only the nodes of each row that lie in the support disc.
+// Coordinates are in lattice units (u = (q_x - x0) / h - 0.5, node i at u = i).
+// ---------------------------------------------------------------------------
+struct LatParams {
+  float u0, v0, inv_h;
+  float R, R2, invR;  // support radius in lattice units
+  int nx, ny;
+  float gscale;       // d h / d q = gscale * sum(...) in metres
+  float r2;           // Gaussian: squared cutoff radius in metres (float32 rule)
+  float inv2s2;       // Gaussian: 1 / (2 sigma^2)
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int KERNEL>
+__device__ __forceinline__ void eval_lattice_one(const LatParams& P, const float* __restrict__ W,
+                                                 const float* __restrict__ xs, const float* __restrict__ ys,
+                                                 float qx, float qy, float& h, float& gx, float& gy) {
+  float u = fmaf(qx, P.inv_h, -P.u0), v = fmaf(qy, P.inv_h, -P.v0);
+  float jl = fmaxf(ceilf(v - P.R), 0.f), jh = fminf(floorf(v + P.R), (float)(P.ny - 1));
+  float ah = 0.f, ax = 0.f, ay = 0.f;
+  if (jl <= jh) {
+    int jlo = (int)jl, jhi = (int)jh;
+    for (int j = jlo; j <= jhi; ++j) {
+      float dv = v - (float)j;
+      float q2 = fmaf(-dv, dv, P.R2);
+      if (q2 <= 0.f) continue;
+      float hw = sqrt_approx(q2);
+      float il = fmaxf(ceilf(u - hw), 0.f), ih = fminf(floorf(u + hw), (float)(P.nx - 1));
+      if (il > ih) continue;
+      int ilo = (int)il, ihi = (int)ih;
+      const float* Wr = W + j * P.nx;
+      float hr = 0.f, xr = 0.f, yr = 0.f;
+      if (KERNEL == RBF_KERNEL_WENDLAND) {
+        // scaled so that the support radius is 1: s^2 = du'^2 + dv'^2
+        float dvs = dv * P.invR;
+        float dv2 = dvs * dvs;
+        float du = (u - (float)ilo) * P.invR;
+#pragma unroll 4
+        for (int i = ilo; i <= ihi; ++i) {
+          float w = Wr[i];
+          float s = sqrt_approx(fmaf(du, du, dv2));
+          float t = 1.f - s;
+          float t2 = t * t;
+          float c = (w * t2) * t;                       // w (1-s)^3
+          hr = fmaf(c, t * fmaf(4.f, s, 1.f), hr);      // w (1-s)^4 (4s+1)
+          xr = fmaf(c, du, xr);
+          yr += c;
+          du -= P.invR;
+        }
+        ah += hr;
+        ax += xr;
+        ay = fmaf(yr, dvs, ay);
+      } else {
+        float dy = qy - ys[j];
+        float dy2 = __fmul_rn(dy, dy);
+        for (int i = ilo; i <= ihi; ++i) {
+          float dx = qx - xs[i];
+          float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
+          if (d2 < P.r2) {
+            float e = Wr[i] * __expf(-d2 * P.inv2s2);
+            hr += e;
+            xr = fmaf(e, dx, xr);
+          }
+        }
+        ah += hr;
+        ax += xr;
+        ay = fmaf(hr, dy, ay);
+      }
+    }
+  }
+  h = ah;
+  gx = ax * P.gscale;
+  gy = ay * P.gscale;
+}
+
+template <int KERNEL, bool SMEM>
+__global__ void __launch_bounds__(256) k_eval_lattice(LatParams P, const float* __restrict__ Wg,
+                                                      const float* __restrict__ xsg, const float* __restrict__ ysg,
+                                                      const float2* __restrict__ q, int64_t Q,
+                                                      float* __restrict__ h, float2* __restrict__ grad) {
+  extern __shared__ float sm[];
+  const float* W = Wg;
+  const float* xs = xsg;
+  const float* ys = ysg;
+  if (SMEM) {
+    int cells = P.nx * P.ny;
+    float* Ws = sm;
+    for (int e = threadIdx.x; e < cells; e += blockDim.x) Ws[e] = Wg[e];
+    W = Ws;
+    if (KERNEL == RBF_KERNEL_GAUSSIAN) {
+      float* xss = sm + cells;
+      float* yss = xss + P.nx;
+      for (int e = threadIdx.x; e < P.nx; e += blockDim.x) xss[e] = xsg[e];
+      for (int e = threadIdx.x; e < P.ny; e += blockDim.x) yss[e] = ysg[e];
+      xs = xss;
+      ys = yss;
+    }
+    __syncthreads();
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float2 p = q[i];
+    float hh, gx, gy;
+    if (isfinite(p.x) && isfinite(p.y)) {
+      eval_lattice_one<KERNEL>(P, W, xs, ys, p.x, p.y, hh, gx, gy);
+    } else {
+      hh = gx = gy = __int_as_float(0x7fc00000);
+    }
+    h[i] = hh;
+    if (grad) grad[i] = make_float2(gx, gy);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-window lattice kernel (Wendland): every lane visits the same
+// 2 RC x 2 RC nodes around its query, so the warp never diverges; nodes
+// outside the support contribute (1 - s)_+ = 0.  Columns go in pairs with
+// packed float32x2 arithmetic; W2[j][i] = (W[j][i], W[j][i+1]) so that a pair
+// is one 8-byte load at any column parity.  The weight array is padded by
+// 2 RC zero nodes on every side, and the window origin is clamped so that it
+// always lies inside the padded array (a clamped window only holds nodes
+// farther than the support radius, i.e. zero terms).
+// ---------------------------------------------------------------------------
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+struct LatWParams {
+  float u0, v0, inv_h, invR;
+  int nx, ny, pitch;  // pitch = nx + 4 RC (padded row length of W2)
+  float gscale;
+};
+
+template <int RC, bool SMEM>
+__global__ void __launch_bounds__(256) k_eval_lattice_win(LatWParams P, const float2* __restrict__ W2g,
+                                                          const float2* __restrict__ q, int64_t Q,
+                                                          float* __restrict__ h, float2* __restrict__ grad) {
+  extern __shared__ float2 sw2[];
+  const float2* W2 = W2g;
+  if (SMEM) {
+    int cells = P.pitch * (P.ny + 4 * RC);
+    for (int e = threadIdx.x; e < cells; e += blockDim.x) sw2[e] = W2g[e];
+    W2 = sw2;
+    __syncthreads();
+  }
+  const u64 one2 = pk2(1.f, 1.f), four2 = pk2(4.f, 4.f), mone2 = pk2(-1.f, -1.f);
+  for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < Q;
+       qi += (int64_t)gridDim.x * blockDim.x) {
+    float2 p = q[qi];
+    if (!(isfinite(p.x) && isfinite(p.y))) {
+      float nan = __int_as_float(0x7fc00000);
+      h[qi] = nan;
+      if (grad) grad[qi] = make_float2(nan, nan);
+      continue;
+    }
+    float u = fmaf(p.x, P.inv_h, -P.u0), v = fmaf(p.y, P.inv_h, -P.v0);
+    // a query farther than RC + 1 nodes outside the lattice meets no support;
+    // clamping it there keeps every offset below finite and the terms zero
+    u = fminf(fmaxf(u, (float)(-2 * RC - 2)), (float)(P.nx + 2 * RC + 1));
+    v = fminf(fmaxf(v, (float)(-2 * RC - 2)), (float)(P.ny + 2 * RC + 1));
+    // window origin (node coordinates): floor(u) - RC + 1, clamped into the pad
+    float fu = fminf(fmaxf(floorf(u), (float)(-RC - 1)), (float)(P.nx + RC - 1));
+    float fv = fminf(fmaxf(floorf(v), (float)(-RC - 1)), (float)(P.ny + RC - 1));
+    int ib = (int)fu + RC + 1;  // padded column of the window's first node
+    int jb = (int)fv + RC + 1;
+    // offsets of the window's first node, in units of the support radius
+    float du0 = (u - fu + (float)(RC - 1)) * P.invR;
+    float dv0 = (v - fv + (float)(RC - 1)) * P.invR;
+    u64 dup[RC], du2p[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+      float a = du0 - (float)(2 * k) * P.invR, b = du0 - (float)(2 * k + 1) * P.invR;
+      dup[k] = pk2(a, b);
+      du2p[k] = pk2(a * a, b * b);
+    }
+    u64 hacc = 0ull, xacc = 0ull;
+    float yacc = 0.f;
+    const float2* base = W2 + (int64_t)jb * P.pitch + ib;
+#pragma unroll
+    for (int m = 0; m < 2 * RC; ++m) {
+      float dv = dv0 - (float)m * P.invR;
+      u64 dv2 = pk2(dv * dv, dv * dv);
+      const float2* row = base + m * P.pitch;
+      u64 yr = 0ull;
+#pragma unroll
+      for (int k = 0; k < RC; ++k) {
+        float2 wv = row[2 * k];
+        u64 w = pk2(wv.x, wv.y);
+        u64 e = add2(du2p[k], dv2);
+        float e0, e1;
+        up2(e, e0, e1);
+        u64 sq = pk2(sqrt_approx(e0), sqrt_approx(e1));
+        u64 t = fma2(sq, mone2, one2);
+        float t0, t1;
+        up2(t, t0, t1);
+        t = pk2(fmaxf(t0, 0.f), fmaxf(t1, 0.f));
+        u64 c = mul2(mul2(w, mul2(t, t)), t);        // w (1-s)^3
+        u64 pp = mul2(fma2(four2, sq, one2), t);      // (1-s)(4s+1)
+        hacc = fma2(c, pp, hacc);
+        xacc = fma2(c, dup[k], xacc);
+        yr = add2(yr, c);
+      }
+      float y0, y1;
+      up2(yr, y0, y1);
+      yacc = fmaf(y0 + y1, dv, yacc);
+    }
+    float h0, h1, x0, x1;
+    up2(hacc, h0, h1);
+    up2(xacc, x0, x1);
+    h[qi] = h0 + h1;
+    if (grad) grad[qi] = make_float2((x0 + x1) * P.gscale, yacc * P.gscale);
+  }
+}
+
+static LatParams make_lat_params(const Ctx* c) {
+  LatParams P;
+  const Lattice& L = c->lat;
+  P.inv_h = (float)(1.0 / L.h);
+  P.u0 = (float)(L.x0 / L.h + 0.5);
+  P.v0 = (float)(L.y0 / L.h + 0.5);
+  double r = eval_radius(c->cfg);
+  double R = r / L.h;
+  P.R = (float)R;
+  P.R2 = (float)(R * R);
+  P.invR = (float)(1.0 / R);
+  P.nx = L.nx;
+  P.ny = L.ny;
+  float r32 = (float)r;
+  P.r2 = r32 * r32;
+  P.inv2s2 = (float)(1.0 / (2.0 * c->cfg.sigma * c->cfg.sigma));
+  if (c->cfg.kernel == RBF_KERNEL_WENDLAND)
+    P.gscale = (float)(-20.0 / (c->cfg.rho * c->cfg.rho) * r);  // du is in units of R lattice cells = r metres
+  else
+    P.gscale = (float)(-1.0 / (c->cfg.sigma * c->cfg.sigma));
+  return P;
+}
+
 static int num_sms(int dev) {
   static int cached[64] = {0};
   if (dev < 0 || dev >= 64) return 148;
@@ -392,9 +659,67 @@ extern "C" rbf_status rbf_eval(rbf_ctx* c, const float* q, int64_t Q, float* h, 
     return fail(RBF_EINVAL, "q and grad must be 8-byte aligned");
   Ctx* x = C(c);
   cudaStream_t s = (cudaStream_t)stream;
+  StageTimer st(x, RBF_STAGE_EVAL, s, 20.0 * (double)Q);
+  if (x->lat.on && x->lat_rc > 0 && x->cfg.kernel == RBF_KERNEL_WENDLAND) {
+    LatWParams L;
+    L.inv_h = (float)(1.0 / x->lat.h);
+    L.u0 = (float)(x->lat.x0 / x->lat.h + 0.5);
+    L.v0 = (float)(x->lat.y0 / x->lat.h + 0.5);
+    L.invR = (float)(x->lat.h / x->cfg.rho);
+    L.nx = x->lat.nx;
+    L.ny = x->lat.ny;
+    L.pitch = x->lat.nx + 4 * x->lat_rc;
+    L.gscale = (float)(-20.0 / x->cfg.rho);
+    size_t smem = (size_t)L.pitch * (x->lat.ny + 4 * x->lat_rc) * sizeof(float2);
+    bool use_smem = smem <= 100 * 1024;
+    const float2* W2 = x->wlat2.as<float2>();
+    auto launch = [&](auto kern) -> rbf_status {
+      int occ = 0;
+      size_t sm = use_smem ? smem : 0;
+      if (sm > 48 * 1024) RBF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm));
+      if (occ < 1) occ = 1;
+      unsigned nb = grid_for(Q, 256, x->device, occ);
+      kern<<<nb, 256, sm, s>>>(L, W2, (const float2*)q, Q, h, (float2*)grad);
+      ::rbf::note_launch();
+      RBF_CUDA(cudaGetLastError());
+      return RBF_OK;
+    };
+    switch (x->lat_rc) {
+      case 1: return use_smem ? launch(k_eval_lattice_win<1, true>) : launch(k_eval_lattice_win<1, false>);
+      case 2: return use_smem ? launch(k_eval_lattice_win<2, true>) : launch(k_eval_lattice_win<2, false>);
+      case 3: return use_smem ? launch(k_eval_lattice_win<3, true>) : launch(k_eval_lattice_win<3, false>);
+      default: return use_smem ? launch(k_eval_lattice_win<4, true>) : launch(k_eval_lattice_win<4, false>);
+    }
+  }
+  if (x->lat.on) {
+    LatParams L = make_lat_params(x);
+    size_t cells = (size_t)x->lat.nx * x->lat.ny;
+    size_t smem = (cells + (x->cfg.kernel == RBF_KERNEL_GAUSSIAN ? x->lat.nx + x->lat.ny : 0)) * sizeof(float);
+    bool use_smem = smem <= 160 * 1024;
+    const float* xs = x->lat_xs.as<float>();
+    const float* ys = x->lat_ys.as<float>();
+    const float* Wl = x->wlat.as<float>();
+    auto launch = [&](auto kern) -> rbf_status {
+      int occ = 0;
+      size_t sm = use_smem ? smem : 0;
+      if (sm > 48 * 1024) RBF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm));
+      if (occ < 1) occ = 1;
+      unsigned nb = grid_for(Q, 256, x->device, occ);
+      kern<<<nb, 256, sm, s>>>(L, Wl, xs, ys, (const float2*)q, Q, h, (float2*)grad);
+      ::rbf::note_launch();
+      RBF_CUDA(cudaGetLastError());
+      return RBF_OK;
+    };
+    if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
+      return use_smem ? launch(k_eval_lattice<RBF_KERNEL_WENDLAND, true>)
+                      : launch(k_eval_lattice<RBF_KERNEL_WENDLAND, false>);
+    return use_smem ? launch(k_eval_lattice<RBF_KERNEL_GAUSSIAN, true>)
+                    : launch(k_eval_lattice<RBF_KERNEL_GAUSSIAN, false>);
+  }
   EvalParams P = make_eval_params(x);
   unsigned nb = grid_for(Q, 256, x->device, 8);
-  StageTimer st(x, RBF_STAGE_EVAL, s, 20.0 * (double)Q);
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
     { k_eval<RBF_KERNEL_WENDLAND><<<nb, 256, 0, s>>>(P, x->cell_start.as<int32_t>(),
                                                    x->sorted_xyw.as<float4>(), (const float2*)q, Q,

@@ -413,6 +413,15 @@ __global__ void k_pg_init(double* __restrict__ Pg, int64_t M, double diag) {
   if (j < M) Pg[j * M + j] = diag;
 }
 
+// P[u][v] = 0.5 (X[pos[u]][v] + X[pos[v]][u]) for X = H^{-1} E_pos (n x k)
+__global__ void k_gather_inv_block(const double* __restrict__ X, int64_t k, const int32_t* __restrict__ pos,
+                                   double* __restrict__ P) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  int64_t uu = e / k, v = e % k;
+  P[e] = 0.5 * (X[(int64_t)pos[uu] * k + v] + X[(int64_t)pos[v] * k + uu]);
+}
+
 __global__ void k_w_add(double* __restrict__ w, const int32_t* __restrict__ A, int64_t a,
                         const double* __restrict__ delta) {
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -641,15 +650,23 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_CUDA(cudaMemsetAsync(Hn.p, 0, (size_t)an * an * sizeof(double), s));
   Buf& Pdd = c->scratch(38);
   if (d > 0) {
-    // Y = L_prev^{-1} E_D, P_DD = Y^T Y
     Buf& Y = c->scratch(39);
     RBF_TRY(Y.ensure((size_t)ap * d * sizeof(double)));
     RBF_TRY(Pdd.ensure((size_t)d * d * sizeof(double)));
     { k_unit_rhs<<<nblk(ap * d), 256, 0, s>>>(Y.as<double>(), ap, d, Dl.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s));
-    RBF_TRY(gemm_f64(c, true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
-                     Pdd.as<double>(), d, s));
+    if (mixed) {
+      // X = H_prev^{-1} E_D by refined solves with the float32 factor; P_DD = X[D, :]
+      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(), ap,
+                          Y.as<double>(), d, c->refine_sweeps, s));
+      { k_gather_inv_block<<<nblk(d * d), 256, 0, s>>>(Y.as<double>(), d, Dl.as<int32_t>(), Pdd.as<double>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    } else {
+      // Y = L_prev^{-1} E_D, P_DD = Y^T Y
+      RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s));
+      RBF_TRY(gemm_f64(c, true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
+                       Pdd.as<double>(), d, s));
+    }
     if (sN > 0) {
       // T = H_prev permuted to [D; S]; d steps of Cholesky leave H_S in T[d:, d:]
       Buf& perm = c->scratch(40);
@@ -718,14 +735,28 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   }
 
   // 8. factor H' and solve for the weight increment
-  RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, mixed, s));
+  Buf& Wn = c->scratch(27);
+  Buf& Zdn = c->scratch(63);
+  const int64_t ldw = (an + 3) & ~(int64_t)3;
+  if (mixed) {
+    RBF_TRY(Wn.ensure((size_t)an * ldw * sizeof(float)));
+    RBF_TRY(Zdn.ensure((size_t)((an + 63) / 64) * 64 * 64 * sizeof(float)));
+    RBF_TRY(potrf_mixed(c, Hn.as<double>(), ld, an, Wn.as<float>(), ldw, Zdn.as<float>(), s));
+  } else {
+    RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s));
+  }
   int flag = 0;
   RBF_TRY(read_dev_flag(c, s, &flag));
   if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
   {
-    StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 14.0 : 2.0) * (double)an * an);
-    RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), mixed, s));
+    StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 2.0 * c->refine_sweeps + 2.0 * (c->refine_sweeps - 1) : 2.0) *
+                                            (double)an * an);
+    if (mixed)
+      RBF_TRY(mixed_solve(c, Hn.as<double>(), ld, Wn.as<float>(), ldw, Zdn.as<float>(), an, u.as<double>(), 1,
+                          c->refine_sweeps, s));
+    else
+      RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), false, s));
   }
   RBF_TRY(read_dev_flag(c, s, &flag));
   if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
@@ -748,7 +779,13 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaGetLastError());
   }
   std::swap(c->H, Hn);
-  std::swap(c->L, Ln);
+  if (mixed) {
+    std::swap(c->Lf, Wn);
+    std::swap(c->Zd, Zdn);
+    c->ldw = ldw;
+  } else {
+    std::swap(c->L, Ln);
+  }
   std::swap(c->A, An);
   std::swap(c->g2l, g2ln);
   c->a = an;
@@ -862,9 +899,16 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
     RBF_CUDA(cudaMemcpyAsync(lb.p, lpos.data(), (size_t)ka * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     { k_unit_rhs<<<nblk(c->a * ka), 256, 0, s>>>(Y.as<double>(), c->a, ka, lb.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s));
-    RBF_TRY(gemm_f64(c, true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,
-                     Paa.as<double>(), ka, s));
+    if (c->cfg.update_precision == RBF_UPDATE_MIXED) {
+      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(), c->a,
+                          Y.as<double>(), ka, c->refine_sweeps, s));
+      { k_gather_inv_block<<<nblk(ka * ka), 256, 0, s>>>(Y.as<double>(), ka, lb.as<int32_t>(), Paa.as<double>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    } else {
+      RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s));
+      RBF_TRY(gemm_f64(c, true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,
+                       Paa.as<double>(), ka, s));
+    }
   }
   { k_cov_assemble<<<nblk(k * k), 256, 0, s>>>(k, ib.as<int32_t>(), c->g2l.as<int32_t>(), rb.as<int32_t>(),
                                              ka > 0 ? Paa.as<double>() : nullptr, ka,
