@@ -73,6 +73,10 @@ typedef struct rbf_config {
   double mesh_h;            /*   (mesh_x0 + (i + 0.5) mesh_h, mesh_y0 + (j + 0.5) mesh_h) */
   int32_t mesh_nx, mesh_ny; /*   0 <= i < mesh_nx, 0 <= j < mesh_ny, row-major (j outer) */
   double r_kd;              /* center selection radius (Sec. III-A) */
+  int32_t refine_sweeps;    /* RBF_UPDATE_MIXED: float64 refinement sweeps of the solves with
+                               the float32 factor (0 = defaults: 3 for the weights, 2 for
+                               covariance blocks; n > 0: n for both; 1 = no refinement) */
+  int32_t reserved0;
 } rbf_config;
 
 /* Create a context on the current CUDA device.  Validates cfg (positive radii,

@@ -436,6 +436,8 @@ rbf_status install_centers(Ctx* c, const double* cxy, int64_t M, cudaStream_t s)
   RBF_TRY(c->A.ensure((size_t)M * sizeof(int32_t)));
   RBF_TRY(c->g2l.ensure((size_t)M * sizeof(int32_t)));
   RBF_CUDA(cudaMemsetAsync(c->g2l.p, 0xff, (size_t)M * sizeof(int32_t), s));
+  RBF_TRY(c->departed.ensure((size_t)M * sizeof(int32_t)));
+  RBF_CUDA(cudaMemsetAsync(c->departed.p, 0, (size_t)M * sizeof(int32_t), s));
   c->M = M;
   RBF_TRY(reset_update_state(c));
   rbf_status st = build_center_grid(c, s);
@@ -543,10 +545,13 @@ extern "C" rbf_status rbf_create(const rbf_config* cfg, rbf_ctx** out) {
   if (!(cfg->lambda > 0)) return fail(RBF_EINVAL, "lambda must be > 0");
   if (cfg->loss == RBF_LOSS_HUBER && !(cfg->huber_delta > 0))
     return fail(RBF_EINVAL, "huber_delta must be > 0");
+  if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 16)
+    return fail(RBF_EINVAL, "refine_sweeps must be in [0, 16]");
   rbf_ctx* c = new (std::nothrow) rbf_ctx();
   if (!c) return fail(RBF_ENOMEM, "host allocation failed");
   Ctx* x = C(c);
   x->cfg = *cfg;
+  if (cfg->refine_sweeps > 0) x->refine_sweeps = x->refine_sweeps_cov = cfg->refine_sweeps;
   cudaError_t e = cudaGetDevice(&x->device);
   if (e != cudaSuccess) {
     delete c;
@@ -575,7 +580,7 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   Ctx* x = C(c);
   cudaDeviceSynchronize();
   Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2,
-                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Pg, &x->dflag, &x->sync_flags};
+                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   if (x->host_small) cudaFreeHost(x->host_small);

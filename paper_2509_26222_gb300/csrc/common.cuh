@@ -94,8 +94,10 @@ struct Ctx {
   Buf Lf;            // float32 factor of H (mixed precision), a x a, leading dimension ldw
   Buf Zd;            // float32 inverses of its 64 x 64 diagonal blocks
   int64_t ldw = 0;
-  int refine_sweeps = 4;  // float64 refinement sweeps of every mixed-precision solve
+  int refine_sweeps = 3;      // float64 refinement sweeps of the weight solve (mixed precision)
+  int refine_sweeps_cov = 2;  // ... of the covariance solves (leaving centers, rbf_get_cov)
   Buf Pg;            // float64 M x M covariance of the centers outside the block
+  Buf departed;      // int32 M: 1 once a center has left an active block (its P may be coupled)
   bool pg_on = false;
 
   // device status word + epoch counter for flag-based waits
@@ -237,6 +239,7 @@ rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Z
                   int64_t ldb, bool transpose, cudaStream_t s);
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
                        int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s);
+rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,
                          const double* b, double* r, cudaStream_t s);
 

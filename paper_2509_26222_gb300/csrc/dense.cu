@@ -307,9 +307,11 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __re
       pp += __shfl_xor_sync(0xffffffffu, pp, 4);
       if (tg == 0 && ti < rb) B[(r0 + ti) * ldb + c0 + j] = pp;
     }
-    __threadfence();
     __syncthreads();
-    if (tid == 0) st_release(flags + r, epoch);
+    if (tid == 0) {
+      __threadfence();  // cumulative: orders the block's stores (seen through the barrier) before the flag
+      st_release(flags + r, epoch);
+    }
   }
 }
 
@@ -343,6 +345,85 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
     RBF_CUDA(cooperative_launch((const void*)k_trsm_syncfree, dim3((unsigned)grid),
                                          dim3(TS_THREADS), args, 0, s));
   }
+  return RBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Inverse of a small SPD matrix (m <= 64) in one CTA: Cholesky, inverse of
+// the factor, G^{-1} = Z^T Z.  In place, row-major m x m.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_spd_inverse_small(double* __restrict__ G, int m, int* __restrict__ flag) {
+  __shared__ double T[64][65];
+  __shared__ double Z[64][65];
+  __shared__ double rinv[64];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 64 * 64; e += blockDim.x) {
+    int i = e / 64, j = e % 64;
+    T[i][j] = (i < m && j < m) ? G[i * m + j] : (i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (tid < 32) {  // warp-synchronous left-looking Cholesky, lane owns rows lane, lane + 32
+    const int lane = tid;
+    for (int j = 0; j < m; ++j) {
+      double piv = 0.0;
+      if (lane == (j & 31)) {
+        double s = T[j][j];
+        for (int t = 0; t < j; ++t) s = fma(-T[j][t], T[j][t], s);
+        if (!(s > 0.0)) {
+          atomicOr(flag, DEV_NOT_SPD);
+          s = 1.0;
+        }
+        piv = sqrt(s);
+        T[j][j] = piv;
+        rinv[j] = 1.0 / piv;
+      }
+      piv = __shfl_sync(0xffffffffu, piv, j & 31);
+      double ri = 1.0 / piv;
+      for (int half = 0; half < 2; ++half) {
+        int r = lane + 32 * half;
+        if (r > j && r < m) {
+          double s = T[r][j];
+          for (int t = 0; t < j; ++t) s = fma(-T[r][t], T[j][t], s);
+          T[r][j] = s * ri;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  {  // Z = L^{-1}, column c by threads 4c .. 4c + 3
+    const int cidx = tid >> 2, g = tid & 3;
+    const unsigned gm = 0xfu << (tid & 28);
+    for (int i = 0; i < m; ++i) {
+      if (cidx < m) {
+        if (i < cidx) {
+          if (g == 0) Z[i][cidx] = 0.0;
+        } else if (i == cidx) {
+          if (g == 0) Z[i][cidx] = rinv[i];
+        } else {
+          double s = 0.0;
+          for (int t = cidx + g; t < i; t += 4) s = fma(T[i][t], Z[t][cidx], s);
+          s += __shfl_xor_sync(gm, s, 1);
+          s += __shfl_xor_sync(gm, s, 2);
+          if (g == 0) Z[i][cidx] = -s * rinv[i];
+        }
+      }
+      __syncwarp(gm);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    int i = e / m, j = e % m;
+    double s = 0.0;
+    for (int t = (i > j ? i : j); t < m; ++t) s = fma(Z[t][i], Z[t][j], s);
+    G[e] = s;
+  }
+}
+
+rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s) {
+  if (m <= 0 || m > 64) return fail(RBF_EINVAL, "spd_inverse_small: m must be in [1, 64]");
+  { k_spd_inverse_small<<<1, 256, 0, s>>>(G, (int)m, c->dflag.as<int>()); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
 

@@ -34,11 +34,15 @@ __global__ void k_mx_to_f32(const double* __restrict__ H, int64_t ldh, int64_t n
   W[i * ldw + j] = (float)H[i * ldh + j];
 }
 
+// Cholesky of the 64 x 64 diagonal block (float32, one CTA of 256 threads),
+// right-looking with one barrier per column: every thread computes the
+// pivot's reciprocal square root itself, the trailing update uses
+// T_ik -= T_ij T_kj / T_jj with unscaled columns, and the columns are scaled
+// once at the end.  rd[j] = 1 / L_jj is kept for the panel solve.
 __global__ void __launch_bounds__(256) k_mx_diag(float* __restrict__ W, int64_t ldw, int64_t k, int kb,
-                                                 float* __restrict__ Zout, int* __restrict__ flag) {
+                                                 float* __restrict__ rd_out, int* __restrict__ flag) {
   __shared__ float T[MB][MB + 1];
-  __shared__ float Z[MB][MB + 1];
-  __shared__ float rinv;
+  __shared__ float rv[MB];
   const int tid = threadIdx.x;
   for (int e = tid; e < MB * MB; e += blockDim.x) {
     int i = e / MB, j = e % MB;
@@ -48,85 +52,135 @@ __global__ void __launch_bounds__(256) k_mx_diag(float* __restrict__ W, int64_t 
     T[i][j] = v;
   }
   __syncthreads();
-  const int tx = tid & (MB - 1), ty = tid >> 6, ny = blockDim.x >> 6;
+  const int tx = tid & (MB - 1), ty = tid >> 6;
   for (int j = 0; j < MB; ++j) {
+    float d = T[j][j];
+    float ri = rsqrtf(d);
     if (tid == 0) {
-      float d = T[j][j];
-      if (!(d > 0.f)) {
-        atomicOr(flag, DEV_NOT_SPD);
-        d = 1.f;
-      }
-      float r = sqrtf(d);
-      T[j][j] = r;
-      rinv = 1.f / r;
+      if (!(d > 0.f)) atomicOr(flag, DEV_NOT_SPD);
+      rv[j] = ri;
     }
-    __syncthreads();
-    if (tid < MB && tid > j) T[tid][j] *= rinv;
-    __syncthreads();
     if (tx > j) {
-      float tkj = T[tx][j];
-      for (int i = ty; i < MB; i += ny)
-        if (i >= tx) T[i][tx] = fmaf(-T[i][j], tkj, T[i][tx]);
+      float ckj = T[tx][j] * ri * ri;
+      float tij[MB / 4], tik[MB / 4];
+#pragma unroll
+      for (int q = 0; q < MB / 4; ++q) {
+        int i = ty + 4 * q;
+        tij[q] = T[i][j];
+        tik[q] = T[i][tx];
+      }
+#pragma unroll
+      for (int q = 0; q < MB / 4; ++q) {
+        int i = ty + 4 * q;
+        if (i >= tx) T[i][tx] = fmaf(-tij[q], ckj, tik[q]);
+      }
     }
     __syncthreads();
   }
-  // Z = T^{-1} (lower triangular), one column per thread
-  if (tid < MB) {
-    const int cidx = tid;
-    for (int i = 0; i < cidx; ++i) Z[i][cidx] = 0.f;
-    Z[cidx][cidx] = 1.f / T[cidx][cidx];
-    for (int i = cidx + 1; i < MB; ++i) {
-      float s = 0.f;
-      for (int t = cidx; t < i; ++t) s = fmaf(T[i][t], Z[t][cidx], s);
-      Z[i][cidx] = -s / T[i][i];
-    }
-  }
-  __syncthreads();
   for (int e = tid; e < MB * MB; e += blockDim.x) {
     int i = e / MB, j = e % MB;
-    if (i < kb && j < kb) W[(k + i) * ldw + k + j] = (j <= i) ? T[i][j] : 0.f;
-    Zout[e] = Z[i][j];
+    if (i < kb && j < kb) W[(k + i) * ldw + k + j] = (j <= i) ? T[i][j] * rv[j] : 0.f;
   }
+  if (tid < MB) rd_out[tid] = rv[tid];
 }
 
-// Panel rows [k + kb, n): L = W[rows, k:k+kb] Z^T, written to W and as bf16
-// slices (row index relative to k + kb, 64 columns, zero beyond kb).
+// Panel rows [k + kb, n): solve X L_kk^T = W[rows, k:k+kb] row by row (four
+// threads per row share each dot product), write X to W and as bf16 slices
+// (row index relative to k + kb, 64 columns, zero beyond kb).
 __global__ void __launch_bounds__(256) k_mx_panel(float* __restrict__ W, int64_t ldw, int64_t n, int64_t k,
-                                                  int kb, const float* __restrict__ Zk,
+                                                  int kb, const float* __restrict__ rd,
                                                   __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pm,
                                                   __nv_bfloat16* __restrict__ Pl) {
-  __shared__ float Zs[MB][MB + 1];
-  __shared__ float As[MB][MB + 1];
+  __shared__ float Ls[MB][MB + 1];  // L_kk (lower)
+  __shared__ float X[MB][MB + 1];   // this CTA's 64 rows
+  __shared__ float rds[MB];
   const int tid = threadIdx.x;
   const int64_t k0 = k + kb;
   const int64_t r0 = k0 + (int64_t)blockIdx.x * MB;
   for (int e = tid; e < MB * MB; e += blockDim.x) {
     int i = e / MB, t = e % MB;
-    Zs[i][t] = Zk[e];
+    Ls[i][t] = (i < kb && t <= i) ? W[(k + i) * ldw + k + t] : 0.f;
     int64_t r = r0 + i;
-    As[i][t] = (r < n && t < kb) ? W[r * ldw + k + t] : 0.f;
+    X[i][t] = (r < n && t < kb) ? W[r * ldw + k + t] : 0.f;
   }
+  if (tid < MB) rds[tid] = tid < kb ? rd[tid] : 0.f;
   __syncthreads();
   const int ri = tid >> 2, g = tid & 3;
-  const int64_t r = r0 + ri;
-  for (int q = 0; q < MB / 4; ++q) {
-    int j = g + 4 * q;
-    float x = 0.f;
-    for (int t = 0; t <= j; ++t) x = fmaf(As[ri][t], Zs[j][t], x);
-    if (r < n) {
-      if (j < kb) W[r * ldw + k + j] = x;
-      else x = 0.f;
-      __nv_bfloat16 h = __float2bfloat16_rn(x);
-      float rem = x - __bfloat162float(h);
-      __nv_bfloat16 m = __float2bfloat16_rn(rem);
-      float rem2 = rem - __bfloat162float(m);
-      __nv_bfloat16 l = __float2bfloat16_rn(rem2);
-      int64_t pr = r - k0;
-      Ph[pr * MB + j] = h;
-      Pm[pr * MB + j] = m;
-      Pl[pr * MB + j] = l;
-    }
+  const unsigned gm = 0xfu << (tid & 28);
+  for (int j = 0; j < kb; ++j) {
+    float s = 0.f;
+    for (int t = g; t < j; t += 4) s = fmaf(X[ri][t], Ls[j][t], s);
+    s += __shfl_xor_sync(gm, s, 1);
+    s += __shfl_xor_sync(gm, s, 2);
+    if (g == 0) X[ri][j] = (X[ri][j] - s) * rds[j];
+    __syncwarp(gm);
   }
+  __syncthreads();
+  for (int e = tid; e < MB * MB; e += blockDim.x) {
+    int i = e / MB, j = e % MB;
+    int64_t r = r0 + i;
+    if (r >= n) continue;
+    float x = X[i][j];
+    if (j < kb) W[r * ldw + k + j] = x;
+    else x = 0.f;
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    float rem = x - __bfloat162float(h);
+    __nv_bfloat16 mm = __float2bfloat16_rn(rem);
+    float rem2 = rem - __bfloat162float(mm);
+    __nv_bfloat16 l = __float2bfloat16_rn(rem2);
+    int64_t pr = r - k0;
+    Ph[pr * MB + j] = h;
+    Pm[pr * MB + j] = mm;
+    Pl[pr * MB + j] = l;
+  }
+}
+
+// Inverses of every 64 x 64 diagonal block of the finished factor, one CTA per
+// block (all blocks at once, off the factorization's critical chain): a row
+// sweep with one barrier per row, Z_ic -= L_ij Z_jc after row j is final.
+__global__ void __launch_bounds__(256) k_mx_blockinv(const float* __restrict__ W, int64_t ldw, int64_t n,
+                                                     float* __restrict__ Zd) {
+  __shared__ float T[MB][MB + 1];
+  __shared__ float Z[MB][MB + 1];
+  __shared__ float rl[MB];
+  const int tid = threadIdx.x;
+  const int64_t k = (int64_t)blockIdx.x * MB;
+  const int kb = (int)((n - k) < MB ? (n - k) : MB);
+  for (int e = tid; e < MB * MB; e += blockDim.x) {
+    int i = e / MB, j = e % MB;
+    float v;
+    if (i < kb && j < kb) v = (j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
+    else v = (i == j) ? 1.f : 0.f;
+    T[i][j] = v;
+    Z[i][j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  if (tid < MB) rl[tid] = 1.f / T[tid][tid];
+  __syncthreads();
+  const int tx = tid & (MB - 1), ty = tid >> 6;
+  for (int j = 0; j < MB; ++j) {
+    float lj = rl[j];
+    if (tx <= j) {
+      float zjc = Z[j][tx] * lj;
+      float lij[MB / 4], zic[MB / 4];
+#pragma unroll
+      for (int q = 0; q < MB / 4; ++q) {
+        int i = ty + 4 * q;
+        lij[q] = T[i][j];
+        zic[q] = Z[i][tx];
+      }
+#pragma unroll
+      for (int q = 0; q < MB / 4; ++q) {
+        int i = ty + 4 * q;
+        if (i > j) Z[i][tx] = fmaf(-lij[q], zjc, zic[q]);
+      }
+    }
+    __syncthreads();
+    if (ty == 0 && tx <= j) Z[j][tx] *= lj;
+    __syncthreads();
+  }
+  float* out = Zd + (int64_t)blockIdx.x * MB * MB;
+  for (int e = tid; e < MB * MB; e += blockDim.x) out[e] = Z[e / MB][e % MB];
 }
 
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
@@ -143,6 +197,9 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
   __nv_bfloat16* Ph = pb.as<__nv_bfloat16>();
   __nv_bfloat16* Pm = Ph + (n + MB) * MB;
   __nv_bfloat16* Pl = Pm + (n + MB) * MB;
+  Buf& rb = c->scratch(54);
+  RBF_TRY(rb.ensure(MB * sizeof(float)));
+  float* rdiag = rb.as<float>();
   static bool attr_set[64] = {false};
   if (!attr_set[c->device & 63]) {
     RBF_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
@@ -153,10 +210,10 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
     int64_t rows = n - k - kb;
     {
       StageTimer st(c, RBF_STAGE_PANEL, s, (double)kb * kb * kb / 3.0 + (double)rows * kb * kb);
-      { k_mx_diag<<<1, 256, 0, s>>>(W, ldw, k, kb, Zd + step * MB * MB, flag); ::rbf::note_launch(); }
+      { k_mx_diag<<<1, 256, 0, s>>>(W, ldw, k, kb, rdiag, flag); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
       if (rows > 0) {
-        { k_mx_panel<<<(unsigned)((rows + MB - 1) / MB), 256, 0, s>>>(W, ldw, n, k, kb, Zd + step * MB * MB, Ph, Pm,
+        { k_mx_panel<<<(unsigned)((rows + MB - 1) / MB), 256, 0, s>>>(W, ldw, n, k, kb, rdiag, Ph, Pm,
                                                                        Pl); ::rbf::note_launch(); }
         RBF_CUDA(cudaGetLastError());
       }
@@ -169,14 +226,20 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
       RBF_CUDA(cudaGetLastError());
     }
   }
+  {
+    StageTimer st(c, RBF_STAGE_PANEL, s, 0.0);
+    int64_t nb = (n + MB - 1) / MB;
+    { k_mx_blockinv<<<(unsigned)nb, 256, 0, s>>>(W, ldw, n, Zd); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  }
   return RBF_OK;
 }
 
 // ---------------------------------------------------------------------------
 // float32 sync-free triangular solve (block 64) with the stored inverses of
-// the diagonal blocks: op(L) X = B for up to 16 right-hand sides per launch.
+// the diagonal blocks: op(L) X = B for up to 48 right-hand sides per launch.
 // ---------------------------------------------------------------------------
-constexpr int T32_MC = 16;
+constexpr int T32_MC = 48;
 constexpr long long T32_SPIN = 1LL << 22;
 
 __device__ __forceinline__ int ld_acq(const int* p) {
@@ -261,9 +324,11 @@ __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int
       pp += __shfl_xor_sync(0xffffffffu, pp, 2);
       if (tg == 0 && ti < rb) B[(r0 + ti) * ldb + c0 + j] = pp;
     }
-    __threadfence();
     __syncthreads();
-    if (tid == 0) st_rel(flags + r, epoch);
+    if (tid == 0) {
+      __threadfence();  // cumulative: orders the block's stores (seen through the barrier) before the flag
+      st_rel(flags + r, epoch);
+    }
   }
 }
 
@@ -313,19 +378,33 @@ __global__ void k_add_f32_to_f64(double* __restrict__ x, const float* __restrict
   if (i < n) x[i] += (double)c[i];
 }
 
-// R = B - H X  for m right-hand sides (row-major n x m), one warp per (row, rhs)
+// R = B - H X for m right-hand sides (row-major n x m): one warp per row of H,
+// 8 right-hand sides per pass, lanes stride over the row.
 __global__ void __launch_bounds__(256) k_residual_multi(const double* __restrict__ H, int64_t n, int64_t ldh,
                                                         const double* __restrict__ X, const double* __restrict__ Bm,
                                                         int64_t m, double* __restrict__ R) {
   int lane = threadIdx.x & 31;
-  int64_t wrp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (wrp >= n * m) return;
-  int64_t row = wrp / m, j = wrp % m;
-  double acc = 0.0;
-  for (int64_t t = lane; t < n; t += 32) acc = fma(H[row * ldh + t], X[t * m + j], acc);
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const double* hr = H + row * ldh;
+  for (int64_t j0 = 0; j0 < m; j0 += 8) {
+    int q = (int)((m - j0) < 8 ? (m - j0) : 8);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t t = lane; t < n; t += 32) {
+      double h = hr[t];
+      const double* xr = X + t * m + j0;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) R[row * m + j] = Bm[row * m + j] - acc;
+      for (int u = 0; u < 8; ++u)
+        if (u < q) acc[u] = fma(h, xr[u], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double v = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0 && u < q) R[row * m + j0 + u] = Bm[row * m + j0 + u] - v;
+    }
+  }
 }
 
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
@@ -358,7 +437,7 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int
       if (m == 1) {
         RBF_TRY(symv_residual(H, n, ldh, X, bb.as<double>(), Rr, s));
       } else {
-        unsigned nw = (unsigned)((tot * 32 + 255) / 256);
+        unsigned nw = (unsigned)((n * 32 + 255) / 256);
         { k_residual_multi<<<nw, 256, 0, s>>>(H, n, ldh, X, bb.as<double>(), m, Rr); ::rbf::note_launch(); }
         RBF_CUDA(cudaGetLastError());
       }

@@ -422,6 +422,27 @@ __global__ void k_gather_inv_block(const double* __restrict__ X, int64_t k, cons
   P[e] = 0.5 * (X[(int64_t)pos[uu] * k + v] + X[(int64_t)pos[v] * k + uu]);
 }
 
+// Count the entering centers (lpos[0 .. *e_count)) that left some earlier block.
+// The list length is only known on the device here, so it is read from
+// e_count; both indirections are range-checked.
+__global__ void k_count_departed(const int32_t* __restrict__ ids, int64_t a, const int32_t* __restrict__ lpos,
+                                 const int32_t* __restrict__ e_count, const int32_t* __restrict__ departed,
+                                 int64_t M, int32_t* __restrict__ count) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= *e_count) return;
+  int32_t l = lpos[u];
+  if (l < 0 || l >= a) return;
+  int32_t id = ids[l];
+  if (id < 0 || id >= M) return;
+  if (departed[id]) atomicAdd(count, 1);
+}
+
+__global__ void k_mark_departed(const int32_t* __restrict__ ids, const int32_t* __restrict__ lpos, int64_t d,
+                                int32_t* __restrict__ departed) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < d) departed[ids[lpos[u]]] = 1;
+}
+
 __global__ void k_w_add(double* __restrict__ w, const int32_t* __restrict__ A, int64_t a,
                         const double* __restrict__ delta) {
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -561,7 +582,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_CUDA(cudaStreamSynchronize(s));
   const int64_t an = (int64_t)((int32_t*)hs)[0];
   if (an == 0) return RBF_OK;
-  int64_t d = 0, sN = 0, e = an;
+  int64_t d = 0, sN = 0, e = an, e_returning = 0;
   if (ap > 0) {
     { k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 0, flD); ::rbf::note_launch(); }
     { k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 1, flS); ::rbf::note_launch(); }
@@ -583,13 +604,22 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     { k_list_from_flags<<<nblk(an), 256, 0, s>>>(flSn.as<int32_t>(), fpSn, an, Sn.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     int32_t* h32 = (int32_t*)hs;
+    // entering centers that left some earlier block (their stored covariance may be coupled)
+    Buf& cnt = c->scratch(53);
+    RBF_TRY(cnt.ensure(sizeof(int32_t)));
+    RBF_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
+    { k_count_departed<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, El.as<int32_t>(), fpE + an,
+                                                 c->departed.as<int32_t>(), M, cnt.as<int32_t>()); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
     RBF_CUDA(cudaMemcpyAsync(h32 + 0, fpD + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaMemcpyAsync(h32 + 1, fpS + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaMemcpyAsync(h32 + 2, fpE + an, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaMemcpyAsync(h32 + 3, cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaStreamSynchronize(s));
     d = h32[0];
     sN = h32[1];
     e = h32[2];
+    e_returning = h32[3];
     if (sN + e != an || sN + d != ap) return fail(RBF_ECUDA, "inconsistent active-set bookkeeping");
   } else {
     // every new center enters
@@ -658,7 +688,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     if (mixed) {
       // X = H_prev^{-1} E_D by refined solves with the float32 factor; P_DD = X[D, :]
       RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(), ap,
-                          Y.as<double>(), d, c->refine_sweeps, s));
+                          Y.as<double>(), d, c->refine_sweeps_cov, s));
       { k_gather_inv_block<<<nblk(d * d), 256, 0, s>>>(Y.as<double>(), d, Dl.as<int32_t>(), Pdd.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {
@@ -698,7 +728,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
 
   // 6. entering centers: inverse of their stored covariance block
   if (e > 0) {
-    if (!c->pg_on) {
+    if (!c->pg_on || e_returning == 0) {
+      // never-departed centers keep the prior P = I / lambda with no coupling
       { k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {
@@ -707,7 +738,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       { k_gather_global<<<nblk(e * e), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
                                                    El.as<int32_t>(), e, Gb.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
-      RBF_TRY(spd_inverse(c, Gb.as<double>(), e, s, 43));
+      if (e <= 64) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), e, s));
+      else RBF_TRY(spd_inverse(c, Gb.as<double>(), e, s, 43));
       { k_scatter_sym<<<nblk(e * e), 256, 0, s>>>(Gb.as<double>(), e, e, El.as<int32_t>(), Hn.as<double>(),
                                                 ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
@@ -773,6 +805,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       c->pg_on = true;
     }
     { k_pg_zero<<<nblk(d * M), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    { k_mark_departed<<<nblk(d), 256, 0, s>>>(c->A.as<int32_t>(), Dl.as<int32_t>(), d, c->departed.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     { k_pg_block<<<nblk(d * d), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d,
                                            Pdd.as<double>()); ::rbf::note_launch(); }
@@ -901,7 +935,7 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
     RBF_CUDA(cudaGetLastError());
     if (c->cfg.update_precision == RBF_UPDATE_MIXED) {
       RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(), c->a,
-                          Y.as<double>(), ka, c->refine_sweeps, s));
+                          Y.as<double>(), ka, c->refine_sweeps_cov, s));
       { k_gather_inv_block<<<nblk(ka * ka), 256, 0, s>>>(Y.as<double>(), ka, lb.as<int32_t>(), Paa.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {

@@ -50,6 +50,8 @@ class RbfConfig(ctypes.Structure):
         ("mesh_nx", ctypes.c_int32),
         ("mesh_ny", ctypes.c_int32),
         ("r_kd", ctypes.c_double),
+        ("refine_sweeps", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -142,7 +144,7 @@ class Terrain:
 
     def __init__(self, kernel=KERNEL_WENDLAND, rho=0.6, sigma=0.04, cutoff_mult=4.0, lam=1e-3,
                  update_precision=UPDATE_FP64, loss=LOSS_HUBER, huber_delta=0.05, lambda_m=1.0,
-                 wheel_offset=0.0, mesh=None, r_kd=0.1, min_count=1):
+                 wheel_offset=0.0, mesh=None, r_kd=0.1, min_count=1, refine_sweeps=0):
         self.lib = load()
         cfg = RbfConfig()
         cfg.kernel = kernel
@@ -159,6 +161,7 @@ class Terrain:
         x0, y0, h, nx, ny = mesh if mesh is not None else (0.0, 0.0, 1.0, 1, 1)
         cfg.mesh_x0, cfg.mesh_y0, cfg.mesh_h, cfg.mesh_nx, cfg.mesh_ny = x0, y0, h, nx, ny
         cfg.r_kd = r_kd
+        cfg.refine_sweeps = refine_sweeps
         self.cfg = cfg
         self.device = torch.cuda.current_device()
         h_ = ctypes.c_void_p()
