@@ -265,8 +265,52 @@ def run_ours(args, ws, rank, local):
     T.profile(False)
     eval_ms = float(np.median(ev))
     T.close()
+
+    # ----- batched patches (256 independent terrains, update + evaluation) -----
+    batch = None
+    if args.batch_patches > 0:
+        import ctypes
+        TB = N.Terrain(rho=0.6, lam=1e-3, update_precision=prec)
+        arr = (N.RbfPatch * args.batch_patches)()
+        keep = []
+        npts = 0
+        for k in range(args.batch_patches):
+            sp = W.config4_patch(k)
+            M = sp["M"]
+            gx = int(math.ceil(math.sqrt(M)))
+            pts = torch.tensor(sp["points"].astype(np.float32), device=dev)
+            q = pts[:, :2].contiguous()
+            w = torch.empty(M, dtype=torch.float64, device=dev)
+            hh = torch.empty(q.shape[0], device=dev)
+            gg = torch.empty(q.shape[0], 2, device=dev)
+            keep.append((pts, q, w, hh, gg))
+            d = arr[k]
+            d.x0, d.y0, d.spacing, d.nx, d.M = 0.0, 0.0, 0.2, gx, M
+            d.n, d.Q = pts.shape[0], q.shape[0]
+            d.pts, d.q, d.w, d.h, d.grad = pts.data_ptr(), q.data_ptr(), w.data_ptr(), hh.data_ptr(), gg.data_ptr()
+            npts += pts.shape[0]
+        for _ in range(3):  # eager (sizes workspaces), capture, replay
+            TB.batch_update_eval_into(arr, args.batch_patches)
+        torch.cuda.synchronize()
+        bt = []
+        for r in range(3):
+            flush.fill_(float(r))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            TB.batch_update_eval_into(arr, args.batch_patches)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bt.append(e0.elapsed_time(e1))
+        bms = float(np.median(bt))
+        batch = {"workload": f"{args.batch_patches} patches: M log-uniform 64-4096, n log-uniform 500-50000; "
+                             "update from the prior + h/grad h at the patch points, one graph launch",
+                 "ms_per_batch": bms, "patches_per_s": args.batch_patches / (bms * 1e-3),
+                 "points_per_s": npts / (bms * 1e-3)}
+        TB.close()
     return dict(times=times, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, prof=prof,
-                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q)
+                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch)
 
 
 # ---------------------------------------------------------------------------
@@ -326,10 +370,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--eval-log2", type=int, default=26)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--batch-patches", type=int, default=256, help="patches of the batched measurement (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -392,6 +437,7 @@ def main():
                               "frac": eval_gbs / pk["hbm_gbs"], "traffic": None,
                               "bytes_per_query": 20, "peak_kind": pk_kind}},
         "stage_ms_per_step": stage_ms,
+        "batch": r["batch"],
         "clocks": r["clocks"],
         "cpu_baseline": cpu,
     }

@@ -185,6 +185,36 @@ rbf_status rbf_get_neighbors(rbf_ctx* ctx, const float* pts, int64_t n, double n
                              int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz_out,
                              void* stream);
 
+/* One terrain patch of a batch (lattice centers, see rbf_batch_update_eval). */
+typedef struct rbf_patch {
+  double x0, y0;      /* center id = j * nx + i sits at */
+  double spacing;     /*   (x0 + (i + 0.5) spacing, y0 + (j + 0.5) spacing) */
+  int32_t nx;         /* nodes per lattice row */
+  int32_t pad0;
+  int64_t M;          /* the patch's centers are ids 0 .. M-1 (rows of nx, the last may be partial) */
+  int64_t n;          /* points (world frame), device float32 n x 3 */
+  const float* pts;
+  int64_t Q;          /* queries, device float32 Q x 2 */
+  const float* q;
+  double* w;          /* out: device float64 M weights */
+  float* h;           /* out: device float32 Q heights */
+  float* grad;        /* out: device float32 Q x 2 gradients (may be NULL) */
+} rbf_patch;
+
+/* A batch of independent terrain patches (no counterpart beyond Sec. III:
+ * every patch is its own terrain model).  For every patch: prior w = 0,
+ * P = I / lambda; one recursive update with its n points (Sec. III-C; from
+ * the prior this equals batch ridge, Sec. III-B); then h and grad h at its Q
+ * queries (Eq. RBF_fml).  The context supplies the kernel parameters and the
+ * update precision; its own centers and state are not used or changed.
+ * The regression rows use noise 0 (sigma~ = sigma for the Gaussian kernel).
+ * patches: host array of npatch descriptors (device pointers inside).  The
+ * patches run concurrently on internal streams forked from `stream`; the
+ * whole batch is recorded once into a CUDA graph per distinct batch shape and
+ * replayed.  The call synchronizes at its end and returns RBF_ENOTSPD or
+ * RBF_EINVAL (non-finite point) if any patch failed. */
+rbf_status rbf_batch_update_eval(rbf_ctx* ctx, const rbf_patch* patches, int32_t npatch, void* stream);
+
 /* Stage timing.  While enabled, every call records CUDA events on its own
  * stream around each stage below and adds the stage's algorithmic work
  * (floating-point operations, or bytes for the memory-bound stages).

@@ -579,6 +579,7 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   if (!c) return RBF_OK;
   Ctx* x = C(c);
   cudaDeviceSynchronize();
+  batch_destroy(x);
   Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2,
                  &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
   for (Buf* b : bufs) b->release();

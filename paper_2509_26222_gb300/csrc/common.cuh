@@ -113,6 +113,8 @@ struct Ctx {
   // host pinned staging for small readbacks
   int64_t* host_small = nullptr;
 
+  void* batch = nullptr;  // state of rbf_batch_update_eval (streams, workspaces, graphs)
+
   // stage timing (rbf_profile_enable)
   bool prof = false;
   struct Mark {
@@ -240,6 +242,9 @@ rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Z
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
                        int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s);
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
+rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
+                      cudaStream_t s);
+void batch_destroy(Ctx* c);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,
                          const double* b, double* r, cudaStream_t s);
 

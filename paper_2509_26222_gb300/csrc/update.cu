@@ -469,8 +469,8 @@ static RowParams row_params(const rbf_config& cfg, double noise) {
 // Solve H x = b with the Cholesky factor L (x overwrites b).  In mixed mode
 // the factor is only single-precision accurate, so the solution is refined
 // with float64 residuals r = b - H x until the correction stops shrinking.
-static rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld,
-                             double* b, bool refine, cudaStream_t s) {
+rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
+                      cudaStream_t s) {
   if (!refine) {
     RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, false, s));
     RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, true, s));

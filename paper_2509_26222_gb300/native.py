@@ -55,6 +55,25 @@ class RbfConfig(ctypes.Structure):
     ]
 
 
+class RbfPatch(ctypes.Structure):
+    """Mirror of ``rbf_patch`` in include/rbfgb.h."""
+    _fields_ = [
+        ("x0", ctypes.c_double),
+        ("y0", ctypes.c_double),
+        ("spacing", ctypes.c_double),
+        ("nx", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
+        ("M", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+        ("pts", ctypes.c_void_p),
+        ("Q", ctypes.c_int64),
+        ("q", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("h", ctypes.c_void_p),
+        ("grad", ctypes.c_void_p),
+    ]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -77,6 +96,7 @@ _SIGS = {
     "rbf_profile_enable": [_P, ctypes.c_int],
     "rbf_profile_read": [_P, _P, _P, _P, ctypes.c_int],
     "rbf_launch_count": [ctypes.POINTER(_I64)],
+    "rbf_batch_update_eval": [_P, _P, ctypes.c_int32, _P],
 }
 
 STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward"]
@@ -251,6 +271,36 @@ class Terrain:
         _check(self.lib.rbf_soft_cost_backward(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], _ptr(g),
                                                _ptr(dw), _ptr(dc), _ptr(dpose), _stream()))
         return dw, dc, dpose
+
+    # -- batched patches --------------------------------------------------
+    def batch_update_eval(self, patches):
+        """patches: list of dicts with keys x0, y0, spacing, nx, M, pts (device n x 3
+        float32), q (device Q x 2 float32).  Returns a list of (w, h, grad) device
+        tensors.  Each patch is its own terrain updated once from the prior."""
+        arr = (RbfPatch * len(patches))()
+        outs = []
+        keep = []
+        for k, p in enumerate(patches):
+            pts = _dev_tensor(p["pts"], torch.float32, 3)
+            q = _dev_tensor(p["q"], torch.float32, 2)
+            M = int(p["M"])
+            w = torch.empty(M, dtype=torch.float64, device=pts.device)
+            h = torch.empty(q.shape[0], dtype=torch.float32, device=pts.device)
+            g = torch.empty(q.shape[0], 2, dtype=torch.float32, device=pts.device)
+            keep += [pts, q]
+            outs.append((w, h, g))
+            d = arr[k]
+            d.x0, d.y0, d.spacing, d.nx = float(p["x0"]), float(p["y0"]), float(p["spacing"]), int(p["nx"])
+            d.M, d.n, d.Q = M, pts.shape[0], q.shape[0]
+            d.pts, d.q = pts.data_ptr(), q.data_ptr()
+            d.w, d.h, d.grad = w.data_ptr(), h.data_ptr(), g.data_ptr()
+        _check(self.lib.rbf_batch_update_eval(self._h, ctypes.cast(arr, ctypes.c_void_p), len(patches), _stream()))
+        self._batch_keep = keep
+        return outs
+
+    def batch_update_eval_into(self, arr, count):
+        """Run a prepared RbfPatch array (buffers owned by the caller)."""
+        _check(self.lib.rbf_batch_update_eval(self._h, ctypes.cast(arr, ctypes.c_void_p), count, _stream()))
 
     # -- stage timing -----------------------------------------------------
     def profile(self, on=True):

@@ -299,3 +299,44 @@ def test_status_codes(N):
     buf = torch.empty(3, dtype=torch.int32, device="cuda")
     st = T.lib.rbf_get_active(T._h, ctypes.c_void_p(buf.data_ptr()), 3, ctypes.byref(a), None)
     assert st == -7 and a.value == 256
+
+
+# ---------------------------------------------------------------------------
+# batched patches (independent terrains, update from the prior + evaluation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_patches_match_oracle_and_replay(N, prec):
+    ids = [3, 17, 42, 77, 101, 150]
+    specs = [W.config4_patch(pid, m_hi=900, n_hi=6000) for pid in ids]
+    T = N.Terrain(rho=0.6, update_precision=prec)
+    # descriptors with caller-owned buffers, so repeated calls see the same shape
+    import ctypes
+    arr = (N.RbfPatch * len(specs))()
+    bufs = []
+    for k, sp in enumerate(specs):
+        M = sp["M"]
+        gx = int(math.ceil(math.sqrt(M)))
+        pts = dev(sp["points"].astype(np.float32))
+        q = dev(sp["points"][:, :2].astype(np.float32)[::3].copy())
+        w = torch.empty(M, dtype=torch.float64, device="cuda")
+        h = torch.empty(q.shape[0], dtype=torch.float32, device="cuda")
+        g = torch.empty(q.shape[0], 2, dtype=torch.float32, device="cuda")
+        bufs.append((pts, q, w, h, g))
+        d = arr[k]
+        d.x0, d.y0, d.spacing, d.nx, d.M = 0.0, 0.0, 0.2, gx, M
+        d.n, d.Q = pts.shape[0], q.shape[0]
+        d.pts, d.q, d.w, d.h, d.grad = pts.data_ptr(), q.data_ptr(), w.data_ptr(), h.data_ptr(), g.data_ptr()
+    results = []
+    for call in range(3):  # eager, captured, replayed
+        T.batch_update_eval_into(arr, len(specs))
+        torch.cuda.synchronize()
+        results.append([(b[2].cpu().numpy().copy(), b[3].cpu().numpy().copy()) for b in bufs])
+    for call in (1, 2):
+        for (w0, h0), (w1, h1) in zip(results[0], results[call]):
+            assert np.array_equal(w0, w1) and np.array_equal(h0, h1)
+    for sp, (pts, q, w, h, g) in zip(specs, bufs):
+        p64 = sp["points"].astype(np.float32).astype(np.float64)
+        ref = O.batch_ridge(p64, sp["centers"], 1e-3, O.WENDLAND, rho=0.6)
+        assert rel_inf(w.cpu().numpy(), ref) < F64_TOL
+        qq = q.cpu().numpy().astype(np.float64)
+        check_eval(h, g, O.eval_h(qq, sp["centers"], ref, O.WENDLAND, rho=0.6))
