@@ -55,6 +55,18 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Maximum of a per-rank value over the process group (identity when no
+    group is initialized); device None means a CPU (gloo) tensor."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,11 +205,7 @@ def run_ours(args, ws, rank, local):
     launches = N.launch_count() - l0
     prof = T.profile_read(reset=True)
     T.profile(False)
-    total_ms = float(sum(times))
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), dev)
     a_last = int(T.active().numel())
 
     # ----- end to end through host buffers -----
@@ -394,24 +402,38 @@ def main():
     K = len(r["times"])
     value = ws * K / (r["total_ms"] * 1e-3)
     prof = r["prof"]
-    # dominant kernel stage of the step
-    kstages = ["trailing", "panel", "solve", "assembly", "block", "neighbors", "eval", "softcost"]
-    dom = max(kstages, key=lambda s: prof[s][0])
+    # Roofline of the dominant kernel class of the step, timed per launch by
+    # the library's event timing: the float32 sync-free solve (FP32 ALU
+    # roofline), the tensor-core trailing update (BF16 tensor roofline) or
+    # the evaluation (HBM roofline).  FP32 peak: 152 SMs x 128 lanes x 2 flops
+    # x 2.07 GHz.
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    cand = {"trsm32": ("alu", fp32_peak, "FP32 CUDA cores, 152 SM x 128 lanes x 2 x 2.07 GHz"),
+            "trailing": ("tensor", pk["bf16_tflops_sustained"], "bf16 sustained (" + pk_kind + "), 6 bf16 products"),
+            "eval": ("hbm", pk["hbm_gbs"], pk_kind)}
+    dom = max(cand, key=lambda s: prof[s][0])
     ms, work, cnt = prof[dom]
+    bound, peak, pkind = cand[dom]
     roof = None
-    if dom in ("trailing", "panel", "solve") and ms > 0:
-        tf = work / (ms * 1e-3) / 1e12
-        prec_mixed = args.precision == "mixed" and dom == "trailing"
-        peak = pk["bf16_tflops_sustained"] if prec_mixed else FP64_NOMINAL_TFLOPS
-        roof = {"kernel": dom, "bound": "tensor" if prec_mixed else "alu", "achieved": tf, "peak": peak,
-                "unit": "TFLOP/s", "frac": tf / peak, "traffic": None,
-                "peak_kind": ("bf16 sustained, " + pk_kind) if prec_mixed else "FP64 nominal 1.25 TFLOP/s (recipe)",
-                "launches": int(cnt), "ms_per_launch": ms / max(cnt, 1),
-                "flops_per_launch": work / max(cnt, 1)}
-    elif ms > 0:
-        gbs = work / (ms * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind}
+    if ms > 0:
+        if bound == "hbm":
+            ach = work / (ms * 1e-3) / 1e9
+            unit = "GB/s"
+        else:
+            flops = work * (6.0 if dom == "trailing" else 1.0)
+            ach = flops / (ms * 1e-3) / 1e12
+            unit = "TFLOP/s"
+        roof = {"kernel": {"trsm32": "k_trsm32", "trailing": "k_syrk_tc", "eval": "k_eval"}[dom], "bound": bound,
+                "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak, "traffic": None,
+                "peak_kind": pkind, "launches": int(cnt), "ms_per_launch": ms / max(cnt, 1),
+                "work_per_launch": work / max(cnt, 1)}
+    trail = prof["trailing"]
+    roof_tc = None
+    if trail[0] > 0:
+        tf = 6.0 * trail[1] / (trail[0] * 1e-3) / 1e12
+        roof_tc = {"kernel": "k_syrk_tc", "bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops_sustained"],
+                   "unit": "TFLOP/s", "frac": tf / pk["bf16_tflops_sustained"], "launches": int(trail[2]),
+                   "ms_per_launch": trail[0] / max(trail[2], 1)}
     eval_qps = r["Q"] / (r["eval_ms"] * 1e-3)
     eval_gbs = 20.0 * eval_qps / 1e9
     stage_ms = {s: round(prof[s][0] / K, 4) for s in prof}
@@ -432,6 +454,7 @@ def main():
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": int(r["launches"]),
         "roofline": roof,
+        "roofline_tensor_update": roof_tc,
         "eval": {"queries_per_s": eval_qps * ws, "Q": r["Q"], "ms": r["eval_ms"],
                  "roofline": {"bound": "hbm", "achieved": eval_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                               "frac": eval_gbs / pk["hbm_gbs"], "traffic": None,

@@ -232,7 +232,9 @@ enum {
   RBF_STAGE_EVAL = 6,       /* rbf_eval (bytes: 8 in + 12 out per query) */
   RBF_STAGE_SOFTCOST = 7,   /* rbf_soft_cost (bytes: 12 in per point) */
   RBF_STAGE_BACKWARD = 8,   /* rbf_soft_cost_backward (bytes: 12 in + 12 out) */
-  RBF_NSTAGE = 9
+  RBF_STAGE_TRSM32 = 9,     /* float32 sync-free triangular solves, one interval per launch
+                               (flops: n^2 per right-hand side), nested inside SOLVE/BLOCK */
+  RBF_NSTAGE = 10
 };
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int on);
 /* Number of CUDA kernels librbfgb.so has launched since it was loaded (all

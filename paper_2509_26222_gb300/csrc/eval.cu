@@ -284,9 +284,12 @@ __global__ void __launch_bounds__(256) k_eval_lattice_win(LatWParams P, const fl
     __syncthreads();
   }
   const u64 one2 = pk2(1.f, 1.f), four2 = pk2(4.f, 4.f), mone2 = pk2(-1.f, -1.f);
-  for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < Q;
-       qi += (int64_t)gridDim.x * blockDim.x) {
-    float2 p = q[qi];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float2 pnext = qi < Q ? __ldcs(q + qi) : make_float2(0.f, 0.f);
+  for (; qi < Q; qi += stride) {
+    float2 p = pnext;
+    if (qi + stride < Q) pnext = __ldcs(q + qi + stride);  // next query in flight during this one
     if (!(isfinite(p.x) && isfinite(p.y))) {
       float nan = __int_as_float(0x7fc00000);
       h[qi] = nan;

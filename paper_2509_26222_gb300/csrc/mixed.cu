@@ -237,9 +237,9 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
 
 // ---------------------------------------------------------------------------
 // float32 sync-free triangular solve (block 64) with the stored inverses of
-// the diagonal blocks: op(L) X = B for up to 48 right-hand sides per launch.
+// the diagonal blocks: op(L) X = B for up to 160 right-hand sides per launch.
 // ---------------------------------------------------------------------------
-constexpr int T32_MC = 48;
+constexpr int T32_MC = 160;
 constexpr long long T32_SPIN = 1LL << 22;
 
 __device__ __forceinline__ int ld_acq(const int* p) {
@@ -254,8 +254,10 @@ __device__ __forceinline__ void st_rel(int* p, int v) {
 __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int64_t ldl, int64_t n,
                                                 const float* __restrict__ Zd, float* B, int64_t ldb, int c0,
                                                 int mc, bool transpose, int* flags, int epoch, int* status) {
-  __shared__ float acc[MB][T32_MC + 1];
-  __shared__ float Xs[MB][T32_MC + 1];
+  // acc and Xs (64 x (T32_MC + 1) floats each) in dynamic shared memory
+  extern __shared__ float t32_dyn[];
+  float (*acc)[T32_MC + 1] = reinterpret_cast<float (*)[T32_MC + 1]>(t32_dyn);
+  float (*Xs)[T32_MC + 1] = reinterpret_cast<float (*)[T32_MC + 1]>(t32_dyn + MB * (T32_MC + 1));
   __shared__ float Zs[MB][MB + 1];
   __shared__ int bail;
   const int tid = threadIdx.x, ti = tid >> 2, tg = tid & 3;
@@ -342,10 +344,12 @@ rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Z
     c->epoch = 0;
   }
   static int max_blocks[64] = {0};
+  const size_t dyn = (size_t)2 * MB * (T32_MC + 1) * sizeof(float);
   int dev = c->device & 63;
   if (!max_blocks[dev]) {
     int per_sm = 0, sms = 0;
-    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsm32, 256, 0));
+    RBF_CUDA(cudaFuncSetAttribute(k_trsm32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsm32, 256, dyn));
     RBF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     max_blocks[dev] = per_sm * sms;
   }
@@ -359,7 +363,8 @@ rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Z
     int c0i = (int)c0;
     void* args[] = {(void*)&L, (void*)&ldl, (void*)&n, (void*)&Zd, (void*)&B, (void*)&ldb, (void*)&c0i,
                     (void*)&mc, (void*)&transpose, (void*)&flags, (void*)&epoch, (void*)&status};
-    RBF_CUDA(cooperative_launch((const void*)k_trsm32, dim3((unsigned)grid), dim3(256), args, 0, s));
+    StageTimer st(c, RBF_STAGE_TRSM32, s, (double)n * (double)n * (double)mc);
+    RBF_CUDA(cooperative_launch((const void*)k_trsm32, dim3((unsigned)grid), dim3(256), args, dyn, s));
   }
   return RBF_OK;
 }

@@ -283,8 +283,16 @@ __global__ void __launch_bounds__(256) k_tsort(const int64_t* __restrict__ tstar
 
 // One warp per active row l1: H'[l1, :] += sum_i m_{i,l1} m_{i,:} (row of
 // m~ m~^T, accumulated in shared memory in ascending point order) and
-// u[l1] = sum_i m_{i,l1} e_i.  The metadata of 32 entries is fetched by the
-// 32 lanes at once, then the entries are applied one after the other.
+// u[l1] = sum_i m_{i,l1} e_i.  Entries go in groups of GR_G: the neighbour
+// lists of a group are first staged in shared memory with all their loads in
+// flight, then applied one entry after the other (same order as before).
+constexpr int GR_G = 8;   // entries per staging group
+constexpr int GR_L = 64;  // staged list length (longer lists finish from global memory)
+
+__host__ __device__ constexpr int64_t gram_warp_doubles(int64_t a) {
+  return a + GR_G * GR_L + GR_G + (GR_G * GR_L + GR_G * 4 + 1) / 2 + 1;
+}
+
 __global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const int64_t* __restrict__ tstart,
                                                    const int64_t* __restrict__ tk,
                                                    const int32_t* __restrict__ tpt,
@@ -295,29 +303,64 @@ __global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const
                                                    double* __restrict__ H, double* __restrict__ u) {
   extern __shared__ double srow[];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* row = srow + (int64_t)wid * a;
+  double* row = srow + (int64_t)wid * gram_warp_doubles(a);
+  double* sval = row + a;                 // GR_G * GR_L staged values
+  double* sm1 = sval + GR_G * GR_L;       // GR_G entry weights m_{i,l1}
+  int32_t* scol = reinterpret_cast<int32_t*>(sm1 + GR_G);  // GR_G * GR_L staged columns
+  int64_t* sra = reinterpret_cast<int64_t*>(scol + GR_G * GR_L + (GR_G * GR_L) % 2);  // list starts
+  int32_t* slen = reinterpret_cast<int32_t*>(sra + GR_G);  // list lengths
   for (int64_t l1 = (int64_t)blockIdx.x * nw + wid; l1 < a; l1 += (int64_t)gridDim.x * nw) {
     for (int64_t j = lane; j < a; j += 32) row[j] = 0.0;
-    __syncwarp();
     double ue = 0.0;
     int64_t p0 = tstart[l1], p1 = tstart[l1 + 1];
-    for (int64_t pb = p0; pb < p1; pb += 32) {
-      int cnt = (int)((p1 - pb) < 32 ? (p1 - pb) : 32);
-      double m1 = 0.0;
-      int64_t ra = 0, rb = 0;
+    for (int64_t pb = p0; pb < p1; pb += GR_G) {
+      int cnt = (int)((p1 - pb) < GR_G ? (p1 - pb) : GR_G);
+      __syncwarp();
       if (lane < cnt) {
         int64_t k1 = tk[pb + lane];
         int64_t i = tpt[pb + lane];
-        m1 = val[k1];
+        double m1 = val[k1];
         ue = fma(m1, e[i], ue);
-        ra = row_ptr[i];
-        rb = row_ptr[i + 1];
+        int64_t ra = row_ptr[i], rb = row_ptr[i + 1];
+        sm1[lane] = m1;
+        sra[lane] = ra;
+        slen[lane] = (int32_t)(rb - ra);
       }
+      __syncwarp();
+      {
+        // every load of the group is issued before any store (registers first)
+        int cr[GR_G][GR_L / 32];
+        double vr[GR_G][GR_L / 32];
+#pragma unroll
+        for (int q = 0; q < GR_G; ++q) {
+#pragma unroll
+          for (int h = 0; h < GR_L / 32; ++h) {
+            int t = lane + 32 * h;
+            bool ok = q < cnt && t < slen[q];
+            cr[q][h] = ok ? lcol[sra[q] + t] : 0;
+            vr[q][h] = ok ? val[sra[q] + t] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < GR_G; ++q) {
+#pragma unroll
+          for (int h = 0; h < GR_L / 32; ++h) {
+            scol[q * GR_L + lane + 32 * h] = cr[q][h];
+            sval[q * GR_L + lane + 32 * h] = vr[q][h];
+          }
+        }
+      }
+      __syncwarp();
       for (int q = 0; q < cnt; ++q) {
-        double mq = __shfl_sync(0xffffffffu, m1, q);
-        int64_t qa = __shfl_sync(0xffffffffu, ra, q);
-        int64_t qb = __shfl_sync(0xffffffffu, rb, q);
-        for (int64_t k2 = qa + lane; k2 < qb; k2 += 32) {
+        double mq = sm1[q];
+        int len = slen[q];
+        int st = len < GR_L ? len : GR_L;
+        for (int t = lane; t < st; t += 32) {
+          int l2 = scol[q * GR_L + t];
+          row[l2] = fma(mq, sval[q * GR_L + t], row[l2]);
+        }
+        for (int64_t t = GR_L + lane; t < len; t += 32) {
+          int64_t k2 = sra[q] + t;
           int l2 = lcol[k2];
           row[l2] = fma(mq, val[k2], row[l2]);
         }
@@ -326,10 +369,10 @@ __global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ue += __shfl_xor_sync(0xffffffffu, ue, o);
+    __syncwarp();
     double* Hr = H + l1 * ldh;
     for (int64_t j = lane; j < a; j += 32) Hr[j] += row[j];
     if (lane == 0) u[l1] = ue;
-    __syncwarp();
   }
 }
 
@@ -752,7 +795,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     StageTimer st(c, RBF_STAGE_ASSEMBLY, s, 0.0);
     int dev_smem = 0;
     RBF_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    int64_t per_warp = an * (int64_t)sizeof(double);
+    int64_t per_warp = gram_warp_doubles(an) * (int64_t)sizeof(double);
     int warps = (int)((int64_t)dev_smem / per_warp);
     if (warps > 4) warps = 4;
     if (warps < 1) return fail(RBF_EINVAL, "active block of %lld centers exceeds shared memory", (long long)an);

@@ -99,7 +99,8 @@ _SIGS = {
     "rbf_batch_update_eval": [_P, _P, ctypes.c_int32, _P],
 }
 
-STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward"]
+STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward",
+          "trsm32"]
 
 
 def launch_count() -> int:
