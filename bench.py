@@ -138,6 +138,11 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
+# DRAM bytes per query of the lattice evaluation kernel, from one ncu capture
+# (2^24 uniform queries on the 64x64 lattice: 134.31 MB read + 141.67 MB written).
+EVAL_DRAM_BYTES_PER_QUERY = (134.307840e6 + 141.672192e6) / (1 << 24)
+
+
 def frame_arrays(k):
     from paper_2509_26222_gb300 import workloads as W
     ground, sensor, _ = W.config2_frame(k)
@@ -207,6 +212,33 @@ def run_ours(args, ws, rank, local):
     T.profile(False)
     total_ms = max_over_ranks(float(sum(times)), dev)
     a_last = int(T.active().numel())
+
+    # ----- the other update precision on the same frames (mixed vs FP64 comparison) -----
+    other = N.UPDATE_FP64 if prec == N.UPDATE_MIXED else N.UPDATE_MIXED
+    To = N.Terrain(rho=0.6, lam=1e-3, update_precision=other, huber_delta=0.05)
+    To.set_centers(centers)
+    To_times = []
+    for k in range(nfr):
+        if k >= args.warmup:
+            flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g, b, s = dev_frames[k]
+        To.update(g, noise=NOISE)
+        To.soft_cost(eye, s, b, out=out7)
+        To.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            To_times.append(e0.elapsed_time(e1))
+    w_a = T.weights().cpu().numpy()
+    w_b = To.weights().cpu().numpy()
+    other_line = {"update_precision": "fp64" if other == N.UPDATE_FP64 else "mixed",
+                  "frames_per_s": len(To_times) / (sum(To_times) * 1e-3),
+                  "max_rel_diff_w": float(np.max(np.abs(w_a - w_b)) / max(np.max(np.abs(w_b)), 1e-300))}
+    To.close()
 
     # ----- end to end through host buffers -----
     T2 = make_terrain()
@@ -317,8 +349,50 @@ def run_ours(args, ws, rank, local):
                  "ms_per_batch": bms, "patches_per_s": args.batch_patches / (bms * 1e-3),
                  "points_per_s": npts / (bms * 1e-3)}
         TB.close()
+    # ----- one update at 65,536 centers with an 8192-center active block -----
+    c5 = None
+    if args.c5_reps > 0:
+        c5 = {"workload": "256x256 centers @ 0.1 m, rho=0.3 m, one update from the prior by 32,768 points "
+                          "touching a 128x64 block (a=8192)"}
+        sp = W.config5(q=16)
+        c5c = torch.tensor(sp["centers"], device=dev)
+        c5p = torch.tensor(sp["points"].astype(np.float32), device=dev)
+        ws_ = {}
+        for name, pr in (("fp64", N.UPDATE_FP64), ("mixed", N.UPDATE_MIXED)):
+            T5 = N.Terrain(rho=0.3, lam=1e-3, update_precision=pr)
+            T5.set_centers(c5c)
+            T5.update(c5p, noise=0.02)
+            ut = []
+            prof5 = None
+            for r in range(args.c5_reps):
+                T5.set_centers(c5c)
+                flush.fill_(float(r))
+                torch.cuda.synchronize()
+                if r == args.c5_reps - 1:
+                    T5.profile(True)
+                    T5.profile_read(reset=True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                T5.update(c5p, noise=0.02)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ut.append(e0.elapsed_time(e1))
+                if r == args.c5_reps - 1:
+                    prof5 = T5.profile_read(reset=True)
+                    T5.profile(False)
+            ws_[name] = T5.weights().cpu().numpy()
+            a5 = int(T5.active().numel())
+            c5[name] = {"ms_per_update": float(np.median(ut)), "active": a5,
+                        "stage_ms": {k: round(v[0], 4) for k, v in prof5.items() if v[0] > 0},
+                        "trailing_flops": prof5["trailing"][1], "trailing_ms": prof5["trailing"][0]}
+            T5.close()
+        c5["max_rel_diff_w_mixed_vs_fp64"] = float(np.max(np.abs(ws_["mixed"] - ws_["fp64"])) /
+                                                  max(np.max(np.abs(ws_["fp64"])), 1e-300))
+        c5["speedup_mixed_over_fp64"] = c5["fp64"]["ms_per_update"] / c5["mixed"]["ms_per_update"]
     return dict(times=times, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, prof=prof,
-                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch)
+                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch,
+                other=other_line, c5=c5)
 
 
 # ---------------------------------------------------------------------------
@@ -383,6 +457,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--batch-patches", type=int, default=256, help="patches of the batched measurement (0: skip)")
+    ap.add_argument("--c5-reps", type=int, default=3, help="timed updates at 65,536 centers per precision (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -434,6 +509,17 @@ def main():
         roof_tc = {"kernel": "k_syrk_tc", "bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops_sustained"],
                    "unit": "TFLOP/s", "frac": tf / pk["bf16_tflops_sustained"], "launches": int(trail[2]),
                    "ms_per_launch": trail[0] / max(trail[2], 1)}
+    c5 = r["c5"]
+    if c5 is not None:
+        for name, pk_t, kind in (("mixed", pk["bf16_tflops_sustained"], "bf16 sustained, 6 bf16 products per flop"),):
+            e = c5[name]
+            if e["trailing_ms"] > 0:
+                tf = 6.0 * e["trailing_flops"] / (e["trailing_ms"] * 1e-3) / 1e12
+                e["roofline_trailing"] = {"kernel": "k_syrk_tc", "bound": "tensor", "achieved": tf, "peak": pk_t,
+                                          "unit": "TFLOP/s", "frac": tf / pk_t, "peak_kind": kind}
+            del e["trailing_flops"], e["trailing_ms"]
+        e = c5["fp64"]
+        del e["trailing_flops"], e["trailing_ms"]
     eval_qps = r["Q"] / (r["eval_ms"] * 1e-3)
     eval_gbs = 20.0 * eval_qps / 1e9
     stage_ms = {s: round(prof[s][0] / K, 4) for s in prof}
@@ -457,9 +543,13 @@ def main():
         "roofline_tensor_update": roof_tc,
         "eval": {"queries_per_s": eval_qps * ws, "Q": r["Q"], "ms": r["eval_ms"],
                  "roofline": {"bound": "hbm", "achieved": eval_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                              "frac": eval_gbs / pk["hbm_gbs"], "traffic": None,
+                              "frac": eval_gbs / pk["hbm_gbs"], "traffic": EVAL_DRAM_BYTES_PER_QUERY * r["Q"],
+                              "traffic_source": "ncu dram__bytes_read+write of k_eval_lattice_win on 2^24 "
+                                                "queries, per query, scaled to Q",
                               "bytes_per_query": 20, "peak_kind": pk_kind}},
         "stage_ms_per_step": stage_ms,
+        "other_precision_same_frames": r["other"],
+        "update_65536_centers": c5,
         "batch": r["batch"],
         "clocks": r["clocks"],
         "cpu_baseline": cpu,

@@ -61,7 +61,7 @@ GAUSSIAN = 1
 __all__ = [
     "WENDLAND", "GAUSSIAN", "phi", "grad_coef", "support_radius_eval",
     "support_radius_assembly", "fl32", "member_f32", "neighbors", "eval_h",
-    "select_centers", "design_rows", "batch_ridge", "CovStore", "BlockState",
+    "select_centers", "design_rows", "batch_ridge", "ridge_sparse", "CovStore", "BlockState",
     "block_update", "ExactState", "exact_update", "skew", "huber", "huber_psi",
     "soft_cost", "soft_cost_backward",
 ]
@@ -262,6 +262,49 @@ def batch_ridge(points_xyz, c_xy, lam, kind, rho=0.6, sigma=0.04, cutoff_mult=4.
     H = Phi.T @ Phi + lam * np.eye(Phi.shape[1])
     b = Phi.T @ p[:, 2]
     return np.linalg.solve(H, b)
+
+
+def ridge_sparse(points_xyz, c_xy, lam, kind, rho=0.6, sigma=0.04, cutoff_mult=4.0,
+                 noise=0.0, cov_ids=None):
+    """The ridge estimator of Sec. III-B with a sparse design matrix, for
+    center counts where the dense rows of ``batch_ridge`` do not fit.
+
+    Same estimator: H = sum_i m_i m_i^T + lambda I, w = H^{-1} sum_i m_i z_i.
+    The nonzeros of each row m(x_i) are the centers of the float32 neighbour
+    rule at the assembly radius (G14); their values are the FP64 regression
+    entries of ``design_rows``.  H is factored by a sparse LU (SuperLU, a
+    library primitive).  With ``cov_ids`` it also returns P[ids, ids] for
+    P = H^{-1}, which is the covariance after one update from the prior (G11).
+    """
+    from scipy.sparse import csr_matrix, identity
+    from scipy.sparse.linalg import splu
+
+    p = np.asarray(points_xyz, dtype=np.float64)
+    c = np.asarray(c_xy, dtype=np.float64)
+    n, M = p.shape[0], c.shape[0]
+    radius = support_radius_assembly(kind, rho, sigma, cutoff_mult, noise)
+    row_ptr, col = neighbors(p[:, :2], c, radius)
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    dx = p[rows, 0] - c[col, 0]
+    dy = p[rows, 1] - c[col, 1]
+    r = np.sqrt(dx * dx + dy * dy)
+    if kind == WENDLAND:
+        val = phi(r, WENDLAND, rho)
+    else:
+        st2 = sigma * sigma + noise * noise
+        val = (sigma * sigma / st2) * np.exp(-(r * r) / (2.0 * st2))
+    Phi = csr_matrix((val, col.astype(np.int64), row_ptr), shape=(n, M))
+    H = (Phi.T @ Phi + lam * identity(M, format="csr")).tocsc()
+    lu = splu(H)
+    w = lu.solve(Phi.T @ p[:, 2])
+    if cov_ids is None:
+        return w
+    ids = np.asarray(cov_ids, dtype=np.int64)
+    E = np.zeros((M, ids.size))
+    E[ids, np.arange(ids.size)] = 1.0
+    X = lu.solve(E)
+    Pk = X[ids, :]
+    return w, 0.5 * (Pk + Pk.T)
 
 
 # ---------------------------------------------------------------------------

@@ -200,6 +200,36 @@ def test_update_config2_sequence_with_departures(N, prec):
         assert rel_inf(T.cov(ids).cpu().numpy(), st.P.block(ids)) < F64_TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_update_config5_full_size(N, prec):
+    """256x256 centers at 0.1 m, rho = 0.3 m: one update by 32,768 points that
+    touch exactly the 128x64 block (a = 8192).  The oracle is the sparse ridge
+    over the block plus a 3-center margin (one update from the prior equals
+    ridge, G11); the GPU's active set must equal the oracle's."""
+    cfg = W.config5(q=16)
+    c = cfg["centers"]
+    p32 = cfg["points"].astype(np.float32)
+    i0, i1, j0, j1 = cfg["block"]
+    T = N.Terrain(rho=0.3, update_precision=prec)
+    T.set_centers(dev(c, torch.float64))
+    T.update(dev(p32), noise=0.02)
+    A = T.active().cpu().numpy()
+    gi, gj = np.meshgrid(np.arange(i0 - 3, i1 + 4), np.arange(j0 - 3, j1 + 4))
+    cand = np.sort((gj * 256 + gi).ravel())
+    p64 = p32.astype(np.float64)
+    A_ref = cand[O.active_set(p64[:, :2], c[cand], 0.3)]
+    assert A.size == 8192 and np.array_equal(A, A_ref)
+    rng = np.random.default_rng(5)
+    ids = np.sort(rng.choice(A, 48, replace=False))
+    w_ref, P_ref = O.ridge_sparse(p64, c[cand], 1e-3, O.WENDLAND, rho=0.3, cov_ids=np.searchsorted(cand, ids))
+    w = T.weights().cpu().numpy()
+    assert rel_inf(w[cand], w_ref) < F64_TOL
+    outside = np.ones(c.shape[0], bool)
+    outside[cand] = False
+    assert np.all(w[outside] == 0.0)
+    assert rel_inf(T.cov(ids).cpu().numpy(), P_ref) < F64_TOL
+
+
 def test_update_gaussian_moment_rows(N):
     rng = np.random.default_rng(9)
     c = W.grid_centers(12, 12, 0.0, 0.0, 0.07)

@@ -153,3 +153,25 @@ def test_empty_and_untouched_updates_are_noops():
     far = np.array([[10.0, 10.0, 1.0]])
     assert O.block_update(st, far).size == 0
     assert np.all(st.w == 0) and np.allclose(st.P.dense(), np.eye(16) * 1e3)
+
+
+@pytest.mark.parametrize("kind", [O.WENDLAND, O.GAUSSIAN])
+def test_sparse_ridge_equals_dense_ridge_and_inverse(kind):
+    """The sparse-design ridge (used at 65,536 centers) against the dense
+    normal equations and numpy's dense inverse; points cover only part of the
+    grid, so untouched centers must keep w = 0 and P = I / lambda."""
+    rng = np.random.default_rng(4)
+    c = W.grid_centers(16, 16, 0, 0, 0.07 if kind == O.GAUSSIAN else 0.25)
+    span = 0.6 if kind == O.GAUSSIAN else 2.5
+    p = _pts(rng, 1500, 0.0, span)
+    kw = dict(rho=0.6, sigma=0.04, cutoff_mult=4.0, noise=0.05)
+    ids = np.array([0, 5, 17, 40, 200, 255])
+    w, Pk = O.ridge_sparse(p, c, 1e-3, kind, cov_ids=ids, **kw)
+    ref = O.batch_ridge(p, c, 1e-3, kind, **kw)
+    assert rel_inf(w, ref) < 1e-9          # cond(H) is about 7e4 for the Gaussian rows
+    Phi = O.design_rows(p[:, :2], c, kind, **kw)
+    Pref = np.linalg.inv(Phi.T @ Phi + 1e-3 * np.eye(c.shape[0]))
+    assert rel_inf(Pk, Pref[np.ix_(ids, ids)]) < 1e-9
+    untouched = np.abs(Phi).sum(axis=0) == 0
+    assert untouched.any() and np.all(w[untouched] == 0.0)
+    assert Pk[-1, -1] == pytest.approx(1e3) and untouched[255]
