@@ -188,8 +188,6 @@ def run_ours(args, ws, rank, local):
         step(dev_frames[k])
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    T.profile(True)
-    T.profile_read(reset=True)
     l0 = N.launch_count()
     times = []
     if ws > 1:
@@ -208,10 +206,24 @@ def run_ours(args, ws, rank, local):
         times.append(e0.elapsed_time(e1))
     clk = clocks.stop()
     launches = N.launch_count() - l0
-    prof = T.profile_read(reset=True)
-    T.profile(False)
     total_ms = max_over_ranks(float(sum(times)), dev)
     a_last = int(T.active().numel())
+
+    # ----- the same frames again with the library's per-stage event timing on -----
+    Tp = make_terrain()
+    for k in range(nfr):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            Tp.profile(True)
+            Tp.profile_read(reset=True)
+        g, b, s = dev_frames[k]
+        Tp.update(g, noise=NOISE)
+        Tp.soft_cost(eye, s, b, out=out7)
+        Tp.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
+    torch.cuda.synchronize()
+    prof = Tp.profile_read(reset=True)
+    Tp.profile(False)
+    Tp.close()
 
     # ----- the other update precision on the same frames (mixed vs FP64 comparison) -----
     other = N.UPDATE_FP64 if prec == N.UPDATE_MIXED else N.UPDATE_MIXED
@@ -289,8 +301,6 @@ def run_ours(args, ws, rank, local):
     for _ in range(3):
         T.eval(q, out_h=hq, out_grad=gq)
     torch.cuda.synchronize()
-    T.profile(True)
-    T.profile_read(reset=True)
     ev = []
     for r in range(5):
         flush.fill_(float(r))
@@ -302,7 +312,6 @@ def run_ours(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ev.append(e0.elapsed_time(e1))
-    T.profile(False)
     eval_ms = float(np.median(ev))
     T.close()
 
@@ -477,31 +486,34 @@ def main():
     K = len(r["times"])
     value = ws * K / (r["total_ms"] * 1e-3)
     prof = r["prof"]
-    # Roofline of the dominant kernel class of the step, timed per launch by
-    # the library's event timing: the float32 sync-free solve (FP32 ALU
-    # roofline), the tensor-core trailing update (BF16 tensor roofline) or
-    # the evaluation (HBM roofline).  FP32 peak: 152 SMs x 128 lanes x 2 flops
-    # x 2.07 GHz.
+    # Roofline of the dominant kernel of the step.  Each candidate is one
+    # kernel (or one kernel pair) timed per launch by the library's event
+    # timing in the profiled pass: name -> (kernel, bound, peak, peak note,
+    # flops (or bytes) per unit of recorded work).  FP32 peak: 152 SMs x 128
+    # lanes x 2 flops x 2.07 GHz.
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    cand = {"trsm32": ("alu", fp32_peak, "FP32 CUDA cores, 152 SM x 128 lanes x 2 x 2.07 GHz"),
-            "trailing": ("tensor", pk["bf16_tflops_sustained"], "bf16 sustained (" + pk_kind + "), 6 bf16 products"),
-            "eval": ("hbm", pk["hbm_gbs"], pk_kind)}
+    fp32_note = "FP32 CUDA cores, 152 SM x 128 lanes x 2 x 2.07 GHz"
+    cand = {"trsm32": ("k_trsm32", "alu", fp32_peak, fp32_note, 1.0),
+            "invapply": ("k_inv_fwd_gemv+k_inv_bwd_gemv / k_inv_apply", "alu", fp32_peak, fp32_note, 1.0),
+            "inverse": ("k_trtri_level", "alu", fp32_peak, fp32_note, 1.0),
+            "panel": ("k_mx_step", "alu", fp32_peak, fp32_note, 1.0),
+            "trailing": ("k_syrk_tc", "tensor", pk["bf16_tflops_sustained"],
+                         "bf16 sustained (" + pk_kind + "), 6 bf16 products per flop", 6.0),
+            "eval": ("k_eval_lattice_win", "hbm", pk["hbm_gbs"], pk_kind, 1.0)}
     dom = max(cand, key=lambda s: prof[s][0])
     ms, work, cnt = prof[dom]
-    bound, peak, pkind = cand[dom]
+    kname, bound, peak, pkind, mult = cand[dom]
     roof = None
     if ms > 0:
         if bound == "hbm":
             ach = work / (ms * 1e-3) / 1e9
             unit = "GB/s"
         else:
-            flops = work * (6.0 if dom == "trailing" else 1.0)
-            ach = flops / (ms * 1e-3) / 1e12
+            ach = mult * work / (ms * 1e-3) / 1e12
             unit = "TFLOP/s"
-        roof = {"kernel": {"trsm32": "k_trsm32", "trailing": "k_syrk_tc", "eval": "k_eval"}[dom], "bound": bound,
-                "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak, "traffic": None,
-                "peak_kind": pkind, "launches": int(cnt), "ms_per_launch": ms / max(cnt, 1),
-                "work_per_launch": work / max(cnt, 1)}
+        roof = {"kernel": kname, "stage": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak, "traffic": None, "peak_kind": pkind, "launches": int(cnt),
+                "ms_per_launch": ms / max(cnt, 1), "work_per_launch": mult * work / max(cnt, 1)}
     trail = prof["trailing"]
     roof_tc = None
     if trail[0] > 0:

@@ -76,7 +76,9 @@ typedef struct rbf_config {
   int32_t refine_sweeps;    /* RBF_UPDATE_MIXED: float64 refinement sweeps of the solves with
                                the float32 factor (0 = defaults: 3 for the weights, 2 for
                                covariance blocks; n > 0: n for both; 1 = no refinement) */
-  int32_t reserved0;
+  int32_t inverse_max;      /* RBF_UPDATE_MIXED: largest active block for which the update forms
+                               L^{-1} of the float32 factor and solves by two products with it
+                               (0 = default 3072; negative = never: blocked substitution only) */
 } rbf_config;
 
 /* Create a context on the current CUDA device.  Validates cfg (positive radii,
@@ -234,7 +236,10 @@ enum {
   RBF_STAGE_BACKWARD = 8,   /* rbf_soft_cost_backward (bytes: 12 in + 12 out) */
   RBF_STAGE_TRSM32 = 9,     /* float32 sync-free triangular solves, one interval per launch
                                (flops: n^2 per right-hand side), nested inside SOLVE/BLOCK */
-  RBF_NSTAGE = 10
+  RBF_STAGE_INVERSE = 10,   /* explicit inverse of the float32 factor (flops: a^3/3) */
+  RBF_STAGE_INVAPPLY = 11,  /* solves by products with that inverse (flops: 2 a^2 per right-hand side),
+                               nested inside SOLVE/BLOCK */
+  RBF_NSTAGE = 12
 };
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int on);
 /* Number of CUDA kernels librbfgb.so has launched since it was loaded (all

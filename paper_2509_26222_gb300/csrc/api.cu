@@ -423,6 +423,7 @@ rbf_status build_center_grid(Ctx* c, cudaStream_t s) {
 rbf_status reset_update_state(Ctx* c) {
   c->a = 0;
   c->pg_on = false;
+  c->zi_valid = false;
   c->Pg.release();
   return RBF_OK;
 }
@@ -552,6 +553,7 @@ extern "C" rbf_status rbf_create(const rbf_config* cfg, rbf_ctx** out) {
   Ctx* x = C(c);
   x->cfg = *cfg;
   if (cfg->refine_sweeps > 0) x->refine_sweeps = x->refine_sweeps_cov = cfg->refine_sweeps;
+  if (cfg->inverse_max != 0) x->inv_max = cfg->inverse_max < 0 ? -1 : cfg->inverse_max;
   cudaError_t e = cudaGetDevice(&x->device);
   if (e != cudaSuccess) {
     delete c;
@@ -581,7 +583,7 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   cudaDeviceSynchronize();
   batch_destroy(x);
   Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2,
-                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
+                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   if (x->host_small) cudaFreeHost(x->host_small);

@@ -93,6 +93,9 @@ struct Ctx {
   int64_t ldH = 0;   // leading dimension of H and L
   Buf Lf;            // float32 factor of H (mixed precision), a x a, leading dimension ldw
   Buf Zd;            // float32 inverses of its 64 x 64 diagonal blocks
+  Buf Zi;            // float32 L^{-1} of the whole factor (valid when zi_valid)
+  bool zi_valid = false;
+  int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
   int64_t ldw = 0;
   int refine_sweeps = 3;      // float64 refinement sweeps of the weight solve (mixed precision)
   int refine_sweeps_cov = 2;  // ... of the covariance solves (leaving centers, rbf_get_cov)
@@ -106,7 +109,7 @@ struct Ctx {
   uint32_t epoch = 0;
 
   // scratch buffers, addressed by slot (slots 48.. are used by the scans)
-  static constexpr int NSLOT = 64;
+  static constexpr int NSLOT = 80;
   Buf ws[NSLOT];
   Buf& scratch(int i) { return ws[i < NSLOT ? i : NSLOT - 1]; }
 
@@ -240,7 +243,11 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
 rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Zd, float* B, int64_t m,
                   int64_t ldb, bool transpose, cudaStream_t s);
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
-                       int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s);
+                       const float* Zi, int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s);
+// explicit inverse of the float32 factor and solves with it (inverse.cu)
+rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
+                       cudaStream_t s);
+rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, int64_t m, cudaStream_t s);
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
                       cudaStream_t s);

@@ -1,0 +1,318 @@
+// Explicit inverse of the float32 Cholesky factor and solves by products.
+//
+// The refined solves of the mixed-precision update apply the float32 factor
+// many times per frame (the weight increment, and the covariance columns of
+// the centers that leave the active block).  A blocked substitution is a
+// chain of a/64 dependent steps per application.  For active blocks of a few
+// thousand centers it is cheaper to form Z = L^{-1} once per factorization,
+// in log2(a/64) levels of independent products, and to apply
+// H^{-1} ~ Z^T Z as two products that run on every SM at once:
+//
+//   level b (b = 128, 256, ...): for every diagonal pair of b/2-blocks
+//     [L11 0; L21 L22]^{-1} = [Z11 0; -Z22 L21 Z11  Z22]
+//   (T = L21 Z11, then Z21 = -Z22 T; Z11, Z22 come from the level below and
+//   the 64 x 64 blocks from the factorization itself).
+//
+// Z has the factor's shape (row-major, leading dimension ldz) with zeros
+// above the diagonal.  The solves are Y = Z F followed by F = Z^T Y.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rbf {
+namespace {
+
+constexpr int TG = 64;       // output tile (rows and columns)
+constexpr int TK = 32;       // K chunk staged in shared memory
+constexpr int TLD = TG + 4;  // padded row of the staged chunks
+constexpr int GEMV_M = 8;    // right-hand sides handled by the matrix-vector kernels
+
+// Element (r, c) of a row-major matrix, or of the transpose of one.
+struct Mat {
+  const float* p;
+  int64_t ld;
+  bool t;
+};
+
+// acc += A[i0 + 0..63, kb..ke) * B[kb..ke, j0 + 0..63) for rows < M and
+// columns < N; 256 threads, each a 4 x 4 block of the tile.  The next chunk
+// is fetched into registers while the current one is multiplied.
+__device__ __forceinline__ void tile_mma(float (&acc)[4][4], const Mat A, const Mat B, int64_t i0, int64_t j0,
+                                         int64_t M, int64_t N, int64_t kb, int64_t ke, float (*As)[TLD],
+                                         float (*Bs)[TLD]) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float ra[8], rb[8];
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int idx = tid + 256 * e;  // 0 .. 2047
+      int r, kk;
+      if (A.t) { r = idx & (TG - 1); kk = idx >> 6; }
+      else { kk = idx & (TK - 1); r = idx >> 5; }
+      int64_t gi = i0 + r, gk = k0 + kk;
+      ra[e] = (gi < M && gk < ke) ? (A.t ? A.p[gk * A.ld + gi] : A.p[gi * A.ld + gk]) : 0.f;
+      int cc;
+      if (B.t) { kk = idx & (TK - 1); cc = idx >> 5; }
+      else { cc = idx & (TG - 1); kk = idx >> 6; }
+      int64_t gj = j0 + cc;
+      gk = k0 + kk;
+      rb[e] = (gj < N && gk < ke) ? (B.t ? B.p[gj * B.ld + gk] : B.p[gk * B.ld + gj]) : 0.f;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int idx = tid + 256 * e;
+      int r, kk;
+      if (A.t) { r = idx & (TG - 1); kk = idx >> 6; }
+      else { kk = idx & (TK - 1); r = idx >> 5; }
+      As[kk][r] = ra[e];
+      int cc;
+      if (B.t) { kk = idx & (TK - 1); cc = idx >> 5; }
+      else { cc = idx & (TG - 1); kk = idx >> 6; }
+      Bs[kk][cc] = rb[e];
+    }
+  };
+  if (kb >= ke) return;
+  fetch(kb);
+  for (int64_t k0 = kb; k0 < ke; k0 += TK) {
+    stash();
+    __syncthreads();
+    if (k0 + TK < ke) fetch(k0 + TK);
+#pragma unroll 8
+    for (int kk = 0; kk < TK; ++kk) {
+      float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      float av[4] = {a4.x, a4.y, a4.z, a4.w};
+      float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void tile_store(const float (&acc)[4][4], float alpha, float* C, int64_t ldc, int64_t i0,
+                                           int64_t j0, int64_t M, int64_t N) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t i = i0 + ty * 4 + u;
+    if (i >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t j = j0 + tx * 4 + v;
+      if (j < N) C[i * ldc + j] = alpha * acc[u][v];
+    }
+  }
+}
+
+// Copy the 64 x 64 diagonal inverses into Z (whose other entries are zero).
+__global__ void k_inv_diag(const float* __restrict__ Zd, int64_t n, float* __restrict__ Z, int64_t ldz) {
+  int64_t q = blockIdx.x;
+  int64_t k = q * 64;
+  int kb = (int)((n - k) < 64 ? (n - k) : 64);
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    int i = e >> 6, t = e & 63;
+    if (i < kb && t <= i) Z[(k + i) * ldz + k + t] = Zd[q * 64 * 64 + e];
+  }
+}
+
+// One level of the doubling: pair p covers rows [p b, p b + b); its upper
+// half has h1 = b/2 rows, its lower half h2 = min(b/2, n - p b - b/2).
+// kind 0: T21 = L21 Z11 (Z11 lower: only k >= j contributes);
+// kind 1: Z21 = -Z22 T21 (Z22 lower: only k <= i contributes).
+__global__ void __launch_bounds__(256) k_trtri_level(int kind, int64_t b, int64_t n, const float* __restrict__ W,
+                                                     int64_t ldw, float* __restrict__ Z, int64_t ldz,
+                                                     float* __restrict__ T) {
+  __shared__ __align__(16) float As[TK][TLD];
+  __shared__ __align__(16) float Bs[TK][TLD];
+  const int64_t p = blockIdx.z;
+  const int64_t r1 = p * b, h1 = b / 2, r2 = r1 + h1;
+  const int64_t h2 = (n - r2) < h1 ? (n - r2) : h1;
+  if (h2 <= 0) return;
+  const int64_t i0 = (int64_t)blockIdx.y * TG, j0 = (int64_t)blockIdx.x * TG;
+  if (i0 >= h2 || j0 >= h1) return;
+  float acc[4][4] = {};
+  if (kind == 0) {
+    Mat A{W + r2 * ldw + r1, ldw, false};
+    Mat B{Z + r1 * ldz + r1, ldz, false};
+    tile_mma(acc, A, B, i0, j0, h2, h1, j0, h1, As, Bs);
+    tile_store(acc, 1.f, T + r2 * ldz + r1, ldz, i0, j0, h2, h1);
+  } else {
+    Mat A{Z + r2 * ldz + r2, ldz, false};
+    Mat B{T + r2 * ldz + r1, ldz, false};
+    int64_t ke = (i0 + TG) < h2 ? (i0 + TG) : h2;
+    tile_mma(acc, A, B, i0, j0, h2, h1, 0, ke, As, Bs);
+    tile_store(acc, -1.f, Z + r2 * ldz + r1, ldz, i0, j0, h2, h1);
+  }
+}
+
+// Y = Z F (forward, Z lower) or Y = Z^T F (backward) for m > GEMV_M
+// right-hand sides; F, Y row-major n x m.  blockIdx.z splits K; partial
+// products go to P[z] and are summed by k_sum_partials.
+__global__ void __launch_bounds__(256) k_inv_apply(bool backward, int64_t n, int64_t m, const float* __restrict__ Z,
+                                                   int64_t ldz, const float* __restrict__ F, float* __restrict__ P,
+                                                   int nsplit) {
+  __shared__ __align__(16) float As[TK][TLD];
+  __shared__ __align__(16) float Bs[TK][TLD];
+  const int64_t i0 = (int64_t)blockIdx.y * TG, j0 = (int64_t)blockIdx.x * TG;
+  int64_t kb = backward ? i0 : 0;
+  int64_t ke = backward ? n : ((i0 + TG) < n ? (i0 + TG) : n);
+  int64_t len = ke - kb;
+  int64_t chunk = ((len + nsplit - 1) / nsplit + TK - 1) / TK * TK;
+  int64_t sb = kb + (int64_t)blockIdx.z * chunk;
+  int64_t se = (sb + chunk) < ke ? (sb + chunk) : ke;
+  float acc[4][4] = {};
+  Mat A{Z, ldz, backward};
+  Mat B{F, m, false};
+  if (sb < se) tile_mma(acc, A, B, i0, j0, n, m, sb, se, As, Bs);
+  tile_store(acc, 1.f, P + (int64_t)blockIdx.z * n * m, m, i0, j0, n, m);
+}
+
+__global__ void k_sum_partials(const float* __restrict__ P, int nsplit, int64_t tot, float* __restrict__ Y) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  float s = 0.f;
+  for (int z = 0; z < nsplit; ++z) s += P[z * tot + e];
+  Y[e] = s;
+}
+
+// Y = Z F for m <= GEMV_M: one warp per row, lanes over the row of Z, four
+// loads of Z in flight per lane.
+__global__ void __launch_bounds__(256) k_inv_fwd_gemv(int64_t n, int m, const float* __restrict__ Z, int64_t ldz,
+                                                      const float* __restrict__ F, float* __restrict__ Y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;
+  float acc[GEMV_M];
+#pragma unroll
+  for (int j = 0; j < GEMV_M; ++j) acc[j] = 0.f;
+  const float* zr = Z + i * ldz;
+  for (int64_t k0 = lane; k0 <= i; k0 += 128) {
+    float z[4], f[4][GEMV_M];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t k = k0 + 32 * u;
+      bool ok = k <= i;
+      z[u] = ok ? zr[k] : 0.f;
+#pragma unroll
+      for (int j = 0; j < GEMV_M; ++j) f[u][j] = (ok && j < m) ? F[k * m + j] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < GEMV_M; ++j) acc[j] = fmaf(z[u], f[u][j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < GEMV_M; ++j) {
+    if (j >= m) break;
+    float v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) Y[i * m + j] = v;
+  }
+}
+
+// X = Z^T Y for m <= GEMV_M: a CTA of 32 warps owns 32 consecutive outputs
+// (one per lane, so each row of Z is read as one 128-byte segment); the warps
+// take interleaved rows k >= i0, four in flight each, and the partial sums
+// are added in shared memory.
+constexpr int BWD_WARPS = 32;
+__global__ void __launch_bounds__(BWD_WARPS * 32) k_inv_bwd_gemv(int64_t n, int m, const float* __restrict__ Z,
+                                                                 int64_t ldz, const float* __restrict__ Y,
+                                                                 float* __restrict__ X) {
+  __shared__ float part[BWD_WARPS][GEMV_M][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int64_t i = i0 + lane;
+  float acc[GEMV_M];
+#pragma unroll
+  for (int j = 0; j < GEMV_M; ++j) acc[j] = 0.f;
+  for (int64_t k0 = i0 + w; k0 < n; k0 += 4 * BWD_WARPS) {
+    float z[4], y[4][GEMV_M];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t k = k0 + BWD_WARPS * u;
+      bool ok = k < n;
+      z[u] = (ok && i < n && k >= i) ? Z[k * ldz + i] : 0.f;
+#pragma unroll
+      for (int j = 0; j < GEMV_M; ++j) y[u][j] = (ok && j < m) ? Y[k * m + j] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < GEMV_M; ++j) acc[j] = fmaf(z[u], y[u][j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < GEMV_M; ++j) part[w][j][lane] = acc[j];
+  __syncthreads();
+  if (w < GEMV_M && w < m && i < n) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < BWD_WARPS; ++q) s += part[q][w][lane];
+    X[i * m + w] = s;
+  }
+}
+
+unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
+                       cudaStream_t s) {
+  if (n <= 0) return RBF_OK;
+  Buf& tb = c->scratch(65);
+  RBF_TRY(tb.ensure((size_t)n * ldz * sizeof(float)));
+  float* T = tb.as<float>();
+  StageTimer st(c, RBF_STAGE_INVERSE, s, (double)n * n * n / 3.0);
+  RBF_CUDA(cudaMemsetAsync(Z, 0, (size_t)n * ldz * sizeof(float), s));
+  { k_inv_diag<<<cdiv(n, 64), 256, 0, s>>>(Zd, n, Z, ldz); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  for (int64_t b = 128; b / 2 < n; b *= 2) {
+    int64_t h = b / 2;
+    dim3 grid(cdiv(h, TG), cdiv(h, TG), cdiv(n, b));
+    for (int kind = 0; kind < 2; ++kind) {
+      { k_trtri_level<<<grid, 256, 0, s>>>(kind, b, n, W, ldw, Z, ldz, T); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    }
+  }
+  return RBF_OK;
+}
+
+rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, int64_t m, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return RBF_OK;
+  Buf& yb = c->scratch(66);
+  RBF_TRY(yb.ensure((size_t)n * m * sizeof(float)));
+  float* Y = yb.as<float>();
+  StageTimer st(c, RBF_STAGE_INVAPPLY, s, 2.0 * (double)n * n * m);
+  if (m <= GEMV_M) {
+    { k_inv_fwd_gemv<<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Z, ldz, F, Y); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    { k_inv_bwd_gemv<<<cdiv(n, 32), BWD_WARPS * 32, 0, s>>>(n, (int)m, Z, ldz, Y, F); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    return RBF_OK;
+  }
+  int64_t tiles = (int64_t)cdiv(n, TG) * cdiv(m, TG);
+  int nsplit = (int)(2 * 152 / tiles);
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > 8) nsplit = 8;
+  Buf& pb = c->scratch(67);
+  RBF_TRY(pb.ensure((size_t)nsplit * n * m * sizeof(float)));
+  float* P = pb.as<float>();
+  dim3 grid(cdiv(m, TG), cdiv(n, TG), nsplit);
+  unsigned nr = cdiv(n * m, 256);
+  { k_inv_apply<<<grid, 256, 0, s>>>(false, n, m, Z, ldz, F, P, nsplit); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  { k_sum_partials<<<nr, 256, 0, s>>>(P, nsplit, n * m, Y); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  { k_inv_apply<<<grid, 256, 0, s>>>(true, n, m, Z, ldz, Y, P, nsplit); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  { k_sum_partials<<<nr, 256, 0, s>>>(P, nsplit, n * m, F); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}
+
+}  // namespace rbf

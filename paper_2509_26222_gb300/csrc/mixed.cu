@@ -34,93 +34,178 @@ __global__ void k_mx_to_f32(const double* __restrict__ H, int64_t ldh, int64_t n
   W[i * ldw + j] = (float)H[i * ldh + j];
 }
 
-// Cholesky of the 64 x 64 diagonal block (float32, one CTA of 256 threads),
-// right-looking with one barrier per column: every thread computes the
-// pivot's reciprocal square root itself, the trailing update uses
-// T_ik -= T_ij T_kj / T_jj with unscaled columns, and the columns are scaled
-// once at the end.  rd[j] = 1 / L_jj is kept for the panel solve.
-__global__ void __launch_bounds__(256) k_mx_diag(float* __restrict__ W, int64_t ldw, int64_t k, int kb,
-                                                 float* __restrict__ rd_out, int* __restrict__ flag) {
-  __shared__ float T[MB][MB + 1];
-  __shared__ float rv[MB];
-  const int tid = threadIdx.x;
+// ---------------------------------------------------------------------------
+// One block column of the factorization in one launch.  Every CTA factors the
+// 64 x 64 diagonal tile W_kk itself (L_kk, and Z_kk = L_kk^{-1}), then
+// computes its 64 panel rows L_ik = W_ik Z_kk^T as a small matrix product,
+// writes them to W and as three bfloat16 slices for the tensor-core trailing
+// update.  CTA 0 stores Z_kk for the triangular solves.  Repeating the 64 x 64
+// factorization in every CTA replaces a separate launch and a row-by-row
+// substitution with work that runs in parallel on otherwise idle SMs.
+//
+// The 64 x 64 factorization is blocked 2 x 2 with 32 x 32 blocks:
+//   L11 = chol(A11), Z11 = L11^{-1}           (one warp, registers + shuffles)
+//   L21 = A21 Z11^T, S = A22 - L21 L21^T      (all warps)
+//   L22 = chol(S),   Z22 = L22^{-1}           (one warp)
+//   Z21 = -Z22 (L21 Z11)                      (all warps)
+// The diagonal tile of W itself is left as it was: the solves read the
+// diagonal blocks only through Z.
+// ---------------------------------------------------------------------------
+constexpr int MXS_LD = MB + 1;
+constexpr size_t MXS_SMEM = (size_t)(3 * MB * MXS_LD + 32 * 33) * sizeof(float);
+
+// Cholesky of the 32 x 32 lower block T[o.., o..] in place and its inverse
+// into Z[o.., o..]; called by one full warp.  Lane i holds row i.
+__device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, int o, int* flag) {
+  const int lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? T[(o + lane) * MXS_LD + o + j] : 0.f;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    float d = __shfl_sync(0xffffffffu, a[k], k);
+    bad |= !(d > 0.f);
+    float r = rsqrtf(d);
+    float lik = (lane >= k) ? a[k] * r : 0.f;
+    a[k] = lik;
+#pragma unroll
+    for (int j = k + 1; j < 32; ++j) {
+      float ljk = __shfl_sync(0xffffffffu, lik, j);
+      if (lane >= j) a[j] = fmaf(-lik, ljk, a[j]);
+    }
+  }
+  if (bad && lane == 0) atomicOr(flag, DEV_NOT_SPD);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) T[(o + lane) * MXS_LD + o + j] = a[j];
+  __syncwarp();
+  // column `lane` of L^{-1} by forward substitution (rows of L broadcast from shared memory)
+  float x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float sacc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+    for (int t = 0; t < i; ++t) sacc = fmaf(-T[(o + i) * MXS_LD + o + t], x[t], sacc);
+    x[i] = sacc / T[(o + i) * MXS_LD + o + i];
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i) Z[(o + i) * MXS_LD + o + lane] = x[i];
+}
+
+__global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t ldw, int64_t n, int64_t k,
+                                                 int kb, float* __restrict__ Zk, __nv_bfloat16* __restrict__ Ph,
+                                                 __nv_bfloat16* __restrict__ Pm, __nv_bfloat16* __restrict__ Pl,
+                                                 int* __restrict__ flag) {
+  extern __shared__ float mxs[];
+  float* T = mxs;                     // diagonal tile -> L_kk
+  float* Z = T + MB * MXS_LD;         // Z_kk = L_kk^{-1}
+  float* X = Z + MB * MXS_LD;         // this CTA's panel rows
+  float* Y = X + MB * MXS_LD;         // 32 x 33 temporary
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t k0 = k + kb;
+  const int64_t r0 = k0 + (int64_t)blockIdx.x * MB;
   for (int e = tid; e < MB * MB; e += blockDim.x) {
     int i = e / MB, j = e % MB;
     float v;
     if (i < kb && j < kb) v = (j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
-    else v = (i == j) ? 1.f : 0.f;
-    T[i][j] = v;
+    else v = (i == j) ? 1.f : 0.f;  // identity beyond a ragged last block
+    T[i * MXS_LD + j] = v;
+    Z[i * MXS_LD + j] = 0.f;
+    int64_t r = r0 + i;
+    X[i * MXS_LD + j] = (r < n && j < kb) ? W[r * ldw + k + j] : 0.f;
   }
   __syncthreads();
-  const int tx = tid & (MB - 1), ty = tid >> 6;
-  for (int j = 0; j < MB; ++j) {
-    float d = T[j][j];
-    float ri = rsqrtf(d);
-    if (tid == 0) {
-      if (!(d > 0.f)) atomicOr(flag, DEV_NOT_SPD);
-      rv[j] = ri;
+  if (warp == 0) mx_chol_inv32(T, Z, 0, flag);
+  __syncthreads();
+  const int bi = tid >> 3, bj = tid & 7;  // 32 x 32 products: row bi, columns bj + 8q
+  {
+    // L21 = A21 Z11^T
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      float av = T[(32 + bi) * MXS_LD + t];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(av, Z[(bj + 8 * q) * MXS_LD + t], acc[q]);
     }
-    if (tx > j) {
-      float ckj = T[tx][j] * ri * ri;
-      float tij[MB / 4], tik[MB / 4];
+    __syncthreads();
 #pragma unroll
-      for (int q = 0; q < MB / 4; ++q) {
-        int i = ty + 4 * q;
-        tij[q] = T[i][j];
-        tik[q] = T[i][tx];
-      }
+    for (int q = 0; q < 4; ++q) T[(32 + bi) * MXS_LD + bj + 8 * q] = acc[q];
+    __syncthreads();
+    // S = A22 - L21 L21^T (lower part)
 #pragma unroll
-      for (int q = 0; q < MB / 4; ++q) {
-        int i = ty + 4 * q;
-        if (i >= tx) T[i][tx] = fmaf(-tij[q], ckj, tik[q]);
-      }
+    for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      float lv = T[(32 + bi) * MXS_LD + t];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, T[(32 + bj + 8 * q) * MXS_LD + t], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int j = bj + 8 * q;
+      if (j <= bi) T[(32 + bi) * MXS_LD + 32 + j] -= acc[q];
     }
     __syncthreads();
   }
-  for (int e = tid; e < MB * MB; e += blockDim.x) {
-    int i = e / MB, j = e % MB;
-    if (i < kb && j < kb) W[(k + i) * ldw + k + j] = (j <= i) ? T[i][j] * rv[j] : 0.f;
+  if (warp == 0) mx_chol_inv32(T, Z, 32, flag);
+  {
+    // Y = L21 Z11 (all warps but the first; the first joins after its factorization)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      float lv = T[(32 + bi) * MXS_LD + t];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, Z[t * MXS_LD + bj + 8 * q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Y[bi * 33 + bj + 8 * q] = acc[q];
+    __syncthreads();
+    // Z21 = -Z22 Y
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      float zv = Z[(32 + bi) * MXS_LD + 32 + t];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(zv, Y[t * 33 + bj + 8 * q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Z[(32 + bi) * MXS_LD + bj + 8 * q] = -acc[q];
+    __syncthreads();
   }
-  if (tid < MB) rd_out[tid] = rv[tid];
-}
-
-// Panel rows [k + kb, n): solve X L_kk^T = W[rows, k:k+kb] row by row (four
-// threads per row share each dot product), write X to W and as bf16 slices
-// (row index relative to k + kb, 64 columns, zero beyond kb).
-__global__ void __launch_bounds__(256) k_mx_panel(float* __restrict__ W, int64_t ldw, int64_t n, int64_t k,
-                                                  int kb, const float* __restrict__ rd,
-                                                  __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pm,
-                                                  __nv_bfloat16* __restrict__ Pl) {
-  __shared__ float Ls[MB][MB + 1];  // L_kk (lower)
-  __shared__ float X[MB][MB + 1];   // this CTA's 64 rows
-  __shared__ float rds[MB];
-  const int tid = threadIdx.x;
-  const int64_t k0 = k + kb;
-  const int64_t r0 = k0 + (int64_t)blockIdx.x * MB;
-  for (int e = tid; e < MB * MB; e += blockDim.x) {
-    int i = e / MB, t = e % MB;
-    Ls[i][t] = (i < kb && t <= i) ? W[(k + i) * ldw + k + t] : 0.f;
-    int64_t r = r0 + i;
-    X[i][t] = (r < n && t < kb) ? W[r * ldw + k + t] : 0.f;
+  if (blockIdx.x == 0)
+    for (int e = tid; e < MB * MB; e += blockDim.x) Zk[e] = Z[(e / MB) * MXS_LD + e % MB];
+  if (r0 >= n) return;
+  // panel rows: X <- X Z^T, each thread a 4 x 4 block (rows 4 pr.., columns pc + 16 q)
+  const int pr = tid >> 4, pc = tid & 15;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+#pragma unroll 4
+  for (int t = 0; t < MB; ++t) {
+    float xv[4], zv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = X[(4 * pr + u) * MXS_LD + t];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) zv[q] = Z[(pc + 16 * q) * MXS_LD + t];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[u][q] = fmaf(xv[u], zv[q], acc[u][q]);
   }
-  if (tid < MB) rds[tid] = tid < kb ? rd[tid] : 0.f;
   __syncthreads();
-  const int ri = tid >> 2, g = tid & 3;
-  const unsigned gm = 0xfu << (tid & 28);
-  for (int j = 0; j < kb; ++j) {
-    float s = 0.f;
-    for (int t = g; t < j; t += 4) s = fmaf(X[ri][t], Ls[j][t], s);
-    s += __shfl_xor_sync(gm, s, 1);
-    s += __shfl_xor_sync(gm, s, 2);
-    if (g == 0) X[ri][j] = (X[ri][j] - s) * rds[j];
-    __syncwarp(gm);
-  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[(4 * pr + u) * MXS_LD + pc + 16 * q] = acc[u][q];
   __syncthreads();
   for (int e = tid; e < MB * MB; e += blockDim.x) {
     int i = e / MB, j = e % MB;
     int64_t r = r0 + i;
     if (r >= n) continue;
-    float x = X[i][j];
+    float x = X[i * MXS_LD + j];
     if (j < kb) W[r * ldw + k + j] = x;
     else x = 0.f;
     __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -128,59 +213,11 @@ __global__ void __launch_bounds__(256) k_mx_panel(float* __restrict__ W, int64_t
     __nv_bfloat16 mm = __float2bfloat16_rn(rem);
     float rem2 = rem - __bfloat162float(mm);
     __nv_bfloat16 l = __float2bfloat16_rn(rem2);
-    int64_t pr = r - k0;
-    Ph[pr * MB + j] = h;
-    Pm[pr * MB + j] = mm;
-    Pl[pr * MB + j] = l;
+    int64_t prr = r - k0;
+    Ph[prr * MB + j] = h;
+    Pm[prr * MB + j] = mm;
+    Pl[prr * MB + j] = l;
   }
-}
-
-// Inverses of every 64 x 64 diagonal block of the finished factor, one CTA per
-// block (all blocks at once, off the factorization's critical chain): a row
-// sweep with one barrier per row, Z_ic -= L_ij Z_jc after row j is final.
-__global__ void __launch_bounds__(256) k_mx_blockinv(const float* __restrict__ W, int64_t ldw, int64_t n,
-                                                     float* __restrict__ Zd) {
-  __shared__ float T[MB][MB + 1];
-  __shared__ float Z[MB][MB + 1];
-  __shared__ float rl[MB];
-  const int tid = threadIdx.x;
-  const int64_t k = (int64_t)blockIdx.x * MB;
-  const int kb = (int)((n - k) < MB ? (n - k) : MB);
-  for (int e = tid; e < MB * MB; e += blockDim.x) {
-    int i = e / MB, j = e % MB;
-    float v;
-    if (i < kb && j < kb) v = (j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
-    else v = (i == j) ? 1.f : 0.f;
-    T[i][j] = v;
-    Z[i][j] = (i == j) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  if (tid < MB) rl[tid] = 1.f / T[tid][tid];
-  __syncthreads();
-  const int tx = tid & (MB - 1), ty = tid >> 6;
-  for (int j = 0; j < MB; ++j) {
-    float lj = rl[j];
-    if (tx <= j) {
-      float zjc = Z[j][tx] * lj;
-      float lij[MB / 4], zic[MB / 4];
-#pragma unroll
-      for (int q = 0; q < MB / 4; ++q) {
-        int i = ty + 4 * q;
-        lij[q] = T[i][j];
-        zic[q] = Z[i][tx];
-      }
-#pragma unroll
-      for (int q = 0; q < MB / 4; ++q) {
-        int i = ty + 4 * q;
-        if (i > j) Z[i][tx] = fmaf(-lij[q], zjc, zic[q]);
-      }
-    }
-    __syncthreads();
-    if (ty == 0 && tx <= j) Z[j][tx] *= lj;
-    __syncthreads();
-  }
-  float* out = Zd + (int64_t)blockIdx.x * MB * MB;
-  for (int e = tid; e < MB * MB; e += blockDim.x) out[e] = Z[e / MB][e % MB];
 }
 
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
@@ -197,12 +234,10 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
   __nv_bfloat16* Ph = pb.as<__nv_bfloat16>();
   __nv_bfloat16* Pm = Ph + (n + MB) * MB;
   __nv_bfloat16* Pl = Pm + (n + MB) * MB;
-  Buf& rb = c->scratch(54);
-  RBF_TRY(rb.ensure(MB * sizeof(float)));
-  float* rdiag = rb.as<float>();
   static bool attr_set[64] = {false};
   if (!attr_set[c->device & 63]) {
     RBF_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    RBF_CUDA(cudaFuncSetAttribute(k_mx_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MXS_SMEM));
     attr_set[c->device & 63] = true;
   }
   for (int64_t k = 0, step = 0; k < n; k += MB, ++step) {
@@ -210,13 +245,9 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
     int64_t rows = n - k - kb;
     {
       StageTimer st(c, RBF_STAGE_PANEL, s, (double)kb * kb * kb / 3.0 + (double)rows * kb * kb);
-      { k_mx_diag<<<1, 256, 0, s>>>(W, ldw, k, kb, rdiag, flag); ::rbf::note_launch(); }
+      unsigned g = rows > 0 ? (unsigned)((rows + MB - 1) / MB) : 1u;
+      { k_mx_step<<<g, 256, MXS_SMEM, s>>>(W, ldw, n, k, kb, Zd + step * MB * MB, Ph, Pm, Pl, flag); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
-      if (rows > 0) {
-        { k_mx_panel<<<(unsigned)((rows + MB - 1) / MB), 256, 0, s>>>(W, ldw, n, k, kb, rdiag, Ph, Pm,
-                                                                       Pl); ::rbf::note_launch(); }
-        RBF_CUDA(cudaGetLastError());
-      }
     }
     if (rows > 0) {
       StageTimer st(c, RBF_STAGE_TRAILING, s, (double)rows * (double)(rows + 1) * kb);
@@ -225,12 +256,6 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
                                                                               rows, Ph, Pm, Pl, flag); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
-  }
-  {
-    StageTimer st(c, RBF_STAGE_PANEL, s, 0.0);
-    int64_t nb = (n + MB - 1) / MB;
-    { k_mx_blockinv<<<(unsigned)nb, 256, 0, s>>>(W, ldw, n, Zd); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
   }
   return RBF_OK;
 }
@@ -413,7 +438,7 @@ __global__ void __launch_bounds__(256) k_residual_multi(const double* __restrict
 }
 
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
-                       int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s) {
+                       const float* Zi, int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s) {
   if (n <= 0 || m <= 0) return RBF_OK;
   int64_t tot = n * m;
   Buf& xb = c->scratch(59);
@@ -434,8 +459,12 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int
   for (int it = 0; it < sweeps; ++it) {
     { k_f64_to_f32<<<nb, 256, 0, s>>>(R, F, tot); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, false, s));
-    RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, true, s));
+    if (Zi) {
+      RBF_TRY(inv_solve(c, Zi, ldw, n, F, m, s));
+    } else {
+      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, false, s));
+      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, true, s));
+    }
     { k_add_f32_to_f64<<<nb, 256, 0, s>>>(X, F, tot); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     if (it + 1 < sweeps) {

@@ -730,8 +730,9 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaGetLastError());
     if (mixed) {
       // X = H_prev^{-1} E_D by refined solves with the float32 factor; P_DD = X[D, :]
-      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(), ap,
-                          Y.as<double>(), d, c->refine_sweeps_cov, s));
+      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
+                          c->zi_valid ? c->Zi.as<float>() : nullptr, ap, Y.as<double>(), d,
+                          c->refine_sweeps_cov, s));
       { k_gather_inv_block<<<nblk(d * d), 256, 0, s>>>(Y.as<double>(), d, Dl.as<int32_t>(), Pdd.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {
@@ -812,11 +813,17 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   // 8. factor H' and solve for the weight increment
   Buf& Wn = c->scratch(27);
   Buf& Zdn = c->scratch(63);
+  Buf& Zin = c->scratch(64);
   const int64_t ldw = (an + 3) & ~(int64_t)3;
+  const bool use_inv = mixed && an <= c->inv_max;
   if (mixed) {
     RBF_TRY(Wn.ensure((size_t)an * ldw * sizeof(float)));
     RBF_TRY(Zdn.ensure((size_t)((an + 63) / 64) * 64 * 64 * sizeof(float)));
     RBF_TRY(potrf_mixed(c, Hn.as<double>(), ld, an, Wn.as<float>(), ldw, Zdn.as<float>(), s));
+    if (use_inv) {
+      RBF_TRY(Zin.ensure((size_t)an * ldw * sizeof(float)));
+      RBF_TRY(trtri_mixed(c, Wn.as<float>(), ldw, an, Zdn.as<float>(), Zin.as<float>(), ldw, s));
+    }
   } else {
     RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s));
@@ -828,8 +835,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 2.0 * c->refine_sweeps + 2.0 * (c->refine_sweeps - 1) : 2.0) *
                                             (double)an * an);
     if (mixed)
-      RBF_TRY(mixed_solve(c, Hn.as<double>(), ld, Wn.as<float>(), ldw, Zdn.as<float>(), an, u.as<double>(), 1,
-                          c->refine_sweeps, s));
+      RBF_TRY(mixed_solve(c, Hn.as<double>(), ld, Wn.as<float>(), ldw, Zdn.as<float>(),
+                          use_inv ? Zin.as<float>() : nullptr, an, u.as<double>(), 1, c->refine_sweeps, s));
     else
       RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), false, s));
   }
@@ -859,6 +866,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   if (mixed) {
     std::swap(c->Lf, Wn);
     std::swap(c->Zd, Zdn);
+    if (use_inv) std::swap(c->Zi, Zin);
+    c->zi_valid = use_inv;
     c->ldw = ldw;
   } else {
     std::swap(c->L, Ln);
@@ -977,8 +986,9 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
     { k_unit_rhs<<<nblk(c->a * ka), 256, 0, s>>>(Y.as<double>(), c->a, ka, lb.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     if (c->cfg.update_precision == RBF_UPDATE_MIXED) {
-      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(), c->a,
-                          Y.as<double>(), ka, c->refine_sweeps_cov, s));
+      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
+                          c->zi_valid ? c->Zi.as<float>() : nullptr, c->a, Y.as<double>(), ka,
+                          c->refine_sweeps_cov, s));
       { k_gather_inv_block<<<nblk(ka * ka), 256, 0, s>>>(Y.as<double>(), ka, lb.as<int32_t>(), Paa.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {

@@ -51,7 +51,7 @@ class RbfConfig(ctypes.Structure):
         ("mesh_ny", ctypes.c_int32),
         ("r_kd", ctypes.c_double),
         ("refine_sweeps", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("inverse_max", ctypes.c_int32),
     ]
 
 
@@ -100,7 +100,7 @@ _SIGS = {
 }
 
 STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward",
-          "trsm32"]
+          "trsm32", "inverse", "invapply"]
 
 
 def launch_count() -> int:
@@ -165,7 +165,7 @@ class Terrain:
 
     def __init__(self, kernel=KERNEL_WENDLAND, rho=0.6, sigma=0.04, cutoff_mult=4.0, lam=1e-3,
                  update_precision=UPDATE_FP64, loss=LOSS_HUBER, huber_delta=0.05, lambda_m=1.0,
-                 wheel_offset=0.0, mesh=None, r_kd=0.1, min_count=1, refine_sweeps=0):
+                 wheel_offset=0.0, mesh=None, r_kd=0.1, min_count=1, refine_sweeps=0, inverse_max=0):
         self.lib = load()
         cfg = RbfConfig()
         cfg.kernel = kernel
@@ -183,6 +183,7 @@ class Terrain:
         cfg.mesh_x0, cfg.mesh_y0, cfg.mesh_h, cfg.mesh_nx, cfg.mesh_ny = x0, y0, h, nx, ny
         cfg.r_kd = r_kd
         cfg.refine_sweeps = refine_sweeps
+        cfg.inverse_max = inverse_max
         self.cfg = cfg
         self.device = torch.cuda.current_device()
         h_ = ctypes.c_void_p()

@@ -180,12 +180,14 @@ def test_update_config1_single_frame(N, prec):
     assert rel_inf(T.weights().cpu().numpy(), ref) < F64_TOL
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_update_config2_sequence_with_departures(N, prec):
+@pytest.mark.parametrize("prec,inv", [(0, 0), (1, 0), (1, -1)])
+def test_update_config2_sequence_with_departures(N, prec, inv):
     """Frames 0, 1, 2, 40, 41 of the staircase sequence: the later frames
-    drop centers from the active block and bring new ones in."""
+    drop centers from the active block and bring new ones in.  The mixed
+    update runs with the explicit factor inverse (inv = 0, default) and with
+    blocked substitution only (inv = -1)."""
     c = W.config2_centers()
-    T = N.Terrain(rho=0.6, update_precision=prec)
+    T = N.Terrain(rho=0.6, update_precision=prec, inverse_max=inv)
     T.set_centers(dev(c, torch.float64))
     st = O.BlockState(c, 1e-3, O.WENDLAND, rho=0.6)
     rng = np.random.default_rng(0)
