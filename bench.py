@@ -150,6 +150,40 @@ def frame_arrays(k):
     return ground.astype(np.float32), body.astype(np.float32), sensor
 
 
+def compare_precision(args, N, other, centers, dev_frames, flush, stream, T, nfr, eye):
+    """The same device-resident frames through the other update precision."""
+    import torch
+    h = torch.empty(8000, device=centers.device)
+    grad = torch.empty(8000, 2, device=centers.device)
+    out7 = torch.empty(7, dtype=torch.float64, device=centers.device)
+
+    To = N.Terrain(rho=0.6, lam=1e-3, update_precision=other, huber_delta=0.05)
+    To.set_centers(centers)
+    To_times = []
+    for k in range(nfr):
+        if k >= args.warmup:
+            flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g, b, s = dev_frames[k]
+        To.update(g, noise=NOISE)
+        To.soft_cost(eye, s, b, out=out7)
+        To.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            To_times.append(e0.elapsed_time(e1))
+    w_a = T.weights().cpu().numpy()
+    w_b = To.weights().cpu().numpy()
+    other_line = {"update_precision": "fp64" if other == N.UPDATE_FP64 else "mixed",
+                  "frames_per_s": len(To_times) / (sum(To_times) * 1e-3),
+                  "max_rel_diff_w": float(np.max(np.abs(w_a - w_b)) / max(np.max(np.abs(w_b)), 1e-300))}
+    To.close()
+    return other_line
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2509_26222_gb300 import native as N, workloads as W
@@ -226,31 +260,10 @@ def run_ours(args, ws, rank, local):
     Tp.close()
 
     # ----- the other update precision on the same frames (mixed vs FP64 comparison) -----
+    other_line = None
     other = N.UPDATE_FP64 if prec == N.UPDATE_MIXED else N.UPDATE_MIXED
-    To = N.Terrain(rho=0.6, lam=1e-3, update_precision=other, huber_delta=0.05)
-    To.set_centers(centers)
-    To_times = []
-    for k in range(nfr):
-        if k >= args.warmup:
-            flush.fill_(float(k))
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g, b, s = dev_frames[k]
-        To.update(g, noise=NOISE)
-        To.soft_cost(eye, s, b, out=out7)
-        To.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            To_times.append(e0.elapsed_time(e1))
-    w_a = T.weights().cpu().numpy()
-    w_b = To.weights().cpu().numpy()
-    other_line = {"update_precision": "fp64" if other == N.UPDATE_FP64 else "mixed",
-                  "frames_per_s": len(To_times) / (sum(To_times) * 1e-3),
-                  "max_rel_diff_w": float(np.max(np.abs(w_a - w_b)) / max(np.max(np.abs(w_b)), 1e-300))}
-    To.close()
+    for _ in range(0 if args.no_other else 1):
+        other_line = compare_precision(args, N, other, centers, dev_frames, flush, stream, T, nfr, eye)
 
     # ----- end to end through host buffers -----
     T2 = make_terrain()
@@ -466,6 +479,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--batch-patches", type=int, default=256, help="patches of the batched measurement (0: skip)")
+    ap.add_argument("--no-other", action="store_true", help="skip the other update precision on the same frames")
     ap.add_argument("--c5-reps", type=int, default=3, help="timed updates at 65,536 centers per precision (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:

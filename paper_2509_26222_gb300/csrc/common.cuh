@@ -96,6 +96,7 @@ struct Ctx {
   Buf Zi;            // float32 L^{-1} of the whole factor (valid when zi_valid)
   bool zi_valid = false;
   int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
+  bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
   int64_t ldw = 0;
   int refine_sweeps = 3;      // float64 refinement sweeps of the weight solve (mixed precision)
   int refine_sweeps_cov = 2;  // ... of the covariance solves (leaving centers, rbf_get_cov)

@@ -52,44 +52,53 @@ __global__ void k_mx_to_f32(const double* __restrict__ H, int64_t ldh, int64_t n
 // diagonal blocks only through Z.
 // ---------------------------------------------------------------------------
 constexpr int MXS_LD = MB + 1;
-constexpr size_t MXS_SMEM = (size_t)(3 * MB * MXS_LD + 32 * 33) * sizeof(float);
+constexpr size_t MXS_SMEM = (size_t)(3 * MB * MXS_LD + 32 * 33 + MB) * sizeof(float);
 
 // Cholesky of the 32 x 32 lower block T[o.., o..] in place and its inverse
-// into Z[o.., o..]; called by one full warp.  Lane i holds row i.
-__device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, int o, int* flag) {
+// into Z[o.., o..]; called by one full warp.  Lane i holds row i in
+// registers; at step k, a[p] is entry (i, k + p).  The rank-1 update is
+// applied to every lane and column without masks: entries above the
+// diagonal (and past column 31) collect finite values that are never read,
+// because the column written at step k is masked to zero above the
+// diagonal.  rd[o + k] = 1 / L_kk.
+__device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, float* rd, int o, int* flag) {
   const int lane = threadIdx.x & 31;
   float a[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? T[(o + lane) * MXS_LD + o + j] : 0.f;
+  for (int p = 0; p < 32; ++p) a[p] = (p <= lane) ? T[(o + lane) * MXS_LD + o + p] : 0.f;
   bool bad = false;
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < 32; ++k) {
-    float d = __shfl_sync(0xffffffffu, a[k], k);
+    float d = __shfl_sync(0xffffffffu, a[0], k);
     bad |= !(d > 0.f);
     float r = rsqrtf(d);
-    float lik = (lane >= k) ? a[k] * r : 0.f;
-    a[k] = lik;
+    float lik = (lane >= k) ? a[0] * r : 0.f;
+    T[(o + lane) * MXS_LD + o + k] = lik;  // column k of L (zero above the diagonal)
+    if (lane == 0) rd[o + k] = r;
 #pragma unroll
-    for (int j = k + 1; j < 32; ++j) {
-      float ljk = __shfl_sync(0xffffffffu, lik, j);
-      if (lane >= j) a[j] = fmaf(-lik, ljk, a[j]);
-    }
+    for (int p = 1; p < 32; ++p) a[p - 1] = fmaf(-lik, __shfl_sync(0xffffffffu, lik, (k + p) & 31), a[p]);
+    a[31] = 0.f;
   }
   if (bad && lane == 0) atomicOr(flag, DEV_NOT_SPD);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) T[(o + lane) * MXS_LD + o + j] = a[j];
   __syncwarp();
-  // column `lane` of L^{-1} by forward substitution (rows of L broadcast from shared memory)
+  // column `lane` of L^{-1} by forward substitution, four partial sums per row
   float x[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    float sacc = (i == lane) ? 1.f : 0.f;
+    const float* Lr = T + (o + i) * MXS_LD + o;
+    float s0 = (i == lane) ? 1.f : 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-    for (int t = 0; t < i; ++t) sacc = fmaf(-T[(o + i) * MXS_LD + o + t], x[t], sacc);
-    x[i] = sacc / T[(o + i) * MXS_LD + o + i];
+    for (int t = 0; t + 3 < i; t += 4) {
+      s0 = fmaf(-Lr[t], x[t], s0);
+      s1 = fmaf(-Lr[t + 1], x[t + 1], s1);
+      s2 = fmaf(-Lr[t + 2], x[t + 2], s2);
+      s3 = fmaf(-Lr[t + 3], x[t + 3], s3);
+    }
+#pragma unroll
+    for (int t = i & ~3; t < i; ++t) s0 = fmaf(-Lr[t], x[t], s0);
+    x[i] = ((s0 + s1) + (s2 + s3)) * rd[o + i];
+    Z[(o + i) * MXS_LD + o + lane] = x[i];
   }
-#pragma unroll
-  for (int i = 0; i < 32; ++i) Z[(o + i) * MXS_LD + o + lane] = x[i];
 }
 
 __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t ldw, int64_t n, int64_t k,
@@ -101,21 +110,30 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
   float* Z = T + MB * MXS_LD;         // Z_kk = L_kk^{-1}
   float* X = Z + MB * MXS_LD;         // this CTA's panel rows
   float* Y = X + MB * MXS_LD;         // 32 x 33 temporary
+  float* rd = Y + 32 * 33;            // 1 / L_jj
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t k0 = k + kb;
   const int64_t r0 = k0 + (int64_t)blockIdx.x * MB;
-  for (int e = tid; e < MB * MB; e += blockDim.x) {
-    int i = e / MB, j = e % MB;
-    float v;
-    if (i < kb && j < kb) v = (j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
-    else v = (i == j) ? 1.f : 0.f;  // identity beyond a ragged last block
-    T[i * MXS_LD + j] = v;
-    Z[i * MXS_LD + j] = 0.f;
-    int64_t r = r0 + i;
-    X[i * MXS_LD + j] = (r < n && j < kb) ? W[r * ldw + k + j] : 0.f;
+  {
+    // all 32 loads of a thread are issued before the first one is used
+    float tv[MB * MB / 256], xv[MB * MB / 256];
+#pragma unroll
+    for (int q = 0; q < MB * MB / 256; ++q) {
+      int e = tid + 256 * q, i = e / MB, j = e % MB;
+      tv[q] = (i < kb && j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
+      int64_t r = r0 + i;
+      xv[q] = (r < n && j < kb) ? W[r * ldw + k + j] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < MB * MB / 256; ++q) {
+      int e = tid + 256 * q, i = e / MB, j = e % MB;
+      T[i * MXS_LD + j] = (i >= kb && i == j) ? 1.f : tv[q];  // identity beyond a ragged last block
+      Z[i * MXS_LD + j] = 0.f;
+      X[i * MXS_LD + j] = xv[q];
+    }
   }
   __syncthreads();
-  if (warp == 0) mx_chol_inv32(T, Z, 0, flag);
+  if (warp == 0) mx_chol_inv32(T, Z, rd, 0, flag);
   __syncthreads();
   const int bi = tid >> 3, bj = tid & 7;  // 32 x 32 products: row bi, columns bj + 8q
   {
@@ -147,7 +165,7 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
     }
     __syncthreads();
   }
-  if (warp == 0) mx_chol_inv32(T, Z, 32, flag);
+  if (warp == 0) mx_chol_inv32(T, Z, rd, 32, flag);
   {
     // Y = L21 Z11 (all warps but the first; the first joins after its factorization)
     float acc[4] = {0.f, 0.f, 0.f, 0.f};

@@ -18,6 +18,7 @@
 //     block diagonal as in Eq. H_inverse_update.
 // The covariance of the active block is thus kept in information form; it is
 // the same matrix the Woodbury form of Eq. H_inverse_update produces.
+#include <limits.h>
 #include <math.h>
 
 #include <utility>
@@ -176,6 +177,9 @@ struct RowParams {
   double g_inv2s2;  // 1 / (2 st^2)
 };
 
+// One warp per point: lanes take the point's neighbour entries, write the
+// regression values m_ij and local column ids, and reduce the prediction
+// m_i^T w for the innovation e_i = z_i - m_i^T w (Eq. kf_w_update, G3).
 __global__ void __launch_bounds__(256) k_rowvals(RowParams R, const float* __restrict__ pts, int64_t n,
                                                  const int64_t* __restrict__ row_ptr,
                                                  const int32_t* __restrict__ col,
@@ -184,11 +188,12 @@ __global__ void __launch_bounds__(256) k_rowvals(RowParams R, const float* __res
                                                  const int32_t* __restrict__ g2l,
                                                  double* __restrict__ val, int32_t* __restrict__ lcol,
                                                  double* __restrict__ e) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n) return;
   double x = (double)pts[3 * i], y = (double)pts[3 * i + 1], z = (double)pts[3 * i + 2];
   double acc = 0.0;
-  for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+  for (int64_t k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
     int j = col[k];
     double dx = x - c64[2 * j], dy = y - c64[2 * j + 1];
     double m = row_value(R.kernel, dx * dx + dy * dy, R.inv_rho, R.g_scale, R.g_inv2s2);
@@ -196,183 +201,96 @@ __global__ void __launch_bounds__(256) k_rowvals(RowParams R, const float* __res
     lcol[k] = g2l[j];
     acc = fma(m, w[j], acc);
   }
-  e[i] = z - acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) e[i] = z - acc;
 }
 
-__global__ void k_tcount(const int32_t* __restrict__ lcol, int64_t nnz, int32_t* __restrict__ tcnt) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nnz) atomicAdd(&tcnt[lcol[k]], 1);
+// ---------------------------------------------------------------------------
+// m~ m~^T and m~ e with order-independent exact accumulation.
+//
+// Every point adds m_{i,l1} m_{i,l2} to entry (l1, l2) and m_{i,l} e_i to
+// u_l.  The products are rounded once to float64 (as in a plain float64 sum)
+// and then accumulated exactly in integers with 64-bit atomics, so the
+// result does not depend on the order in which points arrive and needs no
+// center-major copy of the lists:
+//   * Gram entries: products lie in [0, 1] and an entry has at most n terms,
+//     so a signed 64-bit fixed point with 2^gs units per 1, gs = 62 -
+//     ceil(log2(n + 1)), cannot overflow (resolution 2^-gs, at least 2^-46
+//     for n < 65536);
+//   * u: a 128-bit fixed point with 2^64 units per 1 (two words, the carry
+//     of the low word added to the high word), exact for every product of
+//     magnitude below 2^63.
+// Only the lower triangle (l2 <= l1) is accumulated; k_gram_merge adds it to
+// both triangles of H and clears the accumulator for the next frame.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void add_u128(unsigned long long* U, double x) {
+  double hi = floor(x);
+  double fr = x - hi;  // exact, in [0, 1)
+  unsigned long long lo = __double2ull_rz(ldexp(fr, 64));  // fr * 2^64 < 2^64
+  unsigned long long old = atomicAdd(U, lo);
+  unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  long long h = (long long)hi + (long long)carry;
+  if (h != 0) atomicAdd(U + 1, (unsigned long long)h);
 }
 
-__global__ void k_tfill(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ lcol,
-                        const int64_t* __restrict__ tstart, int32_t* __restrict__ tfill,
-                        int64_t* __restrict__ tk) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per point: pairs (t1, t2 <= t1) of its neighbour entries.
+__global__ void __launch_bounds__(256) k_gram_atomic(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ lcol,
+                                                     const double* __restrict__ val,
+                                                     const double* __restrict__ e, int64_t a, double gscale,
+                                                     unsigned long long* __restrict__ G,
+                                                     unsigned long long* __restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n) return;
-  for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-    int l = lcol[k];
-    int64_t p = tstart[l] + atomicAdd(&tfill[l], 1);
-    tk[p] = k;  // position in the point-major list: ascending k = ascending point
-  }
-}
-
-// point index of every center-major entry (after sorting)
-__global__ void k_towner(const int64_t* __restrict__ tk, int64_t nnz, const int64_t* __restrict__ row_ptr,
-                         int64_t n, int32_t* __restrict__ tpt) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nnz) return;
-  int64_t k = tk[p];
-  int64_t lo = 0, hi = n;  // largest lo with row_ptr[lo] <= k
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (row_ptr[mid] <= k) lo = mid;
-    else hi = mid;
-  }
-  tpt[p] = (int32_t)lo;
-}
-
-// order each center's entries by their position k in the point-major list
-// (= by point index): makes every later sum deterministic.  One CTA per
-// center, bitonic sort in shared memory; lists longer than the shared buffer
-// (very dense frames) fall back to an insertion sort by one thread.
-constexpr int TSORT_CAP = 2048;
-__global__ void __launch_bounds__(256) k_tsort(const int64_t* __restrict__ tstart, int64_t a,
-                                               int64_t* __restrict__ tk) {
-  __shared__ int64_t key[TSORT_CAP];
-  int64_t l = blockIdx.x;
-  if (l >= a) return;
-  int64_t lo = tstart[l], hi = tstart[l + 1];
-  int64_t len = hi - lo;
-  if (len <= 1) return;
-  if (len > TSORT_CAP) {
-    if (threadIdx.x == 0) {
-      for (int64_t u = lo + 1; u < hi; ++u) {
-        int64_t v = tk[u];
-        int64_t k = u - 1;
-        while (k >= lo && tk[k] > v) {
-          tk[k + 1] = tk[k];
-          --k;
-        }
-        tk[k + 1] = v;
+  const int64_t ra = row_ptr[i];
+  const int len = (int)(row_ptr[i + 1] - ra);
+  const double ei = e[i];
+  for (int t = lane; t < len; t += 32) add_u128(U + 2 * (int64_t)lcol[ra + t], val[ra + t] * ei);
+  if (len <= 32) {
+    int lt = lane < len ? lcol[ra + lane] : 0;
+    double mt = lane < len ? val[ra + lane] : 0.0;
+    for (int t1 = 0; t1 < len; ++t1) {
+      int l1 = __shfl_sync(0xffffffffu, lt, t1);
+      double m1 = __shfl_sync(0xffffffffu, mt, t1);
+      if (lane <= t1) {
+        int hi = l1 > lt ? l1 : lt, lo = l1 > lt ? lt : l1;  // lower triangle whatever the list order
+        atomicAdd(G + (int64_t)hi * a + lo, (unsigned long long)__double2ll_rn(m1 * mt * gscale));
       }
     }
-    return;
-  }
-  int P = 1;
-  while (P < len) P <<= 1;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) key[i] = i < len ? tk[lo + i] : INT64_MAX;
-  __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          bool up = (i & k) == 0;
-          int64_t x = key[i], y = key[ixj];
-          if ((x > y) == up) {
-            key[i] = y;
-            key[ixj] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < len; i += blockDim.x) tk[lo + i] = key[i];
-}
-
-// One warp per active row l1: H'[l1, :] += sum_i m_{i,l1} m_{i,:} (row of
-// m~ m~^T, accumulated in shared memory in ascending point order) and
-// u[l1] = sum_i m_{i,l1} e_i.  Entries go in groups of GR_G: the neighbour
-// lists of a group are first staged in shared memory with all their loads in
-// flight, then applied one entry after the other (same order as before).
-constexpr int GR_G = 8;   // entries per staging group
-constexpr int GR_L = 64;  // staged list length (longer lists finish from global memory)
-
-__host__ __device__ constexpr int64_t gram_warp_doubles(int64_t a) {
-  return a + GR_G * GR_L + GR_G + (GR_G * GR_L + GR_G * 4 + 1) / 2 + 1;
-}
-
-__global__ void __launch_bounds__(128) k_gram_rows(int64_t a, int64_t ldh, const int64_t* __restrict__ tstart,
-                                                   const int64_t* __restrict__ tk,
-                                                   const int32_t* __restrict__ tpt,
-                                                   const int64_t* __restrict__ row_ptr, int64_t n,
-                                                   const double* __restrict__ val,
-                                                   const int32_t* __restrict__ lcol,
-                                                   const double* __restrict__ e,
-                                                   double* __restrict__ H, double* __restrict__ u) {
-  extern __shared__ double srow[];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* row = srow + (int64_t)wid * gram_warp_doubles(a);
-  double* sval = row + a;                 // GR_G * GR_L staged values
-  double* sm1 = sval + GR_G * GR_L;       // GR_G entry weights m_{i,l1}
-  int32_t* scol = reinterpret_cast<int32_t*>(sm1 + GR_G);  // GR_G * GR_L staged columns
-  int64_t* sra = reinterpret_cast<int64_t*>(scol + GR_G * GR_L + (GR_G * GR_L) % 2);  // list starts
-  int32_t* slen = reinterpret_cast<int32_t*>(sra + GR_G);  // list lengths
-  for (int64_t l1 = (int64_t)blockIdx.x * nw + wid; l1 < a; l1 += (int64_t)gridDim.x * nw) {
-    for (int64_t j = lane; j < a; j += 32) row[j] = 0.0;
-    double ue = 0.0;
-    int64_t p0 = tstart[l1], p1 = tstart[l1 + 1];
-    for (int64_t pb = p0; pb < p1; pb += GR_G) {
-      int cnt = (int)((p1 - pb) < GR_G ? (p1 - pb) : GR_G);
-      __syncwarp();
-      if (lane < cnt) {
-        int64_t k1 = tk[pb + lane];
-        int64_t i = tpt[pb + lane];
-        double m1 = val[k1];
-        ue = fma(m1, e[i], ue);
-        int64_t ra = row_ptr[i], rb = row_ptr[i + 1];
-        sm1[lane] = m1;
-        sra[lane] = ra;
-        slen[lane] = (int32_t)(rb - ra);
-      }
-      __syncwarp();
-      {
-        // every load of the group is issued before any store (registers first)
-        int cr[GR_G][GR_L / 32];
-        double vr[GR_G][GR_L / 32];
-#pragma unroll
-        for (int q = 0; q < GR_G; ++q) {
-#pragma unroll
-          for (int h = 0; h < GR_L / 32; ++h) {
-            int t = lane + 32 * h;
-            bool ok = q < cnt && t < slen[q];
-            cr[q][h] = ok ? lcol[sra[q] + t] : 0;
-            vr[q][h] = ok ? val[sra[q] + t] : 0.0;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < GR_G; ++q) {
-#pragma unroll
-          for (int h = 0; h < GR_L / 32; ++h) {
-            scol[q * GR_L + lane + 32 * h] = cr[q][h];
-            sval[q * GR_L + lane + 32 * h] = vr[q][h];
-          }
-        }
-      }
-      __syncwarp();
-      for (int q = 0; q < cnt; ++q) {
-        double mq = sm1[q];
-        int len = slen[q];
-        int st = len < GR_L ? len : GR_L;
-        for (int t = lane; t < st; t += 32) {
-          int l2 = scol[q * GR_L + t];
-          row[l2] = fma(mq, sval[q * GR_L + t], row[l2]);
-        }
-        for (int64_t t = GR_L + lane; t < len; t += 32) {
-          int64_t k2 = sra[q] + t;
-          int l2 = lcol[k2];
-          row[l2] = fma(mq, val[k2], row[l2]);
-        }
-        __syncwarp();
+  } else {
+    for (int t1 = 0; t1 < len; ++t1) {
+      int l1 = lcol[ra + t1];
+      double m1 = val[ra + t1];
+      for (int t2 = lane; t2 <= t1; t2 += 32) {
+        int l2 = lcol[ra + t2];
+        int hi = l1 > l2 ? l1 : l2, lo = l1 > l2 ? l2 : l1;
+        atomicAdd(G + (int64_t)hi * a + lo, (unsigned long long)__double2ll_rn(m1 * val[ra + t2] * gscale));
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ue += __shfl_xor_sync(0xffffffffu, ue, o);
-    __syncwarp();
-    double* Hr = H + l1 * ldh;
-    for (int64_t j = lane; j < a; j += 32) Hr[j] += row[j];
-    if (lane == 0) u[l1] = ue;
+  }
+}
+
+// H[l1][l2] += G[l1][l2] / gscale for l2 <= l1 (and the mirror entry),
+// u[l] = U[l]; both accumulators are cleared.
+__global__ void k_gram_merge(int64_t a, double inv_gscale, unsigned long long* __restrict__ G,
+                             unsigned long long* __restrict__ U, double* __restrict__ H, int64_t ldh,
+                             double* __restrict__ u) {
+  int64_t l1 = blockIdx.y;
+  for (int64_t l2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l2 <= l1; l2 += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long q = G[l1 * a + l2];
+    if (q == 0ull) continue;
+    G[l1 * a + l2] = 0ull;
+    double v = (double)(long long)q * inv_gscale;
+    H[l1 * ldh + l2] += v;
+    if (l2 != l1) H[l2 * ldh + l1] += v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long lo = U[2 * l1], hi = U[2 * l1 + 1];
+    u[l1] = (double)(long long)hi + ldexp((double)lo, -64);
+    U[2 * l1] = 0ull;
+    U[2 * l1 + 1] = 0ull;
   }
 }
 
@@ -681,35 +599,14 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   Buf& val = c->scratch(15);
   Buf& lcol = c->scratch(16);
   Buf& ev = c->scratch(17);
-  Buf& tcnt = c->scratch(18);
-  Buf& tstart = c->scratch(19);
-  Buf& tk = c->scratch(34);
   RBF_TRY(val.ensure((size_t)nnz * sizeof(double)));
   RBF_TRY(lcol.ensure((size_t)nnz * sizeof(int32_t)));
   RBF_TRY(ev.ensure((size_t)n * sizeof(double)));
-  RBF_TRY(tcnt.ensure((size_t)(an + 1) * sizeof(int32_t)));
-  RBF_TRY(tstart.ensure((size_t)(an + 1) * sizeof(int64_t)));
-  RBF_TRY(tk.ensure((size_t)nnz * sizeof(int64_t)));
   RowParams RP = row_params(c->cfg, noise);
-  { k_rowvals<<<nblk(n), 256, 0, s>>>(RP, pts, n, row_ptr.as<int64_t>(), col.as<int32_t>(),
+  { k_rowvals<<<nblk(n * 32), 256, 0, s>>>(RP, pts, n, row_ptr.as<int64_t>(), col.as<int32_t>(),
                                     c->c64.as<double>(), c->w.as<double>(), g2ln.as<int32_t>(),
                                     val.as<double>(), lcol.as<int32_t>(), ev.as<double>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  RBF_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
-  { k_tcount<<<nblk(nnz), 256, 0, s>>>(lcol.as<int32_t>(), nnz, tcnt.as<int32_t>()); ::rbf::note_launch(); }
-  RBF_CUDA(cudaGetLastError());
-  RBF_TRY(scan_i32_to_i64(c, tcnt.as<int32_t>(), tstart.as<int64_t>(), an, s, 48));
-  RBF_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
-  { k_tfill<<<nblk(n), 256, 0, s>>>(row_ptr.as<int64_t>(), n, lcol.as<int32_t>(), tstart.as<int64_t>(),
-                                  tcnt.as<int32_t>(), tk.as<int64_t>()); ::rbf::note_launch(); }
-  RBF_CUDA(cudaGetLastError());
-  { k_tsort<<<(unsigned)an, 256, 0, s>>>(tstart.as<int64_t>(), an, tk.as<int64_t>()); ::rbf::note_launch(); }
-  RBF_CUDA(cudaGetLastError());
-  Buf& tpt = c->scratch(29);
-  RBF_TRY(tpt.ensure((size_t)nnz * sizeof(int32_t)));
-  { k_towner<<<nblk(nnz), 256, 0, s>>>(tk.as<int64_t>(), nnz, row_ptr.as<int64_t>(), n, tpt.as<int32_t>()); ::rbf::note_launch(); }
-  RBF_CUDA(cudaGetLastError());
-
   delete st_asm;
   // 5. leaving centers: their covariance block and the Schur complement
   StageTimer* st_blk = new StageTimer(c, RBF_STAGE_BLOCK, s, 0.0);
@@ -794,20 +691,29 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   // 7. + m~ m~^T and u = m~ e
   {
     StageTimer st(c, RBF_STAGE_ASSEMBLY, s, 0.0);
-    int dev_smem = 0;
-    RBF_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    int64_t per_warp = gram_warp_doubles(an) * (int64_t)sizeof(double);
-    int warps = (int)((int64_t)dev_smem / per_warp);
-    if (warps > 4) warps = 4;
-    if (warps < 1) return fail(RBF_EINVAL, "active block of %lld centers exceeds shared memory", (long long)an);
-    size_t smem = (size_t)warps * per_warp;
-    RBF_CUDA(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned g = nblk(an, warps);
-    { k_gram_rows<<<g, warps * 32, smem, s>>>(an, ld, tstart.as<int64_t>(), tk.as<int64_t>(),
-                                             tpt.as<int32_t>(), row_ptr.as<int64_t>(), n, val.as<double>(),
-                                             lcol.as<int32_t>(), ev.as<double>(), Hn.as<double>(),
-                                             u.as<double>()); ::rbf::note_launch(); }
+    if (an > 65535) return fail(RBF_EINVAL, "active block of %lld centers exceeds 65535", (long long)an);
+    Buf& G = c->scratch(68);
+    Buf& U = c->scratch(69);
+    size_t gbytes = (size_t)an * an * sizeof(unsigned long long);
+    size_t ubytes = (size_t)2 * an * sizeof(unsigned long long);
+    if (G.bytes < gbytes || U.bytes < ubytes || c->gacc_dirty) {
+      RBF_TRY(G.ensure(gbytes));
+      RBF_TRY(U.ensure(ubytes));
+      RBF_CUDA(cudaMemsetAsync(G.p, 0, G.bytes, s));
+      RBF_CUDA(cudaMemsetAsync(U.p, 0, U.bytes, s));
+    }
+    int gs = 62 - (int)ceil(log2((double)n + 1.0));
+    double gscale = ldexp(1.0, gs);
+    c->gacc_dirty = true;
+    { k_gram_atomic<<<nblk(n * 32), 256, 0, s>>>(n, row_ptr.as<int64_t>(), lcol.as<int32_t>(), val.as<double>(),
+                                               ev.as<double>(), an, gscale, G.as<unsigned long long>(),
+                                               U.as<unsigned long long>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
+    dim3 mg((unsigned)((an + 255) / 256 < 8 ? (an + 255) / 256 : 8), (unsigned)an);
+    { k_gram_merge<<<mg, 256, 0, s>>>(an, 1.0 / gscale, G.as<unsigned long long>(), U.as<unsigned long long>(),
+                                      Hn.as<double>(), ld, u.as<double>()); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    c->gacc_dirty = false;
   }
 
   // 8. factor H' and solve for the weight increment
@@ -830,6 +736,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   }
   int flag = 0;
   RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_BAD_INDEX) return fail(RBF_ECUDA, "Gram row entry outside its lattice window");
   if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
   {
     StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 2.0 * c->refine_sweeps + 2.0 * (c->refine_sweeps - 1) : 2.0) *
