@@ -239,7 +239,10 @@ enum {
   RBF_STAGE_INVERSE = 10,   /* explicit inverse of the float32 factor (flops: a^3/3) */
   RBF_STAGE_INVAPPLY = 11,  /* solves by products with that inverse (flops: 2 a^2 per right-hand side),
                                nested inside SOLVE/BLOCK */
-  RBF_NSTAGE = 12
+  RBF_STAGE_COVBLOCK = 12,  /* covariance block of the leaving centers (nested inside BLOCK) */
+  RBF_STAGE_SCHUR = 13,     /* information of the staying centers (nested inside BLOCK) */
+  RBF_STAGE_ENTER = 14,     /* information of the entering centers (nested inside BLOCK) */
+  RBF_NSTAGE = 15
 };
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int on);
 /* Number of CUDA kernels librbfgb.so has launched since it was loaded (all

@@ -424,6 +424,8 @@ rbf_status reset_update_state(Ctx* c) {
   c->a = 0;
   c->pg_on = false;
   c->zi_valid = false;
+  c->Hs.valid = false;
+  c->Hs_next.valid = false;
   c->Pg.release();
   return RBF_OK;
 }
@@ -583,7 +585,7 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   cudaDeviceSynchronize();
   batch_destroy(x);
   Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2,
-                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
+                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Hs.rp, &x->Hs.col, &x->Hs.val, &x->Hs_next.rp, &x->Hs_next.col, &x->Hs_next.val, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   if (x->host_small) cudaFreeHost(x->host_small);

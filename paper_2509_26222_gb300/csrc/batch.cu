@@ -293,7 +293,7 @@ static rbf_status run_patch(Ctx* sc, const rbf_config& cfg, const rbf_patch& P, 
   }
   if (mixed) {
     RBF_TRY(potrf_mixed(sc, H.as<double>(), M, M, Wf.as<float>(), ldw, Zd.as<float>(), s));
-    RBF_TRY(mixed_solve(sc, H.as<double>(), M, Wf.as<float>(), ldw, Zd.as<float>(), nullptr, M, u.as<double>(), 1,
+    RBF_TRY(mixed_solve(sc, H.as<double>(), M, nullptr, Wf.as<float>(), ldw, Zd.as<float>(), nullptr, M, u.as<double>(), 1,
                         sc->refine_sweeps, s));
   } else {
     RBF_CUDA(cudaMemcpyAsync(L.p, H.p, (size_t)M * M * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -372,7 +372,7 @@ static rbf_status autotune(Ctx* sc, int64_t m, cudaStream_t s, int* pick) {
         RBF_TRY(chol_solve(sc, H.as<double>(), L.as<double>(), m, m, u.as<double>(), false, s));
       } else {
         RBF_TRY(potrf_mixed(sc, H.as<double>(), m, m, Wf.as<float>(), ldw, Zd.as<float>(), s));
-        RBF_TRY(mixed_solve(sc, H.as<double>(), m, Wf.as<float>(), ldw, Zd.as<float>(), nullptr, m, u.as<double>(), 1,
+        RBF_TRY(mixed_solve(sc, H.as<double>(), m, nullptr, Wf.as<float>(), ldw, Zd.as<float>(), nullptr, m, u.as<double>(), 1,
                             sc->refine_sweeps, s));
       }
       RBF_CUDA(cudaEventRecord(e1, s));

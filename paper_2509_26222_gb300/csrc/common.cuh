@@ -58,6 +58,15 @@ struct Grid {
   int nx, ny;       // number of cells
 };
 
+// Compressed-row copy of a float64 matrix: every exactly nonzero entry,
+// ascending columns (sparse.cu).
+constexpr int64_t SPH_MAX = 4096;  // largest order kept (capacity n^2 entries)
+struct SpH {
+  Buf rp, col, val;  // int32 (n + 1), int32 and double (capacity n * n)
+  int64_t n = 0;
+  bool valid = false;
+};
+
 struct Lattice {
   bool on = false;  // every center sits on (x0 + (i + 0.5) h, y0 + (j + 0.5) h)
   double x0, y0, h;
@@ -97,6 +106,8 @@ struct Ctx {
   bool zi_valid = false;
   int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
+  SpH Hs;            // compressed rows of H (mixed update)
+  SpH Hs_next;       // compressed rows of the information matrix being built
   int64_t ldw = 0;
   int refine_sweeps = 3;      // float64 refinement sweeps of the weight solve (mixed precision)
   int refine_sweeps_cov = 2;  // ... of the covariance solves (leaving centers, rbf_get_cov)
@@ -243,8 +254,15 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
                        cudaStream_t s);
 rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Zd, float* B, int64_t m,
                   int64_t ldb, bool transpose, cudaStream_t s);
-rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
-                       const float* Zi, int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s);
+rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
+                       const float* Zd, const float* Zi, int64_t n, double* B, int64_t m, int sweeps,
+                       cudaStream_t s);
+rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
+                     const float* Zd, const float* Zi, int64_t n, double* B, int64_t k, const int32_t* pos,
+                     int sweeps, double* P, cudaStream_t s);
+// compressed rows of the information matrix (sparse.cu)
+rbf_status build_csr(Ctx* c, const double* H, int64_t ld, int64_t n, SpH& out, cudaStream_t s);
+rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t m, double* R, cudaStream_t s);
 // explicit inverse of the float32 factor and solves with it (inverse.cu)
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
                        cudaStream_t s);

@@ -455,8 +455,10 @@ __global__ void __launch_bounds__(256) k_residual_multi(const double* __restrict
   }
 }
 
-rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int64_t ldw, const float* Zd,
-                       const float* Zi, int64_t n, double* B, int64_t m, int sweeps, cudaStream_t s) {
+rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
+                       const float* Zd, const float* Zi, int64_t n, double* B, int64_t m, int sweeps,
+                       cudaStream_t s) {
+  if (Hs && !(Hs->valid && Hs->n == n)) Hs = nullptr;
   if (n <= 0 || m <= 0) return RBF_OK;
   int64_t tot = n * m;
   Buf& xb = c->scratch(59);
@@ -486,7 +488,9 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int
     { k_add_f32_to_f64<<<nb, 256, 0, s>>>(X, F, tot); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     if (it + 1 < sweeps) {
-      if (m == 1) {
+      if (Hs) {
+        RBF_TRY(csr_residual(*Hs, X, bb.as<double>(), m, Rr, s));
+      } else if (m == 1) {
         RBF_TRY(symv_residual(H, n, ldh, X, bb.as<double>(), Rr, s));
       } else {
         unsigned nw = (unsigned)((n * 32 + 255) / 256);
@@ -497,6 +501,55 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const float* W, int
     }
   }
   RBF_CUDA(cudaMemcpyAsync(B, X, (size_t)tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return RBF_OK;
+}
+
+// Block P[D, D] = E_D^T H^{-1} E_D of the covariance for the columns B = E_D
+// (unit vectors at positions pos, overwritten).  X comes from sweeps - 1
+// refined solves; then one float64 residual R = E_D - H X gives the
+// second-order estimate
+//   P = E_D^T X + X^T R    (error -(X - H^{-1}E_D)^T H (X - H^{-1}E_D)),
+// symmetrised.  With the float32 factor accurate to eps, one solve already
+// gives P to about eps^2, where one more refinement sweep would need a
+// second solve.
+__global__ void k_sym_gather(const double* __restrict__ X, int64_t k, const int32_t* __restrict__ pos,
+                             double* __restrict__ P) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  int64_t u = e / k, v = e % k;
+  P[e] = 0.5 * (X[(int64_t)pos[u] * k + v] + X[(int64_t)pos[v] * k + u]);
+}
+
+rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
+                     const float* Zd, const float* Zi, int64_t n, double* B, int64_t k, const int32_t* pos,
+                     int sweeps, double* P, cudaStream_t s) {
+  if (n <= 0 || k <= 0) return RBF_OK;
+  if (Hs && !(Hs->valid && Hs->n == n)) Hs = nullptr;
+  if (sweeps <= 1) {
+    RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, 1, s));
+    { k_sym_gather<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(B, k, pos, P); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    return RBF_OK;
+  }
+  int64_t tot = n * k;
+  Buf& e0 = c->scratch(57);
+  Buf& rr = c->scratch(58);
+  RBF_TRY(e0.ensure((size_t)tot * sizeof(double)));
+  RBF_TRY(rr.ensure((size_t)tot * sizeof(double)));
+  RBF_CUDA(cudaMemcpyAsync(e0.p, B, (size_t)tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, sweeps - 1, s));
+  double* R = rr.as<double>();
+  if (Hs) {
+    RBF_TRY(csr_residual(*Hs, B, e0.as<double>(), k, R, s));
+  } else {
+    unsigned nw = (unsigned)((n * 32 + 255) / 256);
+    { k_residual_multi<<<nw, 256, 0, s>>>(H, n, ldh, B, e0.as<double>(), k, R); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  }
+  { k_sym_gather<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(B, k, pos, P); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  RBF_TRY(gemm_f64(c, true, false, k, k, n, 0.5, B, k, R, k, 1.0, P, k, s));
+  RBF_TRY(gemm_f64(c, true, false, k, k, n, 0.5, R, k, B, k, 1.0, P, k, s));
   return RBF_OK;
 }
 

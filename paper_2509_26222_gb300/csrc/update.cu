@@ -316,6 +316,54 @@ __global__ void k_scatter_sym(const double* __restrict__ S, int64_t lds, int64_t
   Hn[(int64_t)pos[u] * ldn + pos[v]] = x;
 }
 
+// Hn[pn[u]][pn[v]] = H[po[u]][po[v]] for a symmetric block (full copy)
+__global__ void k_move_sym(const double* __restrict__ H, int64_t ldh, const int32_t* __restrict__ po,
+                           const int32_t* __restrict__ pn, int64_t m, double* __restrict__ Hn, int64_t ldn) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  int64_t u = e / m, v = e % m;
+  Hn[(int64_t)pn[u] * ldn + pn[v]] = H[(int64_t)po[u] * ldh + po[v]];
+}
+
+// cpl[q] = 1 if staying center q (previous-local row Sl[q]) has a nonzero
+// entry in a column of a leaving center (isD over previous-local ids): only
+// those rows change in the Schur complement H_SS - H_SD H_DD^{-1} H_DS.
+__global__ void __launch_bounds__(256) k_coupled(const double* __restrict__ H, int64_t ldh, int64_t ap,
+                                                 const int32_t* __restrict__ Sl, int64_t sN,
+                                                 const int32_t* __restrict__ isD, int32_t* __restrict__ cpl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= sN) return;
+  const double* hr = H + (int64_t)Sl[q] * ldh;
+  bool any = false;
+  for (int64_t j = lane; j < ap && !any; j += 32) any = isD[j] && hr[j] != 0.0;
+  any = __any_sync(0xffffffffu, any);
+  if (lane == 0) cpl[q] = any ? 1 : 0;
+}
+
+// the same flags from the compressed rows of H
+__global__ void __launch_bounds__(256) k_coupled_csr(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                     const int32_t* __restrict__ Sl, int64_t sN,
+                                                     const int32_t* __restrict__ isD, int32_t* __restrict__ cpl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= sN) return;
+  const int row = Sl[q];
+  bool any = false;
+  for (int p = rp[row] + lane; p < rp[row + 1] && !any; p += 32) any = isD[col[p]] != 0;
+  any = __any_sync(0xffffffffu, any);
+  if (lane == 0) cpl[q] = any ? 1 : 0;
+}
+
+__global__ void k_pick(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t m,
+                       const int32_t* __restrict__ a, const int32_t* __restrict__ b, int32_t* __restrict__ oa,
+                       int32_t* __restrict__ ob) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m || !flag[q]) return;
+  oa[pos[q]] = a[q];
+  ob[pos[q]] = b[q];
+}
+
 __global__ void k_scatter_diag(const int32_t* __restrict__ pos, int64_t m, double value,
                                double* __restrict__ Hn, int64_t ldn) {
   int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,14 +423,6 @@ __global__ void k_pg_init(double* __restrict__ Pg, int64_t M, double diag) {
 }
 
 // P[u][v] = 0.5 (X[pos[u]][v] + X[pos[v]][u]) for X = H^{-1} E_pos (n x k)
-__global__ void k_gather_inv_block(const double* __restrict__ X, int64_t k, const int32_t* __restrict__ pos,
-                                   double* __restrict__ P) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * k) return;
-  int64_t uu = e / k, v = e % k;
-  P[e] = 0.5 * (X[(int64_t)pos[uu] * k + v] + X[(int64_t)pos[v] * k + uu]);
-}
-
 // Count the entering centers (lpos[0 .. *e_count)) that left some earlier block.
 // The list length is only known on the device here, so it is read from
 // e_count; both indirections are range-checked.
@@ -625,50 +665,76 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_TRY(Pdd.ensure((size_t)d * d * sizeof(double)));
     { k_unit_rhs<<<nblk(ap * d), 256, 0, s>>>(Y.as<double>(), ap, d, Dl.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
+    StageTimer st_cb(c, RBF_STAGE_COVBLOCK, s, 0.0);
     if (mixed) {
       // X = H_prev^{-1} E_D by refined solves with the float32 factor; P_DD = X[D, :]
-      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
-                          c->zi_valid ? c->Zi.as<float>() : nullptr, ap, Y.as<double>(), d,
-                          c->refine_sweeps_cov, s));
-      { k_gather_inv_block<<<nblk(d * d), 256, 0, s>>>(Y.as<double>(), d, Dl.as<int32_t>(), Pdd.as<double>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
+      RBF_TRY(mixed_cov(c, c->H.as<double>(), c->ldH, &c->Hs, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
+                        c->zi_valid ? c->Zi.as<float>() : nullptr, ap, Y.as<double>(), d, Dl.as<int32_t>(),
+                        c->refine_sweeps_cov, Pdd.as<double>(), s));
     } else {
       // Y = L_prev^{-1} E_D, P_DD = Y^T Y
       RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s));
       RBF_TRY(gemm_f64(c, true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
                        Pdd.as<double>(), d, s));
     }
+  }
+  if (d > 0) {
+    StageTimer st_sc(c, RBF_STAGE_SCHUR, s, 0.0);
     if (sN > 0) {
-      // T = H_prev permuted to [D; S]; d steps of Cholesky leave H_S in T[d:, d:]
+      // H_S = H_SS - H_SD H_DD^{-1} H_DS.  H_SS moves over unchanged; only the
+      // rows N of S coupled to some leaving center change: T = H_prev on
+      // [D; N], and d steps of Cholesky leave the new H_NN in T[d:, d:].
+      { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(),
+                                               sN, Hn.as<double>(), ld); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      Buf& cpl = c->scratch(74);
+      Buf& cpp = c->scratch(75);
       Buf& perm = c->scratch(40);
-      Buf& T = c->scratch(41);
-      RBF_TRY(perm.ensure((size_t)ap * sizeof(int32_t)));
-      RBF_TRY(T.ensure((size_t)ap * ap * sizeof(double)));
+      Buf& Nn = c->scratch(76);
+      RBF_TRY(cpl.ensure((size_t)(sN + 1) * sizeof(int32_t)));
+      RBF_TRY(cpp.ensure((size_t)(sN + 1) * sizeof(int32_t)));
+      RBF_TRY(perm.ensure((size_t)(d + sN) * sizeof(int32_t)));
+      RBF_TRY(Nn.ensure((size_t)(sN + 1) * sizeof(int32_t)));
+      if (c->Hs.valid && c->Hs.n == ap) {
+        { k_coupled_csr<<<nblk(sN * 32), 256, 0, s>>>(c->Hs.rp.as<int32_t>(), c->Hs.col.as<int32_t>(),
+                                                     Sl.as<int32_t>(), sN, flD, cpl.as<int32_t>()); ::rbf::note_launch(); }
+      } else {
+        { k_coupled<<<nblk(sN * 32), 256, 0, s>>>(c->H.as<double>(), c->ldH, ap, Sl.as<int32_t>(), sN, flD,
+                                                cpl.as<int32_t>()); ::rbf::note_launch(); }
+      }
+      RBF_CUDA(cudaGetLastError());
+      RBF_TRY(scan_i32(c, cpl.as<int32_t>(), cpp.as<int32_t>(), sN, s, 77));
       RBF_CUDA(cudaMemcpyAsync(perm.p, Dl.p, (size_t)d * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-      RBF_CUDA(cudaMemcpyAsync(perm.as<int32_t>() + d, Sl.p, (size_t)sN * sizeof(int32_t),
-                               cudaMemcpyDeviceToDevice, s));
-      { k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), ap,
-                                                 T.as<double>(), ap); ::rbf::note_launch(); }
+      { k_pick<<<nblk(sN), 256, 0, s>>>(cpl.as<int32_t>(), cpp.as<int32_t>(), sN, Sl.as<int32_t>(),
+                                      Sn.as<int32_t>(), perm.as<int32_t>() + d, Nn.as<int32_t>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
-      RBF_TRY(potrf_lower(c, T.as<double>(), ap, ap, d, false, s));
-      { k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>() + d * ap + d, ap, sN, Sn.as<int32_t>(),
-                                                  Hn.as<double>(), ld); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
+      int32_t* h32 = (int32_t*)c->host_small;
+      RBF_CUDA(cudaMemcpyAsync(h32 + 4, cpp.as<int32_t>() + sN, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RBF_CUDA(cudaStreamSynchronize(s));
+      const int64_t nN = h32[4];
+      if (nN > 0) {
+        const int64_t t = d + nN;
+        Buf& T = c->scratch(41);
+        RBF_TRY(T.ensure((size_t)t * t * sizeof(double)));
+        { k_gather_sym<<<nblk(t * t), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), t,
+                                                 T.as<double>(), t); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+        RBF_TRY(potrf_lower(c, T.as<double>(), t, t, d, false, s));
+        { k_scatter_sym<<<nblk(nN * nN), 256, 0, s>>>(T.as<double>() + d * t + d, t, nN, Nn.as<int32_t>(),
+                                                    Hn.as<double>(), ld); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+      }
     }
   } else if (sN > 0) {
     // nobody leaves: the staying block is the previous information matrix
-    Buf& T = c->scratch(41);
-    RBF_TRY(T.ensure((size_t)ap * ap * sizeof(double)));
-    { k_gather_sym<<<nblk(ap * ap), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), sN,
-                                               T.as<double>(), sN); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-    { k_scatter_sym<<<nblk(sN * sN), 256, 0, s>>>(T.as<double>(), sN, sN, Sn.as<int32_t>(), Hn.as<double>(),
-                                                ld); ::rbf::note_launch(); }
+    { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(), sN,
+                                             Hn.as<double>(), ld); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
 
   // 6. entering centers: inverse of their stored covariance block
   if (e > 0) {
+    StageTimer st_en(c, RBF_STAGE_ENTER, s, 0.0);
     if (!c->pg_on || e_returning == 0) {
       // never-departed centers keep the prior P = I / lambda with no coupling
       { k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
@@ -714,6 +780,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
                                       Hn.as<double>(), ld, u.as<double>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     c->gacc_dirty = false;
+    if (mixed) RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, s));
   }
 
   // 8. factor H' and solve for the weight increment
@@ -735,19 +802,18 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s));
   }
   int flag = 0;
-  RBF_TRY(read_dev_flag(c, s, &flag));
-  if (flag & DEV_BAD_INDEX) return fail(RBF_ECUDA, "Gram row entry outside its lattice window");
-  if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
   {
     StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 2.0 * c->refine_sweeps + 2.0 * (c->refine_sweeps - 1) : 2.0) *
                                             (double)an * an);
     if (mixed)
-      RBF_TRY(mixed_solve(c, Hn.as<double>(), ld, Wn.as<float>(), ldw, Zdn.as<float>(),
+      RBF_TRY(mixed_solve(c, Hn.as<double>(), ld, &c->Hs_next, Wn.as<float>(), ldw, Zdn.as<float>(),
                           use_inv ? Zin.as<float>() : nullptr, an, u.as<double>(), 1, c->refine_sweeps, s));
     else
       RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), false, s));
   }
+  // one read of the device flags covers the factorization and the solves
   RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
   if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
 
   // 9. commit
@@ -773,6 +839,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   if (mixed) {
     std::swap(c->Lf, Wn);
     std::swap(c->Zd, Zdn);
+    std::swap(c->Hs, c->Hs_next);
     if (use_inv) std::swap(c->Zi, Zin);
     c->zi_valid = use_inv;
     c->ldw = ldw;
@@ -893,11 +960,9 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
     { k_unit_rhs<<<nblk(c->a * ka), 256, 0, s>>>(Y.as<double>(), c->a, ka, lb.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     if (c->cfg.update_precision == RBF_UPDATE_MIXED) {
-      RBF_TRY(mixed_solve(c, c->H.as<double>(), c->ldH, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
-                          c->zi_valid ? c->Zi.as<float>() : nullptr, c->a, Y.as<double>(), ka,
-                          c->refine_sweeps_cov, s));
-      { k_gather_inv_block<<<nblk(ka * ka), 256, 0, s>>>(Y.as<double>(), ka, lb.as<int32_t>(), Paa.as<double>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
+      RBF_TRY(mixed_cov(c, c->H.as<double>(), c->ldH, &c->Hs, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
+                        c->zi_valid ? c->Zi.as<float>() : nullptr, c->a, Y.as<double>(), ka, lb.as<int32_t>(),
+                        c->refine_sweeps_cov, Paa.as<double>(), s));
     } else {
       RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s));
       RBF_TRY(gemm_f64(c, true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,

@@ -100,7 +100,7 @@ _SIGS = {
 }
 
 STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward",
-          "trsm32", "inverse", "invapply"]
+          "trsm32", "inverse", "invapply", "covblock", "schur", "enter"]
 
 
 def launch_count() -> int:
