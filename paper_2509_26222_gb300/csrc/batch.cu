@@ -315,6 +315,7 @@ static Ctx* new_sub(const Ctx* parent) {
   sc->device = parent->device;
   sc->refine_sweeps = parent->refine_sweeps;
   sc->refine_sweeps_cov = parent->refine_sweeps_cov;
+  sc->la_ok = false;  // the same kernel sequence eagerly and in the captured graph
   if (sc->dflag.ensure(16 * sizeof(int)) != RBF_OK || cudaMemset(sc->dflag.p, 0, 16 * sizeof(int)) != cudaSuccess) {
     delete sc;
     return nullptr;

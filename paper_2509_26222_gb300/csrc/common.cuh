@@ -106,6 +106,9 @@ struct Ctx {
   bool zi_valid = false;
   int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
+  bool la_ok = true;                 // look-ahead factorization allowed
+  cudaStream_t la_stream = nullptr;  // side stream of the look-ahead factorization
+  cudaEvent_t la_ev[5] = {};          // panel ready (2), trailing done (2), join
   SpH Hs;            // compressed rows of H (mixed update)
   SpH Hs_next;       // compressed rows of the information matrix being built
   int64_t ldw = 0;
@@ -121,7 +124,7 @@ struct Ctx {
   uint32_t epoch = 0;
 
   // scratch buffers, addressed by slot (slots 48.. are used by the scans)
-  static constexpr int NSLOT = 80;
+  static constexpr int NSLOT = 96;
   Buf ws[NSLOT];
   Buf& scratch(int i) { return ws[i < NSLOT ? i : NSLOT - 1]; }
 
@@ -267,6 +270,7 @@ rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t 
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
                        cudaStream_t s);
 rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, int64_t m, cudaStream_t s);
+constexpr int SPD_SMALL_MAX = 128;  // largest order of spd_inverse_small (one CTA, shared memory)
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
                       cudaStream_t s);

@@ -349,80 +349,58 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
 }
 
 // ---------------------------------------------------------------------------
-// Inverse of a small SPD matrix (m <= 64) in one CTA: Cholesky, inverse of
-// the factor, G^{-1} = Z^T Z.  In place, row-major m x m.
+// Inverse of a small SPD matrix (m <= 64) in one CTA by Gauss-Jordan
+// elimination without pivoting (the pivots are the diagonals of successive
+// Schur complements, positive for an SPD matrix).  Each of the m steps is one
+// parallel update of all m^2 entries between two barriers.  In place,
+// row-major m x m, symmetrised on output.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_spd_inverse_small(double* __restrict__ G, int m, int* __restrict__ flag) {
-  __shared__ double T[64][65];
-  __shared__ double Z[64][65];
-  __shared__ double rinv[64];
+  extern __shared__ double gj[];  // A (m x (m + 1)), then the pivot column and row
+  const int ld = m + 1;
+  double* A = gj;
+  double* fcol = gj + (int64_t)m * ld;
+  double* prow = fcol + m;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 64 * 64; e += blockDim.x) {
-    int i = e / 64, j = e % 64;
-    T[i][j] = (i < m && j < m) ? G[i * m + j] : (i == j ? 1.0 : 0.0);
-  }
+  for (int e = tid; e < m * m; e += blockDim.x) A[(e / m) * ld + e % m] = G[e];
   __syncthreads();
-  if (tid < 32) {  // warp-synchronous left-looking Cholesky, lane owns rows lane, lane + 32
-    const int lane = tid;
-    for (int j = 0; j < m; ++j) {
-      double piv = 0.0;
-      if (lane == (j & 31)) {
-        double s = T[j][j];
-        for (int t = 0; t < j; ++t) s = fma(-T[j][t], T[j][t], s);
-        if (!(s > 0.0)) {
-          atomicOr(flag, DEV_NOT_SPD);
-          s = 1.0;
-        }
-        piv = sqrt(s);
-        T[j][j] = piv;
-        rinv[j] = 1.0 / piv;
-      }
-      piv = __shfl_sync(0xffffffffu, piv, j & 31);
-      double ri = 1.0 / piv;
-      for (int half = 0; half < 2; ++half) {
-        int r = lane + 32 * half;
-        if (r > j && r < m) {
-          double s = T[r][j];
-          for (int t = 0; t < j; ++t) s = fma(-T[r][t], T[j][t], s);
-          T[r][j] = s * ri;
-        }
-      }
-      __syncwarp();
+  for (int k = 0; k < m; ++k) {
+    if (tid < m) {
+      fcol[tid] = A[tid * ld + k];
+      prow[tid] = A[k * ld + tid];
     }
-  }
-  __syncthreads();
-  {  // Z = L^{-1}, column c by threads 4c .. 4c + 3
-    const int cidx = tid >> 2, g = tid & 3;
-    const unsigned gm = 0xfu << (tid & 28);
-    for (int i = 0; i < m; ++i) {
-      if (cidx < m) {
-        if (i < cidx) {
-          if (g == 0) Z[i][cidx] = 0.0;
-        } else if (i == cidx) {
-          if (g == 0) Z[i][cidx] = rinv[i];
-        } else {
-          double s = 0.0;
-          for (int t = cidx + g; t < i; t += 4) s = fma(T[i][t], Z[t][cidx], s);
-          s += __shfl_xor_sync(gm, s, 1);
-          s += __shfl_xor_sync(gm, s, 2);
-          if (g == 0) Z[i][cidx] = -s * rinv[i];
-        }
-      }
-      __syncwarp(gm);
+    __syncthreads();
+    double p = prow[k];
+    if (!(p > 0.0)) {
+      if (tid == 0) atomicOr(flag, DEV_NOT_SPD);
+      p = 1.0;
     }
+    const double rp = 1.0 / p;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      int i = e / m, j = e % m;
+      double v;
+      if (i == k) v = (j == k) ? rp : prow[j] * rp;
+      else v = (j == k) ? -fcol[i] * rp : fma(-fcol[i] * rp, prow[j], A[i * ld + j]);
+      A[i * ld + j] = v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < m * m; e += blockDim.x) {
     int i = e / m, j = e % m;
-    double s = 0.0;
-    for (int t = (i > j ? i : j); t < m; ++t) s = fma(Z[t][i], Z[t][j], s);
-    G[e] = s;
+    G[e] = 0.5 * (A[i * ld + j] + A[j * ld + i]);
   }
 }
 
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s) {
-  if (m <= 0 || m > 64) return fail(RBF_EINVAL, "spd_inverse_small: m must be in [1, 64]");
-  { k_spd_inverse_small<<<1, 256, 0, s>>>(G, (int)m, c->dflag.as<int>()); ::rbf::note_launch(); }
+  if (m <= 0 || m > SPD_SMALL_MAX) return fail(RBF_EINVAL, "spd_inverse_small: m must be in [1, %d]", SPD_SMALL_MAX);
+  size_t smem = (size_t)(m * (m + 1) + 2 * m) * sizeof(double);
+  static bool attr[64] = {false};
+  if (!attr[c->device & 63]) {
+    size_t mx = (size_t)(SPD_SMALL_MAX * (SPD_SMALL_MAX + 1) + 2 * SPD_SMALL_MAX) * sizeof(double);
+    RBF_CUDA(cudaFuncSetAttribute(k_spd_inverse_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+    attr[c->device & 63] = true;
+  }
+  { k_spd_inverse_small<<<1, 256, smem, s>>>(G, (int)m, c->dflag.as<int>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }

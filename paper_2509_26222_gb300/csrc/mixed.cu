@@ -52,7 +52,7 @@ __global__ void k_mx_to_f32(const double* __restrict__ H, int64_t ldh, int64_t n
 // diagonal blocks only through Z.
 // ---------------------------------------------------------------------------
 constexpr int MXS_LD = MB + 1;
-constexpr size_t MXS_SMEM = (size_t)(3 * MB * MXS_LD + 32 * 33 + MB) * sizeof(float);
+constexpr size_t MXS_SMEM = (size_t)(5 * MB * MXS_LD + 32 * 33 + MB) * sizeof(float);
 
 // Cholesky of the 32 x 32 lower block T[o.., o..] in place and its inverse
 // into Z[o.., o..]; called by one full warp.  Lane i holds row i in
@@ -102,18 +102,38 @@ __device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, float* rd, int
 }
 
 __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t ldw, int64_t n, int64_t k,
-                                                 int kb, float* __restrict__ Zk, __nv_bfloat16* __restrict__ Ph,
-                                                 __nv_bfloat16* __restrict__ Pm, __nv_bfloat16* __restrict__ Pl,
-                                                 int* __restrict__ flag) {
+                                                 int kb, int prev, float* __restrict__ Zk,
+                                                 __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pm,
+                                                 __nv_bfloat16* __restrict__ Pl, int* __restrict__ flag) {
   extern __shared__ float mxs[];
   float* T = mxs;                     // diagonal tile -> L_kk
   float* Z = T + MB * MXS_LD;         // Z_kk = L_kk^{-1}
   float* X = Z + MB * MXS_LD;         // this CTA's panel rows
   float* Y = X + MB * MXS_LD;         // 32 x 33 temporary
   float* rd = Y + 32 * 33;            // 1 / L_jj
+  float* Lk = rd + MB;                // L_{k,k-1} (look-ahead update)
+  float* Lr = Lk + MB * MXS_LD;       // L_{rows,k-1}
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t k0 = k + kb;
   const int64_t r0 = k0 + (int64_t)blockIdx.x * MB;
+  if (prev) {
+    // this block column has every update but the one of the previous panel:
+    // W_kk -= L_{k,k-1} L_{k,k-1}^T and W_{rows,k} -= L_{rows,k-1} L_{k,k-1}^T
+    float lkv[MB * MB / 256], lrv[MB * MB / 256];
+#pragma unroll
+    for (int q = 0; q < MB * MB / 256; ++q) {
+      int e = tid + 256 * q, i = e / MB, j = e % MB;
+      lkv[q] = i < kb ? W[(k + i) * ldw + (k - MB) + j] : 0.f;
+      int64_t r = r0 + i;
+      lrv[q] = r < n ? W[r * ldw + (k - MB) + j] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < MB * MB / 256; ++q) {
+      int e = tid + 256 * q, i = e / MB, j = e % MB;
+      Lk[i * MXS_LD + j] = lkv[q];
+      Lr[i * MXS_LD + j] = lrv[q];
+    }
+  }
   {
     // all 32 loads of a thread are issued before the first one is used
     float tv[MB * MB / 256], xv[MB * MB / 256];
@@ -133,6 +153,41 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
     }
   }
   __syncthreads();
+  if (prev) {
+    const int pr = tid >> 4, pc = tid & 15;  // 4 x 4 blocks: rows 4 pr + u, columns pc + 16 q
+    float at[4][4], ax[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) at[u][q] = ax[u][q] = 0.f;
+#pragma unroll 4
+    for (int t = 0; t < MB; ++t) {
+      float kv[4], rv[4], cv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        kv[u] = Lk[(4 * pr + u) * MXS_LD + t];
+        rv[u] = Lr[(4 * pr + u) * MXS_LD + t];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cv[q] = Lk[(pc + 16 * q) * MXS_LD + t];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          at[u][q] = fmaf(kv[u], cv[q], at[u][q]);
+          ax[u][q] = fmaf(rv[u], cv[q], ax[u][q]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int i = 4 * pr + u, j = pc + 16 * q;
+        if (j <= i && i < kb) T[i * MXS_LD + j] -= at[u][q];
+        X[i * MXS_LD + j] -= ax[u][q];
+      }
+    __syncthreads();
+  }
   if (warp == 0) mx_chol_inv32(T, Z, rd, 0, flag);
   __syncthreads();
   const int bi = tid >> 3, bj = tid & 7;  // 32 x 32 products: row bi, columns bj + 8q
@@ -247,33 +302,77 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
     { k_mx_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, ldh, n, W, ldw); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
+  // bf16 slices of the panel, two sets (panel k is read by the trailing
+  // update of step k while step k + 1 writes the next one)
+  const size_t slice = (size_t)(n + MB) * MB;
   Buf& pb = c->scratch(26);
-  RBF_TRY(pb.ensure((size_t)3 * (n + MB) * MB * sizeof(__nv_bfloat16)));
-  __nv_bfloat16* Ph = pb.as<__nv_bfloat16>();
-  __nv_bfloat16* Pm = Ph + (n + MB) * MB;
-  __nv_bfloat16* Pl = Pm + (n + MB) * MB;
+  RBF_TRY(pb.ensure(2 * 3 * slice * sizeof(__nv_bfloat16)));
   static bool attr_set[64] = {false};
   if (!attr_set[c->device & 63]) {
     RBF_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
     RBF_CUDA(cudaFuncSetAttribute(k_mx_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MXS_SMEM));
     attr_set[c->device & 63] = true;
   }
+  // Look-ahead: step k applies the previous panel to its own block column,
+  // so the tensor-core update of the rest of the trailing matrix (columns
+  // beyond k + 1) runs on a side stream while step k + 1 factors.  Not used
+  // while the stream is being captured into a graph, nor where the eager and
+  // captured runs must give identical bits (batched patches): the update of
+  // the next block column then runs on the tensor cores with the rest.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RBF_CUDA(cudaStreamIsCapturing(s, &cap));
+  const bool la = c->la_ok && cap == cudaStreamCaptureStatusNone;
+  if (la && !c->la_stream) {
+    RBF_CUDA(cudaStreamCreateWithFlags(&c->la_stream, cudaStreamNonBlocking));
+    for (auto& ev : c->la_ev) RBF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  cudaStream_t side = la ? c->la_stream : s;
+  bool r_pending[2] = {false, false};
+  bool any_side = false;
   for (int64_t k = 0, step = 0; k < n; k += MB, ++step) {
     int kb = (int)((n - k) < MB ? (n - k) : MB);
     int64_t rows = n - k - kb;
+    const int par = (int)(step & 1);
+    __nv_bfloat16* Ph = pb.as<__nv_bfloat16>() + (size_t)par * 3 * slice;
+    __nv_bfloat16* Pm = Ph + slice;
+    __nv_bfloat16* Pl = Pm + slice;
+    if (la && r_pending[par]) {  // trailing update of step - 2: done with this slice set and column
+      RBF_CUDA(cudaStreamWaitEvent(s, c->la_ev[2 + par], 0));
+      r_pending[par] = false;
+    }
     {
       StageTimer st(c, RBF_STAGE_PANEL, s, (double)kb * kb * kb / 3.0 + (double)rows * kb * kb);
       unsigned g = rows > 0 ? (unsigned)((rows + MB - 1) / MB) : 1u;
-      { k_mx_step<<<g, 256, MXS_SMEM, s>>>(W, ldw, n, k, kb, Zd + step * MB * MB, Ph, Pm, Pl, flag); ::rbf::note_launch(); }
+      int prev = (la && step > 0) ? 1 : 0;
+      { k_mx_step<<<g, 256, MXS_SMEM, s>>>(W, ldw, n, k, kb, prev, Zd + step * MB * MB, Ph, Pm, Pl, flag); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
-    if (rows > 0) {
-      StageTimer st(c, RBF_STAGE_TRAILING, s, (double)rows * (double)(rows + 1) * kb);
-      int64_t T = (rows + tc::TILE - 1) / tc::TILE;
-      { tc::k_syrk_tc<<<(unsigned)(T * (T + 1) / 2), 128, tc::SMEM_BYTES, s>>>(W + (k + kb) * ldw + (k + kb), ldw,
-                                                                              rows, Ph, Pm, Pl, flag); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
+    const int64_t off = la ? MB : 0;  // with look-ahead the next block column is left to the next step
+    if (rows > off) {
+      const int64_t tr = rows - off;
+      if (la) {
+        RBF_CUDA(cudaEventRecord(c->la_ev[par], s));
+        RBF_CUDA(cudaStreamWaitEvent(side, c->la_ev[par], 0));
+      }
+      {
+        StageTimer st(c, RBF_STAGE_TRAILING, side, (double)tr * (double)(tr + 1) * kb);
+        int64_t T = (tr + tc::TILE - 1) / tc::TILE;
+        const int64_t o = k + kb + off;
+        { tc::k_syrk_tc<<<(unsigned)(T * (T + 1) / 2), 128, tc::SMEM_BYTES, side>>>(W + o * ldw + o, ldw, tr,
+                                                                                   Ph + off * MB, Pm + off * MB,
+                                                                                   Pl + off * MB, flag); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+      }
+      if (la) {
+        RBF_CUDA(cudaEventRecord(c->la_ev[2 + par], side));
+        r_pending[par] = true;
+        any_side = true;
+      }
     }
+  }
+  if (la && any_side) {
+    RBF_CUDA(cudaEventRecord(c->la_ev[4], side));
+    RBF_CUDA(cudaStreamWaitEvent(s, c->la_ev[4], 0));
   }
   return RBF_OK;
 }

@@ -364,6 +364,15 @@ __global__ void k_pick(const int32_t* __restrict__ flag, const int32_t* __restri
   ob[pos[q]] = b[q];
 }
 
+// D[u][v] = S[u][v] for a rows x cols block
+__global__ void k_copy_block(const double* __restrict__ S, int64_t lds, int64_t rows, int64_t cols,
+                             double* __restrict__ D, int64_t ldd) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t u = e / cols, v = e % cols;
+  D[u * ldd + v] = S[u * lds + v];
+}
+
 __global__ void k_scatter_diag(const int32_t* __restrict__ pos, int64_t m, double value,
                                double* __restrict__ Hn, int64_t ldn) {
   int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -436,6 +445,23 @@ __global__ void k_count_departed(const int32_t* __restrict__ ids, int64_t a, con
   int32_t id = ids[l];
   if (id < 0 || id >= M) return;
   if (departed[id]) atomicAdd(count, 1);
+}
+
+// ret[q] = 1 if entering center q (new-local El[q]) left an earlier block
+__global__ void k_ret_flags(const int32_t* __restrict__ ids, const int32_t* __restrict__ El, int64_t e,
+                            const int32_t* __restrict__ departed, int32_t* __restrict__ ret) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= e) return;
+  ret[q] = departed[ids[El[q]]] ? 1 : 0;
+}
+
+// split El into returning (flag set) and fresh lists, order kept
+__global__ void k_split_flags(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t m,
+                              const int32_t* __restrict__ src, int32_t* __restrict__ yes, int32_t* __restrict__ no) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  if (flag[q]) yes[pos[q]] = src[q];
+  else no[q - pos[q]] = src[q];
 }
 
 __global__ void k_mark_departed(const int32_t* __restrict__ ids, const int32_t* __restrict__ lpos, int64_t d,
@@ -719,7 +745,22 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
         { k_gather_sym<<<nblk(t * t), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), t,
                                                  T.as<double>(), t); ::rbf::note_launch(); }
         RBF_CUDA(cudaGetLastError());
-        RBF_TRY(potrf_lower(c, T.as<double>(), t, t, d, false, s));
+        if (d <= SPD_SMALL_MAX) {
+          // H_NN -= H_ND (H_DD^{-1} H_DN), with H_DD^{-1} by the one-CTA inverse
+          Buf& Gd = c->scratch(84);
+          Buf& Yb = c->scratch(85);
+          RBF_TRY(Gd.ensure((size_t)d * d * sizeof(double)));
+          RBF_TRY(Yb.ensure((size_t)d * nN * sizeof(double)));
+          { k_copy_block<<<nblk(d * d), 256, 0, s>>>(T.as<double>(), t, d, d, Gd.as<double>(), d); ::rbf::note_launch(); }
+          RBF_CUDA(cudaGetLastError());
+          RBF_TRY(spd_inverse_small(c, Gd.as<double>(), d, s));
+          RBF_TRY(gemm_f64(c, false, false, d, nN, d, 1.0, Gd.as<double>(), d, T.as<double>() + d, t, 0.0,
+                           Yb.as<double>(), nN, s));
+          RBF_TRY(gemm_f64(c, false, false, nN, nN, d, -1.0, T.as<double>() + d * t, t, Yb.as<double>(), nN, 1.0,
+                           T.as<double>() + d * t + d, t, s));
+        } else {
+          RBF_TRY(potrf_lower(c, T.as<double>(), t, t, d, false, s));
+        }
         { k_scatter_sym<<<nblk(nN * nN), 256, 0, s>>>(T.as<double>() + d * t + d, t, nN, Nn.as<int32_t>(),
                                                     Hn.as<double>(), ld); ::rbf::note_launch(); }
         RBF_CUDA(cudaGetLastError());
@@ -740,14 +781,37 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       { k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     } else {
-      Buf& Gb = c->scratch(42);
-      RBF_TRY(Gb.ensure((size_t)e * e * sizeof(double)));
-      { k_gather_global<<<nblk(e * e), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
-                                                   El.as<int32_t>(), e, Gb.as<double>()); ::rbf::note_launch(); }
+      // the stored covariance couples the returning centers R only among
+      // themselves (fresh ones F keep the uncoupled prior), so the block's
+      // inverse is diag(P_RR^{-1}, lambda I)
+      const int64_t r = e_returning, f = e - e_returning;
+      Buf& rf = c->scratch(80);
+      Buf& rp = c->scratch(81);
+      Buf& Rl = c->scratch(82);
+      Buf& Fl = c->scratch(83);
+      RBF_TRY(rf.ensure((size_t)(e + 1) * sizeof(int32_t)));
+      RBF_TRY(rp.ensure((size_t)(e + 1) * sizeof(int32_t)));
+      RBF_TRY(Rl.ensure((size_t)(r + 1) * sizeof(int32_t)));
+      RBF_TRY(Fl.ensure((size_t)(f + 1) * sizeof(int32_t)));
+      { k_ret_flags<<<nblk(e), 256, 0, s>>>(An.as<int32_t>(), El.as<int32_t>(), e, c->departed.as<int32_t>(),
+                                          rf.as<int32_t>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
-      if (e <= 64) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), e, s));
-      else RBF_TRY(spd_inverse(c, Gb.as<double>(), e, s, 43));
-      { k_scatter_sym<<<nblk(e * e), 256, 0, s>>>(Gb.as<double>(), e, e, El.as<int32_t>(), Hn.as<double>(),
+      RBF_TRY(scan_i32(c, rf.as<int32_t>(), rp.as<int32_t>(), e, s, 77));
+      { k_split_flags<<<nblk(e), 256, 0, s>>>(rf.as<int32_t>(), rp.as<int32_t>(), e, El.as<int32_t>(),
+                                            Rl.as<int32_t>(), Fl.as<int32_t>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      if (f > 0) {
+        { k_scatter_diag<<<nblk(f), 256, 0, s>>>(Fl.as<int32_t>(), f, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+      }
+      Buf& Gb = c->scratch(42);
+      RBF_TRY(Gb.ensure((size_t)r * r * sizeof(double)));
+      { k_gather_global<<<nblk(r * r), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
+                                                   Rl.as<int32_t>(), r, Gb.as<double>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, s));
+      else RBF_TRY(spd_inverse(c, Gb.as<double>(), r, s, 43));
+      { k_scatter_sym<<<nblk(r * r), 256, 0, s>>>(Gb.as<double>(), r, r, Rl.as<int32_t>(), Hn.as<double>(),
                                                 ld); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
