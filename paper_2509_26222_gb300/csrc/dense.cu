@@ -376,12 +376,14 @@ __global__ void __launch_bounds__(256) k_spd_inverse_small(double* __restrict__ 
       p = 1.0;
     }
     const double rp = 1.0 / p;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      int i = e / m, j = e % m;
-      double v;
-      if (i == k) v = (j == k) ? rp : prow[j] * rp;
-      else v = (j == k) ? -fcol[i] * rp : fma(-fcol[i] * rp, prow[j], A[i * ld + j]);
-      A[i * ld + j] = v;
+    for (int i = tid >> 4; i < m; i += 16) {  // 16 x 16 threads, no index division
+      const double fi = -fcol[i] * rp;
+      for (int j = tid & 15; j < m; j += 16) {
+        double v;
+        if (i == k) v = (j == k) ? rp : prow[j] * rp;
+        else v = (j == k) ? fi : fma(fi, prow[j], A[i * ld + j]);
+        A[i * ld + j] = v;
+      }
     }
     __syncthreads();
   }

@@ -619,6 +619,15 @@ __global__ void k_sym_gather(const double* __restrict__ X, int64_t k, const int3
   P[e] = 0.5 * (X[(int64_t)pos[u] * k + v] + X[(int64_t)pos[v] * k + u]);
 }
 
+// P = sym(X[pos, :]) + sym(G), G = X^T R
+__global__ void k_cov_second_order(const double* __restrict__ X, int64_t k, const int32_t* __restrict__ pos,
+                                   const double* __restrict__ G, double* __restrict__ P) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  int64_t u = e / k, v = e % k;
+  P[e] = 0.5 * (X[(int64_t)pos[u] * k + v] + X[(int64_t)pos[v] * k + u]) + 0.5 * (G[u * k + v] + G[v * k + u]);
+}
+
 rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
                      const float* Zd, const float* Zi, int64_t n, double* B, int64_t k, const int32_t* pos,
                      int sweeps, double* P, cudaStream_t s) {
@@ -645,10 +654,11 @@ rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const 
     { k_residual_multi<<<nw, 256, 0, s>>>(H, n, ldh, B, e0.as<double>(), k, R); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
-  { k_sym_gather<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(B, k, pos, P); ::rbf::note_launch(); }
+  Buf& gq = c->scratch(86);
+  RBF_TRY(gq.ensure((size_t)k * k * sizeof(double)));
+  RBF_TRY(gemm_f64(c, true, false, k, k, n, 1.0, B, k, R, k, 0.0, gq.as<double>(), k, s));
+  { k_cov_second_order<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(B, k, pos, gq.as<double>(), P); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  RBF_TRY(gemm_f64(c, true, false, k, k, n, 0.5, B, k, R, k, 1.0, P, k, s));
-  RBF_TRY(gemm_f64(c, true, false, k, k, n, 0.5, R, k, B, k, 1.0, P, k, s));
   return RBF_OK;
 }
 

@@ -90,3 +90,28 @@ def test_wendland_row_is_phi_and_noise_is_unused():
     r = np.linalg.norm(x[:, None] - c[None], axis=2)
     assert np.array_equal(a, b)
     assert np.allclose(a, O.phi(r, O.WENDLAND, rho=0.6))
+
+
+def _golden_rows():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "basis_closed_form.txt")
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            yield line.split()
+
+
+def test_basis_matches_closed_form_fixture():
+    """Hand-derived values of phi, its gradient coefficient and the Gaussian
+    regression-row scale (tests/golden/basis_closed_form.txt)."""
+    rows = list(_golden_rows())
+    assert len(rows) == 9
+    for kind, r, par, noise, ph, g, row in rows:
+        kind, r, par = int(kind), float(r), float(par)
+        kw = dict(rho=par) if kind == O.WENDLAND else dict(sigma=par)
+        if ph != "-":
+            assert O.phi(r, kind, **kw) == pytest.approx(float(ph), rel=1e-13, abs=1e-15)
+            assert O.grad_coef(r, kind, **kw) == pytest.approx(float(g), rel=1e-13, abs=1e-15)
+        if row != "-":
+            m = O.design_rows(np.array([[r, 0.0]]), np.zeros((1, 2)), kind, sigma=par, noise=float(noise))
+            assert m[0, 0] == pytest.approx(float(row), rel=1e-13)
