@@ -52,20 +52,21 @@ __global__ void k_mx_to_f32(const double* __restrict__ H, int64_t ldh, int64_t n
 // diagonal blocks only through Z.
 // ---------------------------------------------------------------------------
 constexpr int MXS_LD = MB + 1;
-constexpr size_t MXS_SMEM = (size_t)(5 * MB * MXS_LD + 32 * 33 + MB) * sizeof(float);
+constexpr size_t MXS_SMEM = (size_t)(5 * MB * MXS_LD + 32 * 33 + MB + 64) * sizeof(float);
 
-// Cholesky of the 32 x 32 lower block T[o.., o..] in place and its inverse
-// into Z[o.., o..]; called by one full warp.  Lane i holds row i in
-// registers; at step k, a[p] is entry (i, k + p).  The rank-1 update is
-// applied to every lane and column without masks: entries above the
-// diagonal (and past column 31) collect finite values that are never read,
-// because the column written at step k is masked to zero above the
-// diagonal.  rd[o + k] = 1 / L_kk.
-__device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, float* rd, int o, int* flag) {
+// Cholesky of the 32 x 32 lower block T[o.., o..] in place (one full warp;
+// lane i holds row i in registers, a[p] = entry (i, k + p) at step k).  The
+// finished column k goes through shared memory (col) to every lane; the
+// rank-1 update is applied to every lane and column without masks: entries
+// above the diagonal (and past column 31) collect finite values that are
+// never read, because the column written at step k is masked to zero above
+// the diagonal.  rd[o + k] = 1 / L_kk.
+__device__ __forceinline__ void mx_chol32(float* T, float* rd, float* col, int o, int* flag) {
   const int lane = threadIdx.x & 31;
   float a[32];
 #pragma unroll
   for (int p = 0; p < 32; ++p) a[p] = (p <= lane) ? T[(o + lane) * MXS_LD + o + p] : 0.f;
+  col[32 + lane] = 0.f;
   bool bad = false;
 #pragma unroll 1
   for (int k = 0; k < 32; ++k) {
@@ -74,14 +75,22 @@ __device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, float* rd, int
     float r = rsqrtf(d);
     float lik = (lane >= k) ? a[0] * r : 0.f;
     T[(o + lane) * MXS_LD + o + k] = lik;  // column k of L (zero above the diagonal)
+    col[lane] = lik;
     if (lane == 0) rd[o + k] = r;
+    __syncwarp();
+    const float* cb = col + k;
 #pragma unroll
-    for (int p = 1; p < 32; ++p) a[p - 1] = fmaf(-lik, __shfl_sync(0xffffffffu, lik, (k + p) & 31), a[p]);
+    for (int p = 1; p < 32; ++p) a[p - 1] = fmaf(-lik, cb[p], a[p]);
     a[31] = 0.f;
+    __syncwarp();
   }
   if (bad && lane == 0) atomicOr(flag, DEV_NOT_SPD);
-  __syncwarp();
-  // column `lane` of L^{-1} by forward substitution, four partial sums per row
+}
+
+// Z[o.., o..] = inverse of the 32 x 32 factor in T[o.., o..] (one full warp):
+// column `lane` by forward substitution, four partial sums per row.
+__device__ __forceinline__ void mx_inv32(const float* T, float* Z, const float* rd, int o) {
+  const int lane = threadIdx.x & 31;
   float x[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
@@ -101,6 +110,30 @@ __device__ __forceinline__ void mx_chol_inv32(float* T, float* Z, float* rd, int
   }
 }
 
+// L21 = A21 L11^{-T} by substitution, row 32 + lane per lane (one full warp).
+__device__ __forceinline__ void mx_l21(float* T, const float* rd) {
+  const int lane = threadIdx.x & 31;
+  float* row = T + (32 + lane) * MXS_LD;
+  float l[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float* Lj = T + j * MXS_LD;
+    float s0 = row[j], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int t = 0; t + 3 < j; t += 4) {
+      s0 = fmaf(-l[t], Lj[t], s0);
+      s1 = fmaf(-l[t + 1], Lj[t + 1], s1);
+      s2 = fmaf(-l[t + 2], Lj[t + 2], s2);
+      s3 = fmaf(-l[t + 3], Lj[t + 3], s3);
+    }
+#pragma unroll
+    for (int t = j & ~3; t < j; ++t) s0 = fmaf(-l[t], Lj[t], s0);
+    l[j] = ((s0 + s1) + (s2 + s3)) * rd[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) row[j] = l[j];
+}
+
 __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t ldw, int64_t n, int64_t k,
                                                  int kb, int prev, float* __restrict__ Zk,
                                                  __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pm,
@@ -113,36 +146,23 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
   float* rd = Y + 32 * 33;            // 1 / L_jj
   float* Lk = rd + MB;                // L_{k,k-1} (look-ahead update)
   float* Lr = Lk + MB * MXS_LD;       // L_{rows,k-1}
-  const int tid = threadIdx.x, warp = tid >> 5;
+  float* col = Lr + MB * MXS_LD;      // column broadcast of the 32 x 32 Cholesky
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t k0 = k + kb;
   const int64_t r0 = k0 + (int64_t)blockIdx.x * MB;
-  if (prev) {
-    // this block column has every update but the one of the previous panel:
-    // W_kk -= L_{k,k-1} L_{k,k-1}^T and W_{rows,k} -= L_{rows,k-1} L_{k,k-1}^T
-    float lkv[MB * MB / 256], lrv[MB * MB / 256];
-#pragma unroll
-    for (int q = 0; q < MB * MB / 256; ++q) {
-      int e = tid + 256 * q, i = e / MB, j = e % MB;
-      lkv[q] = i < kb ? W[(k + i) * ldw + (k - MB) + j] : 0.f;
-      int64_t r = r0 + i;
-      lrv[q] = r < n ? W[r * ldw + (k - MB) + j] : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < MB * MB / 256; ++q) {
-      int e = tid + 256 * q, i = e / MB, j = e % MB;
-      Lk[i * MXS_LD + j] = lkv[q];
-      Lr[i * MXS_LD + j] = lrv[q];
-    }
-  }
   {
-    // all 32 loads of a thread are issued before the first one is used
-    float tv[MB * MB / 256], xv[MB * MB / 256];
+    // every load of a thread is issued before the first one is used
+    float tv[MB * MB / 256], xv[MB * MB / 256], lkv[MB * MB / 256], lrv[MB * MB / 256];
 #pragma unroll
     for (int q = 0; q < MB * MB / 256; ++q) {
       int e = tid + 256 * q, i = e / MB, j = e % MB;
-      tv[q] = (i < kb && j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
       int64_t r = r0 + i;
+      tv[q] = (i < kb && j <= i) ? W[(k + i) * ldw + k + j] : 0.f;
       xv[q] = (r < n && j < kb) ? W[r * ldw + k + j] : 0.f;
+      // this block column has every update but the one of the previous
+      // panel: W_kk -= L_{k,k-1} L_{k,k-1}^T, W_{rows,k} -= L_{rows,k-1} L_{k,k-1}^T
+      lkv[q] = (prev && i < kb) ? W[(k + i) * ldw + (k - MB) + j] : 0.f;
+      lrv[q] = (prev && r < n) ? W[r * ldw + (k - MB) + j] : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < MB * MB / 256; ++q) {
@@ -150,33 +170,30 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
       T[i * MXS_LD + j] = (i >= kb && i == j) ? 1.f : tv[q];  // identity beyond a ragged last block
       Z[i * MXS_LD + j] = 0.f;
       X[i * MXS_LD + j] = xv[q];
+      Lk[i * MXS_LD + j] = lkv[q];
+      Lr[i * MXS_LD + j] = lrv[q];
     }
   }
   __syncthreads();
   if (prev) {
-    const int pr = tid >> 4, pc = tid & 15;  // 4 x 4 blocks: rows 4 pr + u, columns pc + 16 q
-    float at[4][4], ax[4][4];
+    // T -= Lk Lk^T (lower part), 4 x 4 blocks: rows 4 pr + u, columns pc + 16 q
+    const int pr = tid >> 4, pc = tid & 15;
+    float at[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) at[u][q] = ax[u][q] = 0.f;
+      for (int q = 0; q < 4; ++q) at[u][q] = 0.f;
 #pragma unroll 4
     for (int t = 0; t < MB; ++t) {
-      float kv[4], rv[4], cv[4];
+      float kv[4], cv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        kv[u] = Lk[(4 * pr + u) * MXS_LD + t];
-        rv[u] = Lr[(4 * pr + u) * MXS_LD + t];
-      }
+      for (int u = 0; u < 4; ++u) kv[u] = Lk[(4 * pr + u) * MXS_LD + t];
 #pragma unroll
       for (int q = 0; q < 4; ++q) cv[q] = Lk[(pc + 16 * q) * MXS_LD + t];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          at[u][q] = fmaf(kv[u], cv[q], at[u][q]);
-          ax[u][q] = fmaf(rv[u], cv[q], ax[u][q]);
-        }
+        for (int q = 0; q < 4; ++q) at[u][q] = fmaf(kv[u], cv[q], at[u][q]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -184,29 +201,47 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
       for (int q = 0; q < 4; ++q) {
         int i = 4 * pr + u, j = pc + 16 * q;
         if (j <= i && i < kb) T[i * MXS_LD + j] -= at[u][q];
-        X[i * MXS_LD + j] -= ax[u][q];
       }
     __syncthreads();
   }
-  if (warp == 0) mx_chol_inv32(T, Z, rd, 0, flag);
+  if (warp == 0) {
+    mx_chol32(T, rd, col, 0, flag);
+  } else if (prev) {
+    // X -= Lr Lk^T by warps 1-7 while warp 0 factors: rows w - 1 + 7 m, columns lane and lane + 32
+    float ax[10][2];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) ax[m][0] = ax[m][1] = 0.f;
+#pragma unroll 2
+    for (int t = 0; t < MB; ++t) {
+      float c0 = Lk[lane * MXS_LD + t], c1 = Lk[(lane + 32) * MXS_LD + t];
+#pragma unroll
+      for (int m = 0; m < 10; ++m) {
+        int i = warp - 1 + 7 * m;
+        if (i < MB) {
+          float rv = Lr[i * MXS_LD + t];
+          ax[m][0] = fmaf(rv, c0, ax[m][0]);
+          ax[m][1] = fmaf(rv, c1, ax[m][1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 10; ++m) {
+      int i = warp - 1 + 7 * m;
+      if (i < MB) {
+        X[i * MXS_LD + lane] -= ax[m][0];
+        X[i * MXS_LD + lane + 32] -= ax[m][1];
+      }
+    }
+  }
+  __syncthreads();
+  // Z11 (warp 0) while warp 1 forms L21 = A21 L11^{-T} by substitution
+  if (warp == 0) mx_inv32(T, Z, rd, 0);
+  else if (warp == 1) mx_l21(T, rd);
   __syncthreads();
   const int bi = tid >> 3, bj = tid & 7;  // 32 x 32 products: row bi, columns bj + 8q
   {
-    // L21 = A21 Z11^T
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int t = 0; t < 32; ++t) {
-      float av = T[(32 + bi) * MXS_LD + t];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(av, Z[(bj + 8 * q) * MXS_LD + t], acc[q]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) T[(32 + bi) * MXS_LD + bj + 8 * q] = acc[q];
-    __syncthreads();
     // S = A22 - L21 L21^T (lower part)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
     for (int t = 0; t < 32; ++t) {
       float lv = T[(32 + bi) * MXS_LD + t];
@@ -220,7 +255,10 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
     }
     __syncthreads();
   }
-  if (warp == 0) mx_chol_inv32(T, Z, rd, 32, flag);
+  if (warp == 0) {
+    mx_chol32(T, rd, col, 32, flag);
+    mx_inv32(T, Z, rd, 32);
+  }
   {
     // Y = L21 Z11 (all warps but the first; the first joins after its factorization)
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
