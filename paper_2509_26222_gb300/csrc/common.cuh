@@ -270,6 +270,8 @@ rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t 
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
                        cudaStream_t s);
 rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, int64_t m, cudaStream_t s);
+rbf_status inv_solve_unit(Ctx* c, const float* Z, int64_t ldz, int64_t n, const int32_t* pos, int64_t m, float* F,
+                          cudaStream_t s);
 constexpr int SPD_SMALL_MAX = 128;  // largest order of spd_inverse_small (one CTA, shared memory)
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,

@@ -14,7 +14,8 @@
 //   the 64 x 64 blocks from the factorization itself).
 //
 // Z has the factor's shape (row-major, leading dimension ldz) with zeros
-// above the diagonal.  The solves are Y = Z F followed by F = Z^T Y.
+// above the diagonal; its transpose follows it in the same buffer (rows
+// n .. 2n - 1).  The solves are Y = Z F followed by F = Z^T Y.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(256) k_trtri_level(int kind, int64_t b, int64_
   }
 }
 
-// Y = Z F (forward, Z lower) or Y = Z^T F (backward) for m > GEMV_M
-// right-hand sides; F, Y row-major n x m.  blockIdx.z splits K; partial
+// Y = Z F (forward, Z lower) or Y = Zt F (backward, Zt = Z^T upper) for
+// m > GEMV_M right-hand sides; F, Y row-major n x m.  blockIdx.z splits K; partial
 // products go to P[z] and are summed by k_sum_partials.
 __global__ void __launch_bounds__(256) k_inv_apply(bool backward, int64_t n, int64_t m, const float* __restrict__ Z,
                                                    int64_t ldz, const float* __restrict__ F, float* __restrict__ P,
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) k_inv_apply(bool backward, int64_t n, int
   int64_t sb = kb + (int64_t)blockIdx.z * chunk;
   int64_t se = (sb + chunk) < ke ? (sb + chunk) : ke;
   float acc[4][4] = {};
-  Mat A{Z, ldz, backward};
+  Mat A{Z, ldz, false};  // Z (forward) or its transpose stored row-major (backward)
   Mat B{F, m, false};
   if (sb < se) tile_mma(acc, A, B, i0, j0, n, m, sb, se, As, Bs);
   tile_store(acc, 1.f, P + (int64_t)blockIdx.z * n * m, m, i0, j0, n, m);
@@ -180,29 +181,32 @@ __global__ void k_sum_partials(const float* __restrict__ P, int nsplit, int64_t 
   Y[e] = s;
 }
 
-// Y = Z F for m <= GEMV_M: one warp per row, lanes over the row of Z, four
-// loads of Z in flight per lane.
-__global__ void __launch_bounds__(256) k_inv_fwd_gemv(int64_t n, int m, const float* __restrict__ Z, int64_t ldz,
-                                                      const float* __restrict__ F, float* __restrict__ Y) {
+// Y = A F for m <= GEMV_M with A = Z (lower: row i over k <= i) or A = Z^T
+// stored transposed (upper: row i over k >= i): one warp per row, lanes over
+// the row, eight loads of A in flight per lane.
+template <bool UPPER>
+__global__ void __launch_bounds__(256) k_inv_gemv(int64_t n, int m, const float* __restrict__ A, int64_t lda,
+                                                  const float* __restrict__ F, float* __restrict__ Y) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= n) return;
+  const int64_t lo = UPPER ? i : 0, hi = UPPER ? n : i + 1;
   float acc[GEMV_M];
 #pragma unroll
   for (int j = 0; j < GEMV_M; ++j) acc[j] = 0.f;
-  const float* zr = Z + i * ldz;
-  for (int64_t k0 = lane; k0 <= i; k0 += 128) {
-    float z[4], f[4][GEMV_M];
+  const float* ar = A + i * lda;
+  for (int64_t k0 = lo + lane; k0 < hi; k0 += 256) {
+    float z[8], f[8][GEMV_M];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       int64_t k = k0 + 32 * u;
-      bool ok = k <= i;
-      z[u] = ok ? zr[k] : 0.f;
+      bool ok = k < hi;
+      z[u] = ok ? ar[k] : 0.f;
 #pragma unroll
       for (int j = 0; j < GEMV_M; ++j) f[u][j] = (ok && j < m) ? F[k * m + j] : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
       for (int j = 0; j < GEMV_M; ++j) acc[j] = fmaf(z[u], f[u][j], acc[j]);
   }
@@ -216,45 +220,29 @@ __global__ void __launch_bounds__(256) k_inv_fwd_gemv(int64_t n, int m, const fl
   }
 }
 
-// X = Z^T Y for m <= GEMV_M: a CTA of 32 warps owns 32 consecutive outputs
-// (one per lane, so each row of Z is read as one 128-byte segment); the warps
-// take interleaved rows k >= i0, four in flight each, and the partial sums
-// are added in shared memory.
-constexpr int BWD_WARPS = 32;
-__global__ void __launch_bounds__(BWD_WARPS * 32) k_inv_bwd_gemv(int64_t n, int m, const float* __restrict__ Z,
-                                                                 int64_t ldz, const float* __restrict__ Y,
-                                                                 float* __restrict__ X) {
-  __shared__ float part[BWD_WARPS][GEMV_M][33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
-  const int64_t i = i0 + lane;
-  float acc[GEMV_M];
-#pragma unroll
-  for (int j = 0; j < GEMV_M; ++j) acc[j] = 0.f;
-  for (int64_t k0 = i0 + w; k0 < n; k0 += 4 * BWD_WARPS) {
-    float z[4], y[4][GEMV_M];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int64_t k = k0 + BWD_WARPS * u;
-      bool ok = k < n;
-      z[u] = (ok && i < n && k >= i) ? Z[k * ldz + i] : 0.f;
-#pragma unroll
-      for (int j = 0; j < GEMV_M; ++j) y[u][j] = (ok && j < m) ? Y[k * m + j] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int j = 0; j < GEMV_M; ++j) acc[j] = fmaf(z[u], y[u][j], acc[j]);
+// Zt = Z^T (n x n, both with leading dimension ld), 32 x 32 tiles
+__global__ void k_transpose32(const float* __restrict__ Z, int64_t n, int64_t ld, float* __restrict__ Zt) {
+  __shared__ float t[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = by + r, j = bx + tx;
+    t[r][tx] = (i < n && j < n) ? Z[i * ld + j] : 0.f;
   }
-#pragma unroll
-  for (int j = 0; j < GEMV_M; ++j) part[w][j][lane] = acc[j];
   __syncthreads();
-  if (w < GEMV_M && w < m && i < n) {
-    float s = 0.f;
-#pragma unroll 8
-    for (int q = 0; q < BWD_WARPS; ++q) s += part[q][w][lane];
-    X[i * m + w] = s;
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = bx + r, j = by + tx;
+    if (i < n && j < n) Zt[i * ld + j] = t[tx][r];
   }
+}
+
+// Y[i][u] = Z[i][pos[u]]: the product of Z with unit columns
+__global__ void k_gather_cols(const float* __restrict__ Z, int64_t n, int64_t ld, const int32_t* __restrict__ pos,
+                              int64_t m, float* __restrict__ Y) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * m) return;
+  int64_t i = e / m, u = e % m;
+  Y[e] = Z[i * ld + pos[u]];
 }
 
 unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -279,6 +267,9 @@ rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const flo
       RBF_CUDA(cudaGetLastError());
     }
   }
+  // Z^T stored row-major, so that products with Z^T read rows too
+  { k_transpose32<<<dim3(cdiv(n, 32), cdiv(n, 32)), 256, 0, s>>>(Z, n, ldz, Z + n * ldz); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
 
@@ -288,10 +279,11 @@ rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, i
   RBF_TRY(yb.ensure((size_t)n * m * sizeof(float)));
   float* Y = yb.as<float>();
   StageTimer st(c, RBF_STAGE_INVAPPLY, s, 2.0 * (double)n * n * m);
+  const float* Zt = Z + n * ldz;
   if (m <= GEMV_M) {
-    { k_inv_fwd_gemv<<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Z, ldz, F, Y); ::rbf::note_launch(); }
+    { k_inv_gemv<false><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Z, ldz, F, Y); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    { k_inv_bwd_gemv<<<cdiv(n, 32), BWD_WARPS * 32, 0, s>>>(n, (int)m, Z, ldz, Y, F); ::rbf::note_launch(); }
+    { k_inv_gemv<true><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Zt, ldz, Y, F); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     return RBF_OK;
   }
@@ -308,9 +300,41 @@ rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, i
   RBF_CUDA(cudaGetLastError());
   { k_sum_partials<<<nr, 256, 0, s>>>(P, nsplit, n * m, Y); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  { k_inv_apply<<<grid, 256, 0, s>>>(true, n, m, Z, ldz, Y, P, nsplit); ::rbf::note_launch(); }
+  { k_inv_apply<<<grid, 256, 0, s>>>(true, n, m, Zt, ldz, Y, P, nsplit); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   { k_sum_partials<<<nr, 256, 0, s>>>(P, nsplit, n * m, F); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}
+
+// F = Z^T (Z E_P) for unit columns E_P at positions pos (n x m, row-major):
+// the first product is a gather of columns of Z.
+rbf_status inv_solve_unit(Ctx* c, const float* Z, int64_t ldz, int64_t n, const int32_t* pos, int64_t m, float* F,
+                          cudaStream_t s) {
+  if (n <= 0 || m <= 0) return RBF_OK;
+  Buf& yb = c->scratch(66);
+  RBF_TRY(yb.ensure((size_t)n * m * sizeof(float)));
+  float* Y = yb.as<float>();
+  StageTimer st(c, RBF_STAGE_INVAPPLY, s, (double)n * n * m);
+  const float* Zt = Z + n * ldz;
+  { k_gather_cols<<<cdiv(n * m, 256), 256, 0, s>>>(Z, n, ldz, pos, m, Y); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  if (m <= GEMV_M) {
+    { k_inv_gemv<true><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Zt, ldz, Y, F); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    return RBF_OK;
+  }
+  int64_t tiles = (int64_t)cdiv(n, TG) * cdiv(m, TG);
+  int nsplit = (int)(2 * 152 / tiles);
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > 8) nsplit = 8;
+  Buf& pb = c->scratch(67);
+  RBF_TRY(pb.ensure((size_t)nsplit * n * m * sizeof(float)));
+  float* P = pb.as<float>();
+  dim3 grid(cdiv(m, TG), cdiv(n, TG), nsplit);
+  { k_inv_apply<<<grid, 256, 0, s>>>(true, n, m, Zt, ldz, Y, P, nsplit); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  { k_sum_partials<<<cdiv(n * m, 256), 256, 0, s>>>(P, nsplit, n * m, F); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }

@@ -558,6 +558,10 @@ __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
 __global__ void k_add_f32_to_f64(double* __restrict__ x, const float* __restrict__ c, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] += (double)c[i];
@@ -683,7 +687,16 @@ rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const 
   RBF_TRY(e0.ensure((size_t)tot * sizeof(double)));
   RBF_TRY(rr.ensure((size_t)tot * sizeof(double)));
   RBF_CUDA(cudaMemcpyAsync(e0.p, B, (size_t)tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, sweeps - 1, s));
+  if (Zi && sweeps == 2) {
+    // X = Z^T Z E_D: the first product is a gather of columns of Z
+    Buf& fb = c->scratch(61);
+    RBF_TRY(fb.ensure((size_t)tot * sizeof(float)));
+    RBF_TRY(inv_solve_unit(c, Zi, ldw, n, pos, k, fb.as<float>(), s));
+    { k_f32_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(fb.as<float>(), B, tot); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  } else {
+    RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, sweeps - 1, s));
+  }
   double* R = rr.as<double>();
   if (Hs) {
     RBF_TRY(csr_residual(*Hs, B, e0.as<double>(), k, R, s));

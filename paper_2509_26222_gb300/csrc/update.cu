@@ -858,7 +858,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_TRY(Zdn.ensure((size_t)((an + 63) / 64) * 64 * 64 * sizeof(float)));
     RBF_TRY(potrf_mixed(c, Hn.as<double>(), ld, an, Wn.as<float>(), ldw, Zdn.as<float>(), s));
     if (use_inv) {
-      RBF_TRY(Zin.ensure((size_t)an * ldw * sizeof(float)));
+      RBF_TRY(Zin.ensure((size_t)2 * an * ldw * sizeof(float)));  // L^{-1} and its transpose
       RBF_TRY(trtri_mixed(c, Wn.as<float>(), ldw, an, Zdn.as<float>(), Zin.as<float>(), ldw, s));
     }
   } else {
