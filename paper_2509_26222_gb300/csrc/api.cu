@@ -424,6 +424,7 @@ rbf_status reset_update_state(Ctx* c) {
   c->a = 0;
   c->pg_on = false;
   c->zi_valid = false;
+  c->bw_lf = BW_DENSE;
   c->Hs.valid = false;
   c->Hs_next.valid = false;
   c->Pg.release();

@@ -3,12 +3,11 @@
 // (Eq. RBF_fml), in one call.
 //
 // Every patch's pipeline has sizes bounded by its M, n and Q, so it needs no
-// host synchronization: points are counting-sorted into the cells of the
-// patch lattice, each center gathers its row of m~ m~^T and its entry of m~ z
-// from the points of the cells within the support (deterministic order), the
-// M x M information matrix lambda I + m~ m~^T is factored (FP64, or the
-// mixed-precision tensor-core path) and solved, and the queries are evaluated
-// over the lattice window.  Patches are spread over internal streams, each
+// host synchronization: every point finds its neighbour nodes in the patch
+// lattice and adds its products to m~ m~^T and m~ z by exact (order-independent)
+// integer accumulation, the M x M information matrix lambda I + m~ m~^T is
+// factored within its band (FP64, or the mixed-precision tensor-core path)
+// and solved, and the queries are evaluated over the lattice window.  Patches are spread over internal streams, each
 // with its own workspace context; the first call for a batch shape runs
 // eagerly (sizing every buffer), later calls with the same descriptors replay
 // a CUDA graph recorded from the same enqueue sequence.
@@ -40,107 +39,89 @@ __device__ __forceinline__ double node_coord(double x0, int i, double h) {
   return __dadd_rn(x0, __dmul_rn((double)i + 0.5, h));
 }
 
-__global__ void k_bp_cells(PatchGeom G, const float* __restrict__ pts, int32_t* __restrict__ cell,
-                           int32_t* __restrict__ cnt, int* __restrict__ status) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per point: its neighbour nodes (the float32 rule at the assembly
+// radius over the 2 rca x 2 rca node window), their regression entries, and
+// the exact integer accumulation of every product m_{i,l1} m_{i,l2} (lower
+// triangle) and m_{i,l} z_i (the accumulation of the main update path).
+// Non-finite points set DEV_BAD_INDEX and are skipped.
+constexpr int BP_MAXK = 128;  // window nodes per point kept in shared memory
+__global__ void __launch_bounds__(256) k_bp_gram(PatchGeom G, const float* __restrict__ pts, double gscale,
+                                                 unsigned long long* __restrict__ Gacc,
+                                                 unsigned long long* __restrict__ Uacc, int* __restrict__ status) {
+  __shared__ int32_t sid[8][BP_MAXK];
+  __shared__ double sm[8][BP_MAXK];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= G.n) return;
-  float x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
-    atomicOr(status, DEV_BAD_INDEX);
-    cell[p] = -1;
+  const float px = pts[3 * p], py = pts[3 * p + 1], pz = pts[3 * p + 2];
+  if (!(isfinite(px) && isfinite(py) && isfinite(pz))) {
+    if (lane == 0) atomicOr(status, DEV_BAD_INDEX);
     return;
   }
-  double fi = floor(((double)x - G.x0) / G.h), fj = floor(((double)y - G.y0) / G.h);
-  fi = fmin(fmax(fi, 0.0), (double)(G.nx - 1));
-  fj = fmin(fmax(fj, 0.0), (double)(G.rows - 1));
-  int c = (int)fj * G.nx + (int)fi;
-  cell[p] = c;
-  atomicAdd(&cnt[c], 1);
-}
-
-__global__ void k_bp_fill(int64_t n, const int32_t* __restrict__ cell, const int32_t* __restrict__ start,
-                          int32_t* __restrict__ fill, int32_t* __restrict__ order) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  int c = cell[p];
-  if (c < 0) return;
-  order[start[c] + atomicAdd(&fill[c], 1)] = (int32_t)p;
-}
-
-__global__ void k_bp_sort(const int32_t* __restrict__ start, int ncell, int32_t* __restrict__ ids) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  int a = start[c], b = start[c + 1];
-  for (int i = a + 1; i < b; ++i) {
-    int v = ids[i], k = i - 1;
-    while (k >= a && ids[k] > v) {
-      ids[k + 1] = ids[k];
-      --k;
-    }
-    ids[k + 1] = v;
-  }
-}
-
-// One warp per center l1: its row of lambda I + m~ m~^T (banded: centers within
-// two support radii) and u = m~ z, from the points of the cells within rca
-// nodes, in cell order and ascending point index within a cell.
-__global__ void __launch_bounds__(128) k_bp_gram(PatchGeom G, double lam, const float* __restrict__ pts,
-                                                 const int32_t* __restrict__ start, const int32_t* __restrict__ order,
-                                                 double* __restrict__ H, double* __restrict__ u) {
-  extern __shared__ double band_all[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int B = 4 * G.rca + 1;
-  double* band = band_all + (int64_t)wid * B * B;
-  int64_t l1 = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-  if (l1 >= G.M) return;
-  const int i1 = (int)(l1 % G.nx), j1 = (int)(l1 / G.nx);
-  const double cx1 = node_coord(G.x0, i1, G.h), cy1 = node_coord(G.y0, j1, G.h);
-  const float cx1f = (float)cx1, cy1f = (float)cy1;
-  for (int e = lane; e < B * B; e += 32) band[e] = 0.0;
-  __syncwarp();
-  const int W = 2 * G.rca;  // window width (nodes) around a point
-  double ue = 0.0;
-  for (int cj = j1 - G.rca; cj <= j1 + G.rca; ++cj) {
-    if (cj < 0 || cj >= G.rows) continue;
-    for (int ci = i1 - G.rca; ci <= i1 + G.rca; ++ci) {
-      if (ci < 0 || ci >= G.nx) continue;
-      int c = cj * G.nx + ci;
-      for (int k = start[c]; k < start[c + 1]; ++k) {
-        int64_t p = order[k];
-        float px = pts[3 * p], py = pts[3 * p + 1];
-        if (!(d2_rn(px, py, cx1f, cy1f) < G.r2a)) continue;
-        double dx = (double)px - cx1, dy = (double)py - cy1;
-        double m1 = row_value(G.kernel, dx * dx + dy * dy, G.inv_rho, G.g_scale, G.g_inv2s2);
-        ue = fma(m1, (double)pts[3 * p + 2], ue);
-        double pu = ((double)px - G.x0) / G.h - 0.5, pv = ((double)py - G.y0) / G.h - 0.5;
-        int ib = (int)floor(pu) - G.rca + 1, jb = (int)floor(pv) - G.rca + 1;
-        for (int t = lane; t < W * W; t += 32) {
-          int i2 = ib + t % W, j2 = jb + t / W;
-          if (i2 < 0 || i2 >= G.nx || j2 < 0 || j2 >= G.rows) continue;
-          int64_t id2 = (int64_t)j2 * G.nx + i2;
-          if (id2 >= G.M) continue;
-          double cx2 = node_coord(G.x0, i2, G.h), cy2 = node_coord(G.y0, j2, G.h);
-          if (!(d2_rn(px, py, (float)cx2, (float)cy2) < G.r2a)) continue;
-          int bi = i2 - i1 + 2 * G.rca, bj = j2 - j1 + 2 * G.rca;
-          if (bi < 0 || bi >= B || bj < 0 || bj >= B) continue;
-          double ex = (double)px - cx2, ey = (double)py - cy2;
-          double m2 = row_value(G.kernel, ex * ex + ey * ey, G.inv_rho, G.g_scale, G.g_inv2s2);
-          band[bj * B + bi] = fma(m1, m2, band[bj * B + bi]);
+  const int W = 2 * G.rca;
+  const double pu = ((double)px - G.x0) / G.h - 0.5, pv = ((double)py - G.y0) / G.h - 0.5;
+  const int ib = (int)floor(fmin(fmax(pu, -2.0 * W), (double)G.nx + 2.0 * W)) - G.rca + 1;
+  const int jb = (int)floor(fmin(fmax(pv, -2.0 * W), (double)G.rows + 2.0 * W)) - G.rca + 1;
+  int K = 0;
+  for (int t0 = 0; t0 < W * W; t0 += 32) {
+    int t = t0 + lane;
+    bool in = false;
+    int64_t id = 0;
+    double m = 0.0;
+    if (t < W * W) {
+      int i2 = ib + t % W, j2 = jb + t / W;
+      if (i2 >= 0 && i2 < G.nx && j2 >= 0 && j2 < G.rows) {
+        id = (int64_t)j2 * G.nx + i2;
+        if (id < G.M) {
+          double cx = node_coord(G.x0, i2, G.h), cy = node_coord(G.y0, j2, G.h);
+          if (d2_rn(px, py, (float)cx, (float)cy) < G.r2a) {
+            double ex = (double)px - cx, ey = (double)py - cy;
+            m = row_value(G.kernel, ex * ex + ey * ey, G.inv_rho, G.g_scale, G.g_inv2s2);
+            in = true;
+          }
         }
-        __syncwarp();
       }
     }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    int pos = K + __popc(mask & ((1u << lane) - 1u));
+    if (in && pos < BP_MAXK) {
+      sid[wid][pos] = (int32_t)id;
+      sm[wid][pos] = m;
+    }
+    K += __popc(mask);
   }
-  double* Hr = H + l1 * G.M;
-  for (int e = lane; e < B * B; e += 32) {
-    int bi = e % B, bj = e / B;
-    int i2 = i1 + bi - 2 * G.rca, j2 = j1 + bj - 2 * G.rca;
-    if (i2 < 0 || i2 >= G.nx || j2 < 0) continue;
-    int64_t id2 = (int64_t)j2 * G.nx + i2;
-    if (id2 >= G.M) continue;
-    Hr[id2] = band[e] + (id2 == l1 ? lam : 0.0);
+  if (K > BP_MAXK) {
+    if (lane == 0) atomicOr(status, DEV_BAD_INDEX);
+    return;
   }
-  if (lane == 0) u[l1] = ue;
+  __syncwarp();
+  for (int t = lane; t < K; t += 32) add_u128(Uacc + 2 * (int64_t)sid[wid][t], sm[wid][t] * (double)pz);
+  for (int t1 = 0; t1 < K; ++t1) {
+    const int64_t l1 = sid[wid][t1];
+    const double m1 = sm[wid][t1];
+    for (int t2 = lane; t2 <= t1; t2 += 32) {
+      int64_t l2 = sid[wid][t2];
+      int64_t hi = l1 > l2 ? l1 : l2, lo = l1 > l2 ? l2 : l1;
+      atomicAdd(Gacc + hi * G.M + lo, (unsigned long long)__double2ll_rn(m1 * sm[wid][t2] * gscale));
+    }
+  }
+}
+
+// H = lambda I + (accumulated m~ m~^T), both triangles; u = m~ z
+__global__ void k_bp_merge(int64_t M, double inv_gscale, double lam, const unsigned long long* __restrict__ Gacc,
+                           const unsigned long long* __restrict__ Uacc, double* __restrict__ H,
+                           double* __restrict__ u) {
+  const int64_t l1 = blockIdx.y;
+  for (int64_t l2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l2 <= l1; l2 += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long q = Gacc[l1 * M + l2];
+    if (q == 0ull && l2 != l1) continue;
+    double v = (double)(long long)q * inv_gscale;
+    if (l2 == l1) v += lam;
+    H[l1 * M + l2] = v;
+    if (l2 != l1) H[l2 * M + l1] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    u[l1] = (double)(long long)Uacc[2 * l1 + 1] + ldexp((double)Uacc[2 * l1], -64);
 }
 
 __global__ void k_bp_eval(PatchGeom G, const double* __restrict__ w, const float2* __restrict__ q,
@@ -239,24 +220,26 @@ static PatchGeom make_geom(const rbf_config& cfg, const rbf_patch& p) {
 
 static inline unsigned nb256(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// half-bandwidth of m~ m~^T for a patch (row-major node ids)
+static int64_t patch_bandwidth(const PatchGeom& G) {
+  int64_t bw = 2 * (int64_t)G.rca * ((int64_t)G.nx + 1);
+  return bw < G.M ? bw : BW_DENSE;
+}
+
 // Enqueue one patch on stream s with the workspace of sub-context sc.
 static rbf_status run_patch(Ctx* sc, const rbf_config& cfg, const rbf_patch& P, bool mixed, cudaStream_t s) {
   PatchGeom G = make_geom(cfg, P);
   const int64_t M = G.M, n = G.n;
-  const int ncell = G.nx * G.rows;
-  Buf& cell = sc->scratch(0);
-  Buf& cnt = sc->scratch(1);
-  Buf& start = sc->scratch(2);
-  Buf& order = sc->scratch(3);
+  Buf& Gacc = sc->scratch(0);
+  Buf& Uacc = sc->scratch(1);
   Buf& H = sc->scratch(4);
   Buf& L = sc->scratch(5);
   Buf& u = sc->scratch(6);
   Buf& Wf = sc->scratch(7);
   Buf& Zd = sc->scratch(8);
-  RBF_TRY(cell.ensure((size_t)(n + 1) * sizeof(int32_t)));
-  RBF_TRY(cnt.ensure((size_t)(ncell + 1) * sizeof(int32_t)));
-  RBF_TRY(start.ensure((size_t)(ncell + 1) * sizeof(int32_t)));
-  RBF_TRY(order.ensure((size_t)(n + 1) * sizeof(int32_t)));
+  if (M > 65535) return fail(RBF_EINVAL, "batch: a patch has more than 65535 centers");
+  RBF_TRY(Gacc.ensure((size_t)M * M * sizeof(unsigned long long)));
+  RBF_TRY(Uacc.ensure((size_t)2 * M * sizeof(unsigned long long)));
   RBF_TRY(H.ensure((size_t)M * M * sizeof(double)));
   RBF_TRY(u.ensure((size_t)M * sizeof(double)));
   const int64_t ldw = (M + 3) & ~(int64_t)3;
@@ -266,39 +249,36 @@ static rbf_status run_patch(Ctx* sc, const rbf_config& cfg, const rbf_patch& P, 
   } else {
     RBF_TRY(L.ensure((size_t)M * M * sizeof(double)));
   }
+  if (4 * G.rca * G.rca > 128) return fail(RBF_EINVAL, "batch: support radius too large for the lattice spacing");
   // the sync-free solves of this workspace start from cleared flags
   if (sc->sync_flags.p) RBF_CUDA(cudaMemsetAsync(sc->sync_flags.p, 0, sc->sync_flags.bytes, s));
-  RBF_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
-  if (n > 0) {
-    { k_bp_cells<<<nb256(n), 256, 0, s>>>(G, P.pts, cell.as<int32_t>(), cnt.as<int32_t>(), sc->dflag.as<int>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-  }
-  RBF_TRY(scan_i32(sc, cnt.as<int32_t>(), start.as<int32_t>(), ncell, s, 48));
-  RBF_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(ncell + 1) * sizeof(int32_t), s));
-  if (n > 0) {
-    { k_bp_fill<<<nb256(n), 256, 0, s>>>(n, cell.as<int32_t>(), start.as<int32_t>(), cnt.as<int32_t>(),
-                                         order.as<int32_t>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-    { k_bp_sort<<<nb256(ncell), 256, 0, s>>>(start.as<int32_t>(), ncell, order.as<int32_t>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-  }
+  // lambda I + m~ m~^T and m~ z by exact integer accumulation over the points
+  RBF_CUDA(cudaMemsetAsync(Gacc.p, 0, (size_t)M * M * sizeof(unsigned long long), s));
+  RBF_CUDA(cudaMemsetAsync(Uacc.p, 0, (size_t)2 * M * sizeof(unsigned long long), s));
   RBF_CUDA(cudaMemsetAsync(H.p, 0, (size_t)M * M * sizeof(double), s));
-  {
-    int B = 4 * G.rca + 1;
-    size_t smem = (size_t)4 * B * B * sizeof(double);
-    if (smem > 48 * 1024) return fail(RBF_EINVAL, "batch: support radius too large for the lattice spacing");
-    { k_bp_gram<<<(unsigned)((M + 3) / 4), 128, smem, s>>>(G, cfg.lambda, P.pts, start.as<int32_t>(), order.as<int32_t>(),
-                                                           H.as<double>(), u.as<double>()); ::rbf::note_launch(); }
+  const double gscale = ldexp(1.0, 62 - (int)ceil(log2((double)n + 1.0)));
+  if (n > 0) {
+    { k_bp_gram<<<nb256(n * 32), 256, 0, s>>>(G, P.pts, gscale, Gacc.as<unsigned long long>(),
+                                             Uacc.as<unsigned long long>(), sc->dflag.as<int>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
+  {
+    dim3 mg((unsigned)((M + 255) / 256 < 8 ? (M + 255) / 256 : 8), (unsigned)M);
+    { k_bp_merge<<<mg, 256, 0, s>>>(M, 1.0 / gscale, cfg.lambda, Gacc.as<unsigned long long>(),
+                                    Uacc.as<unsigned long long>(), H.as<double>(), u.as<double>()); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  }
+  // the update from the prior has the band structure of m~ m~^T: centers
+  // coupled through a point are at most 2 rca nodes apart in each direction
+  const int64_t bw = patch_bandwidth(G);
   if (mixed) {
-    RBF_TRY(potrf_mixed(sc, H.as<double>(), M, M, Wf.as<float>(), ldw, Zd.as<float>(), s));
+    RBF_TRY(potrf_mixed(sc, H.as<double>(), M, M, Wf.as<float>(), ldw, Zd.as<float>(), s, bw));
     RBF_TRY(mixed_solve(sc, H.as<double>(), M, nullptr, Wf.as<float>(), ldw, Zd.as<float>(), nullptr, M, u.as<double>(), 1,
-                        sc->refine_sweeps, s));
+                        sc->refine_sweeps, s, bw));
   } else {
     RBF_CUDA(cudaMemcpyAsync(L.p, H.p, (size_t)M * M * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    RBF_TRY(potrf_lower(sc, L.as<double>(), M, M, M, false, s));
-    RBF_TRY(chol_solve(sc, H.as<double>(), L.as<double>(), M, M, u.as<double>(), false, s));
+    RBF_TRY(potrf_lower(sc, L.as<double>(), M, M, M, false, s, bw));
+    RBF_TRY(chol_solve(sc, H.as<double>(), L.as<double>(), M, M, u.as<double>(), false, s, bw));
   }
   RBF_CUDA(cudaMemcpyAsync(P.w, u.p, (size_t)M * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (G.Q > 0) {
@@ -345,7 +325,7 @@ void batch_destroy(Ctx* c) {
 }
 
 // Time FP64 and mixed factorization + solve on a synthetic SPD matrix of size m.
-static rbf_status autotune(Ctx* sc, int64_t m, cudaStream_t s, int* pick) {
+static rbf_status autotune(Ctx* sc, int64_t m, int64_t bw, cudaStream_t s, int* pick) {
   Buf H, L, Wf, Zd, u;
   RBF_TRY(H.ensure((size_t)m * m * sizeof(double)));
   RBF_TRY(L.ensure((size_t)m * m * sizeof(double)));
@@ -369,12 +349,12 @@ static rbf_status autotune(Ctx* sc, int64_t m, cudaStream_t s, int* pick) {
       RBF_CUDA(cudaEventRecord(e0, s));
       if (path == 0) {
         RBF_CUDA(cudaMemcpyAsync(L.p, H.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        RBF_TRY(potrf_lower(sc, L.as<double>(), m, m, m, false, s));
-        RBF_TRY(chol_solve(sc, H.as<double>(), L.as<double>(), m, m, u.as<double>(), false, s));
+        RBF_TRY(potrf_lower(sc, L.as<double>(), m, m, m, false, s, bw));
+        RBF_TRY(chol_solve(sc, H.as<double>(), L.as<double>(), m, m, u.as<double>(), false, s, bw));
       } else {
-        RBF_TRY(potrf_mixed(sc, H.as<double>(), m, m, Wf.as<float>(), ldw, Zd.as<float>(), s));
+        RBF_TRY(potrf_mixed(sc, H.as<double>(), m, m, Wf.as<float>(), ldw, Zd.as<float>(), s, bw));
         RBF_TRY(mixed_solve(sc, H.as<double>(), m, nullptr, Wf.as<float>(), ldw, Zd.as<float>(), nullptr, m, u.as<double>(), 1,
-                            sc->refine_sweeps, s));
+                            sc->refine_sweeps, s, bw));
       }
       RBF_CUDA(cudaEventRecord(e1, s));
       RBF_CUDA(cudaEventSynchronize(e1));
@@ -452,7 +432,7 @@ extern "C" rbf_status rbf_batch_update_eval(rbf_ctx* cx, const rbf_patch* patche
     int b = bucket_of(patches[k].M);
     if (!B->choice[b]) {
       int pick = 1;
-      RBF_TRY(autotune(B->sub[0], patches[k].M, s, &pick));
+      RBF_TRY(autotune(B->sub[0], patches[k].M, patch_bandwidth(make_geom(c->cfg, patches[k])), s, &pick));
       B->choice[b] = pick;
     }
     mixed[k] = B->choice[b] == 2;

@@ -58,6 +58,8 @@ struct Grid {
   int nx, ny;       // number of cells
 };
 
+constexpr int64_t BW_DENSE_CTX = INT64_MAX / 4;  // "dense" half-bandwidth
+
 // Compressed-row copy of a float64 matrix: every exactly nonzero entry,
 // ascending columns (sparse.cu).
 constexpr int64_t SPH_MAX = 4096;  // largest order kept (capacity n^2 entries)
@@ -106,6 +108,7 @@ struct Ctx {
   bool zi_valid = false;
   int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
+  int64_t bw_lf = BW_DENSE_CTX;  // half-bandwidth of the float32 factor Lf
   bool la_ok = true;                 // look-ahead factorization allowed
   cudaStream_t la_stream = nullptr;  // side stream of the look-ahead factorization
   cudaEvent_t la_ev[5] = {};          // panel ready (2), trailing done (2), join
@@ -167,6 +170,19 @@ double eval_radius(const rbf_config& cfg);
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
+// x added exactly to a 128-bit fixed-point accumulator U[0..1] with 2^64
+// units per 1 (low word first; the carry of the low word goes to the high
+// word): order-independent sums of float64 terms of magnitude below 2^63.
+static __device__ __forceinline__ void add_u128(unsigned long long* U, double x) {
+  double hi = floor(x);
+  double fr = x - hi;  // exact, in [0, 1)
+  unsigned long long lo = __double2ull_rz(ldexp(fr, 64));  // fr * 2^64 < 2^64
+  unsigned long long old = atomicAdd(U, lo);
+  unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  long long h = (long long)hi + (long long)carry;
+  if (h != 0) atomicAdd(U + 1, (unsigned long long)h);
+}
+
 // Neighbour rule: dx, dy, d2 each rounded once to float32, no contraction.
 __device__ __forceinline__ float d2_rn(float qx, float qy, float cx, float cy) {
   float dx = __fsub_rn(qx, cx);
@@ -245,26 +261,31 @@ inline cudaError_t cooperative_launch(const void* f, dim3 g, dim3 b, void** args
 }
 
 // dense FP64 / mixed-precision linear algebra (dense.cu)
+// bw: half-bandwidth of the matrix (entries with |i - j| > bw are zero and
+// stay zero in the factor); the default treats it as dense
+constexpr int64_t BW_DENSE = BW_DENSE_CTX;
 rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfactor,
-                       bool mixed, cudaStream_t s);
+                       bool mixed, cudaStream_t s, int64_t bw = BW_DENSE);
 rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B, int64_t m,
-                      int64_t ldb, bool transpose, cudaStream_t s);
+                      int64_t ldb, bool transpose, cudaStream_t s, int64_t bw = BW_DENSE);
 rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                     double* Cm, int64_t ldc, cudaStream_t s);
 // mixed precision (mixed.cu)
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
-                       cudaStream_t s);
+                       cudaStream_t s, int64_t bw = BW_DENSE);
 rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Zd, float* B, int64_t m,
-                  int64_t ldb, bool transpose, cudaStream_t s);
+                  int64_t ldb, bool transpose, cudaStream_t s, int64_t bw = BW_DENSE);
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
                        const float* Zd, const float* Zi, int64_t n, double* B, int64_t m, int sweeps,
-                       cudaStream_t s);
+                       cudaStream_t s, int64_t bw = BW_DENSE);
 rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
                      const float* Zd, const float* Zi, int64_t n, double* B, int64_t k, const int32_t* pos,
-                     int sweeps, double* P, cudaStream_t s);
+                     int sweeps, double* P, cudaStream_t s, int64_t bw = BW_DENSE);
 // compressed rows of the information matrix (sparse.cu)
 rbf_status build_csr(Ctx* c, const double* H, int64_t ld, int64_t n, SpH& out, cudaStream_t s);
+rbf_status csr_bandwidth(Ctx* c, int64_t n, int64_t* bw, cudaStream_t s);
+rbf_status dense_bandwidth(Ctx* c, const double* H, int64_t ld, int64_t n, int64_t* bw, cudaStream_t s);
 rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t m, double* R, cudaStream_t s);
 // explicit inverse of the float32 factor and solves with it (inverse.cu)
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
@@ -275,7 +296,7 @@ rbf_status inv_solve_unit(Ctx* c, const float* Z, int64_t ldz, int64_t n, const 
 constexpr int SPD_SMALL_MAX = 128;  // largest order of spd_inverse_small (one CTA, shared memory)
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
-                      cudaStream_t s);
+                      cudaStream_t s, int64_t bw = BW_DENSE);
 void batch_destroy(Ctx* c);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,
                          const double* b, double* r, cudaStream_t s);

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_syrk_trailing(double* __restrict__ A, i
 }
 
 rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfactor, bool mixed,
-                       cudaStream_t s) {
+                       cudaStream_t s, int64_t bw) {
   (void)mixed;
   if (n <= 0 || nfactor <= 0) return RBF_OK;
   int* flag = c->dflag.as<int>();
@@ -163,12 +163,14 @@ rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfacto
   RBF_TRY(dt.ensure(NB * NB * sizeof(double)));
   for (int64_t k = 0; k < nfactor; k += NB) {
     int kb = (int)((nfactor - k) < NB ? (nfactor - k) : NB);
-    int64_t rows = n - k - kb;
+    // rows beyond the band are zero in this panel and untouched by its update
+    const int64_t ne = (k + kb + bw) < n ? (k + kb + bw) : n;
+    int64_t rows = ne - k - kb;
     int rows_per_cta = 16;
     int64_t ctas = rows > 0 ? (rows + rows_per_cta - 1) / rows_per_cta : 1;
     {
       StageTimer st(c, RBF_STAGE_PANEL, s, (double)kb * kb * kb / 3.0 + (double)rows * kb * kb);
-      { k_potrf_panel<<<(unsigned)ctas, 256, 0, s>>>(A, lda, n, k, kb, rows_per_cta, dt.as<double>(),
+      { k_potrf_panel<<<(unsigned)ctas, 256, 0, s>>>(A, lda, ne, k, kb, rows_per_cta, dt.as<double>(),
                                                    flag); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
       { k_copy_tile<<<1, 256, 0, s>>>(A, lda, k, kb, dt.as<double>()); ::rbf::note_launch(); }
@@ -178,7 +180,7 @@ rbf_status potrf_lower(Ctx* c, double* A, int64_t n, int64_t lda, int64_t nfacto
       StageTimer st(c, RBF_STAGE_TRAILING, s, (double)rows * (double)(rows + 1) * kb);
       int64_t T = (rows + ST - 1) / ST;
       int64_t tiles = T * (T + 1) / 2;
-      { k_syrk_trailing<<<(unsigned)tiles, 256, 0, s>>>(A, lda, n, k, kb); ::rbf::note_launch(); }
+      { k_syrk_trailing<<<(unsigned)tiles, 256, 0, s>>>(A, lda, ne, k, kb); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
   }
@@ -209,7 +211,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // copy of the solved block, and the final step is x = D^{-1} acc.
 __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __restrict__ L, int64_t ldl,
                                                               int64_t n, double* B, int64_t ldb,
-                                                              int c0, int mc, bool transpose,
+                                                              int c0, int mc, bool transpose, int64_t bwb,
                                                               int* flags, int epoch, int* status) {
   __shared__ double acc[NB][TS_MC + 1];
   __shared__ double Xs[NB][TS_MC + 1];
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __re
       }
       Dinv[lane][cidx] = b;
     }
-    for (int64_t lc = 0; lc < lk; ++lc) {
+    for (int64_t lc = (lk - bwb) > 0 ? (lk - bwb) : 0; lc < lk; ++lc) {  // blocks outside the band are zero
       int64_t cb = transpose ? (nblk - 1 - lc) : lc;
       int64_t cc0 = cb * NB;
       int cbs = (int)((n - cc0) < NB ? (n - cc0) : NB);
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __re
 }
 
 rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B, int64_t m,
-                      int64_t ldb, bool transpose, cudaStream_t s) {
+                      int64_t ldb, bool transpose, cudaStream_t s, int64_t bw) {
   if (n <= 0 || m <= 0) return RBF_OK;
   int64_t nblk = (n + NB - 1) / NB;
   if (c->sync_flags.bytes < (size_t)nblk * sizeof(int)) {
@@ -340,8 +342,9 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
     int mc = (int)((m - c0) < TS_MC ? (m - c0) : TS_MC);
     int epoch = (int)(++c->epoch);
     int c0i = (int)c0;
+    int64_t bwb = bw >= n ? nblk : bw / NB + 2;
     void* args[] = {(void*)&L, (void*)&ldl, (void*)&n, (void*)&B, (void*)&ldb, (void*)&c0i,
-                    (void*)&mc, (void*)&transpose, (void*)&flags, (void*)&epoch, (void*)&status};
+                    (void*)&mc, (void*)&transpose, (void*)&bwb, (void*)&flags, (void*)&epoch, (void*)&status};
     RBF_CUDA(cooperative_launch((const void*)k_trsm_syncfree, dim3((unsigned)grid),
                                          dim3(TS_THREADS), args, 0, s));
   }

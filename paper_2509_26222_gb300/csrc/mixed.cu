@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
 }
 
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
-                       cudaStream_t s) {
+                       cudaStream_t s, int64_t bw) {
   if (n <= 0) return RBF_OK;
   int* flag = c->dflag.as<int>();
   {
@@ -369,7 +369,8 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
   bool any_side = false;
   for (int64_t k = 0, step = 0; k < n; k += MB, ++step) {
     int kb = (int)((n - k) < MB ? (n - k) : MB);
-    int64_t rows = n - k - kb;
+    // rows beyond the band are zero in this panel and untouched by its update
+    int64_t rows = ((k + kb + bw) < n ? (k + kb + bw) : n) - k - kb;
     const int par = (int)(step & 1);
     __nv_bfloat16* Ph = pb.as<__nv_bfloat16>() + (size_t)par * 3 * slice;
     __nv_bfloat16* Pm = Ph + slice;
@@ -433,7 +434,8 @@ __device__ __forceinline__ void st_rel(int* p, int v) {
 
 __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int64_t ldl, int64_t n,
                                                 const float* __restrict__ Zd, float* B, int64_t ldb, int c0,
-                                                int mc, bool transpose, int* flags, int epoch, int* status) {
+                                                int mc, bool transpose, int bwb, int* flags, int epoch,
+                                                int* status) {
   // acc and Xs (64 x (T32_MC + 1) floats each) in dynamic shared memory
   extern __shared__ float t32_dyn[];
   float (*acc)[T32_MC + 1] = reinterpret_cast<float (*)[T32_MC + 1]>(t32_dyn);
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int
     }
     if (tid == 0) bail = 0;
     __syncthreads();
-    for (int64_t lc = 0; lc < lk; ++lc) {
+    for (int64_t lc = (lk - bwb) > 0 ? (lk - bwb) : 0; lc < lk; ++lc) {  // blocks outside the band are zero
       int64_t cb = transpose ? (nblk - 1 - lc) : lc;
       int64_t cc0 = cb * MB;
       int cbs = (int)((n - cc0) < MB ? (n - cc0) : MB);
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int
 }
 
 rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Zd, float* B, int64_t m,
-                  int64_t ldb, bool transpose, cudaStream_t s) {
+                  int64_t ldb, bool transpose, cudaStream_t s, int64_t bw) {
   if (n <= 0 || m <= 0) return RBF_OK;
   int64_t nblk = (n + MB - 1) / MB;
   if (c->sync_flags.bytes < (size_t)nblk * sizeof(int)) {
@@ -541,8 +543,9 @@ rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Z
     int mc = (int)((m - c0) < T32_MC ? (m - c0) : T32_MC);
     int epoch = (int)(++c->epoch);
     int c0i = (int)c0;
+    int bwb = (int)(bw >= n ? nblk : bw / MB + 2);
     void* args[] = {(void*)&L, (void*)&ldl, (void*)&n, (void*)&Zd, (void*)&B, (void*)&ldb, (void*)&c0i,
-                    (void*)&mc, (void*)&transpose, (void*)&flags, (void*)&epoch, (void*)&status};
+                    (void*)&mc, (void*)&transpose, (void*)&bwb, (void*)&flags, (void*)&epoch, (void*)&status};
     StageTimer st(c, RBF_STAGE_TRSM32, s, (double)n * (double)n * (double)mc);
     RBF_CUDA(cooperative_launch((const void*)k_trsm32, dim3((unsigned)grid), dim3(256), args, dyn, s));
   }
@@ -598,7 +601,7 @@ __global__ void __launch_bounds__(256) k_residual_multi(const double* __restrict
 
 rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
                        const float* Zd, const float* Zi, int64_t n, double* B, int64_t m, int sweeps,
-                       cudaStream_t s) {
+                       cudaStream_t s, int64_t bw) {
   if (Hs && !(Hs->valid && Hs->n == n)) Hs = nullptr;
   if (n <= 0 || m <= 0) return RBF_OK;
   int64_t tot = n * m;
@@ -623,8 +626,8 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, cons
     if (Zi) {
       RBF_TRY(inv_solve(c, Zi, ldw, n, F, m, s));
     } else {
-      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, false, s));
-      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, true, s));
+      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, false, s, bw));
+      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, true, s, bw));
     }
     { k_add_f32_to_f64<<<nb, 256, 0, s>>>(X, F, tot); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
@@ -672,11 +675,11 @@ __global__ void k_cov_second_order(const double* __restrict__ X, int64_t k, cons
 
 rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const float* W, int64_t ldw,
                      const float* Zd, const float* Zi, int64_t n, double* B, int64_t k, const int32_t* pos,
-                     int sweeps, double* P, cudaStream_t s) {
+                     int sweeps, double* P, cudaStream_t s, int64_t bw) {
   if (n <= 0 || k <= 0) return RBF_OK;
   if (Hs && !(Hs->valid && Hs->n == n)) Hs = nullptr;
   if (sweeps <= 1) {
-    RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, 1, s));
+    RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, 1, s, bw));
     { k_sym_gather<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(B, k, pos, P); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     return RBF_OK;
@@ -695,7 +698,7 @@ rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const 
     { k_f32_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(fb.as<float>(), B, tot); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   } else {
-    RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, sweeps - 1, s));
+    RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, sweeps - 1, s, bw));
   }
   double* R = rr.as<double>();
   if (Hs) {

@@ -18,19 +18,34 @@ namespace rbf {
 namespace {
 
 // nonzeros per row (one warp per row)
+// nonzeros per row (one warp per row) and the half-bandwidth max |i - j|
+// over the nonzero entries (atomicMax into *bw)
 __global__ void __launch_bounds__(256) k_csr_count(const double* __restrict__ H, int64_t n, int64_t ld,
-                                                   int32_t* __restrict__ cnt) {
+                                                   int32_t* __restrict__ cnt, int* __restrict__ bw) {
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
   const double* hr = H + row * ld;
   int c = 0;
+  int64_t far = 0;
   for (int64_t j0 = 0; j0 < n; j0 += 32) {
     int64_t j = j0 + lane;
     bool nz = j < n && hr[j] != 0.0;
     c += __popc(__ballot_sync(0xffffffffu, nz));
+    if (nz) {
+      int64_t dj = j > row ? j - row : row - j;
+      far = dj > far ? dj : far;
+    }
   }
-  if (lane == 0) cnt[row] = c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    int64_t v = __shfl_xor_sync(0xffffffffu, far, o);
+    far = v > far ? v : far;
+  }
+  if (lane == 0) {
+    cnt[row] = c;
+    atomicMax(bw, (int)far);
+  }
 }
 
 // column indices and values in ascending column order (one warp per row)
@@ -124,6 +139,7 @@ unsigned warps_grid(int64_t n) { return (unsigned)((n * 32 + 255) / 256); }
 
 }  // namespace
 
+// The half-bandwidth is left in scratch slot 70 at index n (read by csr_bandwidth).
 rbf_status build_csr(Ctx* c, const double* H, int64_t ld, int64_t n, SpH& out, cudaStream_t s) {
   out.valid = false;
   out.n = n;
@@ -132,8 +148,9 @@ rbf_status build_csr(Ctx* c, const double* H, int64_t ld, int64_t n, SpH& out, c
   RBF_TRY(out.col.ensure((size_t)n * n * sizeof(int32_t)));
   RBF_TRY(out.val.ensure((size_t)n * n * sizeof(double)));
   Buf& cnt = c->scratch(70);
-  RBF_TRY(cnt.ensure((size_t)n * sizeof(int32_t)));
-  { k_csr_count<<<warps_grid(n), 256, 0, s>>>(H, n, ld, cnt.as<int32_t>()); ::rbf::note_launch(); }
+  RBF_TRY(cnt.ensure((size_t)(n + 1) * sizeof(int32_t)));
+  RBF_CUDA(cudaMemsetAsync(cnt.as<int32_t>() + n, 0, sizeof(int32_t), s));
+  { k_csr_count<<<warps_grid(n), 256, 0, s>>>(H, n, ld, cnt.as<int32_t>(), cnt.as<int32_t>() + n); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(c, cnt.as<int32_t>(), out.rp.as<int32_t>(), n, s, 71));
   { k_csr_fill<<<warps_grid(n), 256, 0, s>>>(H, n, ld, out.rp.as<int32_t>(), out.col.as<int32_t>(),
@@ -141,6 +158,25 @@ rbf_status build_csr(Ctx* c, const double* H, int64_t ld, int64_t n, SpH& out, c
   RBF_CUDA(cudaGetLastError());
   out.valid = true;
   return RBF_OK;
+}
+
+// Half-bandwidth of the matrix of the last build_csr (one host read).
+rbf_status csr_bandwidth(Ctx* c, int64_t n, int64_t* bw, cudaStream_t s) {
+  int32_t* h32 = (int32_t*)c->host_small;
+  RBF_CUDA(cudaMemcpyAsync(h32 + 6, c->scratch(70).as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RBF_CUDA(cudaStreamSynchronize(s));
+  *bw = h32[6];
+  return RBF_OK;
+}
+
+// Half-bandwidth of a dense symmetric matrix (no compressed copy kept).
+rbf_status dense_bandwidth(Ctx* c, const double* H, int64_t ld, int64_t n, int64_t* bw, cudaStream_t s) {
+  Buf& cnt = c->scratch(70);
+  RBF_TRY(cnt.ensure((size_t)(n + 1) * sizeof(int32_t)));
+  RBF_CUDA(cudaMemsetAsync(cnt.as<int32_t>() + n, 0, sizeof(int32_t), s));
+  { k_csr_count<<<warps_grid(n), 256, 0, s>>>(H, n, ld, cnt.as<int32_t>(), cnt.as<int32_t>() + n); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return csr_bandwidth(c, n, bw, s);
 }
 
 rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t m, double* R, cudaStream_t s) {

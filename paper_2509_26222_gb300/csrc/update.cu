@@ -224,15 +224,6 @@ __global__ void __launch_bounds__(256) k_rowvals(RowParams R, const float* __res
 // Only the lower triangle (l2 <= l1) is accumulated; k_gram_merge adds it to
 // both triangles of H and clears the accumulator for the next frame.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void add_u128(unsigned long long* U, double x) {
-  double hi = floor(x);
-  double fr = x - hi;  // exact, in [0, 1)
-  unsigned long long lo = __double2ull_rz(ldexp(fr, 64));  // fr * 2^64 < 2^64
-  unsigned long long old = atomicAdd(U, lo);
-  unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-  long long h = (long long)hi + (long long)carry;
-  if (h != 0) atomicAdd(U + 1, (unsigned long long)h);
-}
 
 // One warp per point: pairs (t1, t2 <= t1) of its neighbour entries.
 __global__ void __launch_bounds__(256) k_gram_atomic(int64_t n, const int64_t* __restrict__ row_ptr,
@@ -497,10 +488,10 @@ static RowParams row_params(const rbf_config& cfg, double noise) {
 // the factor is only single-precision accurate, so the solution is refined
 // with float64 residuals r = b - H x until the correction stops shrinking.
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t bw) {
   if (!refine) {
-    RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, false, s));
-    RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, true, s));
+    RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, false, s, bw));
+    RBF_TRY(trsm_lower(c, L, a, ld, b, 1, 1, true, s, bw));
     return RBF_OK;
   }
   Buf& rb = c->scratch(31);
@@ -511,12 +502,12 @@ rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64
   RBF_TRY(bb.ensure((size_t)a * sizeof(double)));
   RBF_CUDA(cudaMemcpyAsync(bb.p, b, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
   RBF_CUDA(cudaMemcpyAsync(xb.p, b, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RBF_TRY(trsm_lower(c, L, a, ld, xb.as<double>(), 1, 1, false, s));
-  RBF_TRY(trsm_lower(c, L, a, ld, xb.as<double>(), 1, 1, true, s));
+  RBF_TRY(trsm_lower(c, L, a, ld, xb.as<double>(), 1, 1, false, s, bw));
+  RBF_TRY(trsm_lower(c, L, a, ld, xb.as<double>(), 1, 1, true, s, bw));
   for (int it = 0; it < 6; ++it) {
     RBF_TRY(symv_residual(H, a, ld, xb.as<double>(), bb.as<double>(), rb.as<double>(), s));
-    RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, false, s));
-    RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, true, s));
+    RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, false, s, bw));
+    RBF_TRY(trsm_lower(c, L, a, ld, rb.as<double>(), 1, 1, true, s, bw));
     { k_axpy<<<nblk(a), 256, 0, s>>>(xb.as<double>(), rb.as<double>(), a); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
@@ -696,10 +687,10 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       // X = H_prev^{-1} E_D by refined solves with the float32 factor; P_DD = X[D, :]
       RBF_TRY(mixed_cov(c, c->H.as<double>(), c->ldH, &c->Hs, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
                         c->zi_valid ? c->Zi.as<float>() : nullptr, ap, Y.as<double>(), d, Dl.as<int32_t>(),
-                        c->refine_sweeps_cov, Pdd.as<double>(), s));
+                        c->refine_sweeps_cov, Pdd.as<double>(), s, c->bw_lf));
     } else {
       // Y = L_prev^{-1} E_D, P_DD = Y^T Y
-      RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s));
+      RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s, c->bw_lf));
       RBF_TRY(gemm_f64(c, true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
                        Pdd.as<double>(), d, s));
     }
@@ -846,24 +837,34 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     c->gacc_dirty = false;
     if (mixed) RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, s));
   }
+  // Until a center has left some block there is no Schur-complement fill and
+  // H' has the band structure of m~ m~^T: read its half-bandwidth then, and
+  // skip the zero blocks outside the band in the factorization and solves.
+  int64_t bw = BW_DENSE;
+  if (!c->pg_on && d == 0) {
+    if (mixed && c->Hs_next.valid) RBF_TRY(csr_bandwidth(c, an, &bw, s));
+    else RBF_TRY(dense_bandwidth(c, Hn.as<double>(), ld, an, &bw, s));
+    if (3 * bw >= an) bw = BW_DENSE;
+  }
 
   // 8. factor H' and solve for the weight increment
   Buf& Wn = c->scratch(27);
   Buf& Zdn = c->scratch(63);
   Buf& Zin = c->scratch(64);
   const int64_t ldw = (an + 3) & ~(int64_t)3;
-  const bool use_inv = mixed && an <= c->inv_max;
+  // the inverse of a banded factor is dense: banded blocks keep the substitution
+  const bool use_inv = mixed && an <= c->inv_max && bw == BW_DENSE;
   if (mixed) {
     RBF_TRY(Wn.ensure((size_t)an * ldw * sizeof(float)));
     RBF_TRY(Zdn.ensure((size_t)((an + 63) / 64) * 64 * 64 * sizeof(float)));
-    RBF_TRY(potrf_mixed(c, Hn.as<double>(), ld, an, Wn.as<float>(), ldw, Zdn.as<float>(), s));
+    RBF_TRY(potrf_mixed(c, Hn.as<double>(), ld, an, Wn.as<float>(), ldw, Zdn.as<float>(), s, bw));
     if (use_inv) {
       RBF_TRY(Zin.ensure((size_t)2 * an * ldw * sizeof(float)));  // L^{-1} and its transpose
       RBF_TRY(trtri_mixed(c, Wn.as<float>(), ldw, an, Zdn.as<float>(), Zin.as<float>(), ldw, s));
     }
   } else {
     RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s));
+    RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s, bw));
   }
   int flag = 0;
   {
@@ -871,9 +872,9 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
                                             (double)an * an);
     if (mixed)
       RBF_TRY(mixed_solve(c, Hn.as<double>(), ld, &c->Hs_next, Wn.as<float>(), ldw, Zdn.as<float>(),
-                          use_inv ? Zin.as<float>() : nullptr, an, u.as<double>(), 1, c->refine_sweeps, s));
+                          use_inv ? Zin.as<float>() : nullptr, an, u.as<double>(), 1, c->refine_sweeps, s, bw));
     else
-      RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), false, s));
+      RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), false, s, bw));
   }
   // one read of the device flags covers the factorization and the solves
   RBF_TRY(read_dev_flag(c, s, &flag));
@@ -906,9 +907,11 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     std::swap(c->Hs, c->Hs_next);
     if (use_inv) std::swap(c->Zi, Zin);
     c->zi_valid = use_inv;
+    c->bw_lf = bw;
     c->ldw = ldw;
   } else {
     std::swap(c->L, Ln);
+    c->bw_lf = bw;
   }
   std::swap(c->A, An);
   std::swap(c->g2l, g2ln);
@@ -1026,9 +1029,9 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
     if (c->cfg.update_precision == RBF_UPDATE_MIXED) {
       RBF_TRY(mixed_cov(c, c->H.as<double>(), c->ldH, &c->Hs, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
                         c->zi_valid ? c->Zi.as<float>() : nullptr, c->a, Y.as<double>(), ka, lb.as<int32_t>(),
-                        c->refine_sweeps_cov, Paa.as<double>(), s));
+                        c->refine_sweeps_cov, Paa.as<double>(), s, c->bw_lf));
     } else {
-      RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s));
+      RBF_TRY(trsm_lower(c, c->L.as<double>(), c->a, c->ldH, Y.as<double>(), ka, ka, false, s, c->bw_lf));
       RBF_TRY(gemm_f64(c, true, false, ka, ka, c->a, 1.0, Y.as<double>(), ka, Y.as<double>(), ka, 0.0,
                        Paa.as<double>(), ka, s));
     }
