@@ -184,6 +184,30 @@ def compare_precision(args, N, other, centers, dev_frames, flush, stream, T, nfr
     return other_line
 
 
+def exact_mode_frames(args, N, prec, centers, dev_frames, flush, stream, nfr):
+    """The same frames with the exact full-covariance recursion (all 4096 rows
+    updated every frame), update only."""
+    import torch
+    Te = N.Terrain(rho=0.6, lam=1e-3, update_precision=prec, exact=True)
+    Te.set_centers(centers)
+    times = []
+    for k in range(nfr):
+        if k >= args.warmup:
+            flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Te.update(dev_frames[k][0], noise=NOISE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    Te.close()
+    return {"mode": "exact recursion, all 4096 centers per update", "updates_per_s": len(times) / (sum(times) * 1e-3),
+            "ms_per_update": sum(times) / len(times)}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2509_26222_gb300 import native as N, workloads as W
@@ -194,7 +218,7 @@ def run_ours(args, ws, rank, local):
     prec = N.UPDATE_MIXED if args.precision == "mixed" else N.UPDATE_FP64
     centers = torch.tensor(W.config2_centers(), device=dev)
     nfr = args.warmup + args.steps
-    frames = [frame_arrays(k % W.C2_FRAMES) for k in range(2 * nfr)]
+    frames = [frame_arrays(k % W.C2_FRAMES) for k in range(nfr)]
     eye = np.eye(3)
 
     def make_terrain():
@@ -261,13 +285,16 @@ def run_ours(args, ws, rank, local):
 
     # ----- the other update precision on the same frames (mixed vs FP64 comparison) -----
     other_line = None
+    exact_line = None
     other = N.UPDATE_FP64 if prec == N.UPDATE_MIXED else N.UPDATE_MIXED
     for _ in range(0 if args.no_other else 1):
         other_line = compare_precision(args, N, other, centers, dev_frames, flush, stream, T, nfr, eye)
+        exact_line = exact_mode_frames(args, N, prec, centers, dev_frames, flush, stream, nfr)
 
     # ----- end to end through host buffers -----
     T2 = make_terrain()
-    host = [(torch.tensor(g).pin_memory(), torch.tensor(b).pin_memory(), s) for g, b, s in frames[nfr:]]
+    # the same frames as the device-resident run, now from pinned host memory
+    host = [(torch.tensor(g).pin_memory(), torch.tensor(b).pin_memory(), s) for g, b, s in frames]
     h_host = torch.empty(8000, pin_memory=True)
     grad_host = torch.empty(8000, 2, pin_memory=True)
     o_host = torch.empty(7, dtype=torch.float64, pin_memory=True)
@@ -414,7 +441,7 @@ def run_ours(args, ws, rank, local):
         c5["speedup_mixed_over_fp64"] = c5["fp64"]["ms_per_update"] / c5["mixed"]["ms_per_update"]
     return dict(times=times, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, prof=prof,
                 launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch,
-                other=other_line, c5=c5)
+                other=other_line, exact=exact_line, c5=c5)
 
 
 # ---------------------------------------------------------------------------
@@ -575,6 +602,7 @@ def main():
                               "bytes_per_query": 20, "peak_kind": pk_kind}},
         "stage_ms_per_step": stage_ms,
         "other_precision_same_frames": r["other"],
+        "exact_mode_same_frames": r["exact"],
         "update_65536_centers": c5,
         "batch": r["batch"],
         "clocks": r["clocks"],

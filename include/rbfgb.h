@@ -79,6 +79,13 @@ typedef struct rbf_config {
   int32_t inverse_max;      /* RBF_UPDATE_MIXED: largest active block for which the update forms
                                L^{-1} of the float32 factor and solves by two products with it
                                (0 = default 3072; negative = never: blocked substitution only) */
+  int32_t exact;            /* 0: the paper's block recursion (Sec. III-C: only the rows touched by
+                                  the frame are updated, P[A, not A] = 0 afterwards);
+                               1: the exact recursion with the full covariance (Eq. kf_w_update and
+                                  Eq. H_inverse_update on all M rows): every center is in the active
+                                  block of every update, so after any sequence of updates the
+                                  weights equal the batch ridge estimate of Sec. III-B */
+  int32_t reserved1;        /* must be 0 */
 } rbf_config;
 
 /* Create a context on the current CUDA device.  Validates cfg (positive radii,

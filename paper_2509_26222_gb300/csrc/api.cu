@@ -551,6 +551,8 @@ extern "C" rbf_status rbf_create(const rbf_config* cfg, rbf_ctx** out) {
     return fail(RBF_EINVAL, "huber_delta must be > 0");
   if (cfg->refine_sweeps < 0 || cfg->refine_sweeps > 16)
     return fail(RBF_EINVAL, "refine_sweeps must be in [0, 16]");
+  if (cfg->exact != 0 && cfg->exact != 1) return fail(RBF_EINVAL, "exact must be 0 or 1");
+  if (cfg->reserved1 != 0) return fail(RBF_EINVAL, "reserved1 must be 0");
   rbf_ctx* c = new (std::nothrow) rbf_ctx();
   if (!c) return fail(RBF_ENOMEM, "host allocation failed");
   Ctx* x = C(c);

@@ -140,6 +140,11 @@ __global__ void k_mark(const int32_t* __restrict__ col, int64_t nnz, int32_t* __
 }
 
 // A[pos[j]] = j for marked j; g2l[j] = pos[j] or -1
+__global__ void k_fill_i32(int32_t* __restrict__ a, int64_t n, int32_t v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
 __global__ void k_compact(const int32_t* __restrict__ mark, const int32_t* __restrict__ pos, int64_t M,
                           int32_t* __restrict__ A, int32_t* __restrict__ g2l) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -561,8 +566,13 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_TRY(pos.ensure((size_t)(M + 1) * sizeof(int32_t)));
   RBF_TRY(An.ensure((size_t)M * sizeof(int32_t)));
   RBF_TRY(g2ln.ensure((size_t)M * sizeof(int32_t)));
-  RBF_CUDA(cudaMemsetAsync(mark.p, 0, (size_t)M * sizeof(int32_t), s));
-  { k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>()); ::rbf::note_launch(); }
+  if (c->cfg.exact) {
+    // exact recursion: every center is in the block of every update
+    { k_fill_i32<<<nblk(M), 256, 0, s>>>(mark.as<int32_t>(), M, 1); ::rbf::note_launch(); }
+  } else {
+    RBF_CUDA(cudaMemsetAsync(mark.p, 0, (size_t)M * sizeof(int32_t), s));
+    { k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>()); ::rbf::note_launch(); }
+  }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(c, mark.as<int32_t>(), pos.as<int32_t>(), M, s, 48));
   { k_compact<<<nblk(M), 256, 0, s>>>(mark.as<int32_t>(), pos.as<int32_t>(), M, An.as<int32_t>(),

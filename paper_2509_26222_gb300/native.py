@@ -52,6 +52,8 @@ class RbfConfig(ctypes.Structure):
         ("r_kd", ctypes.c_double),
         ("refine_sweeps", ctypes.c_int32),
         ("inverse_max", ctypes.c_int32),
+        ("exact", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -165,7 +167,8 @@ class Terrain:
 
     def __init__(self, kernel=KERNEL_WENDLAND, rho=0.6, sigma=0.04, cutoff_mult=4.0, lam=1e-3,
                  update_precision=UPDATE_FP64, loss=LOSS_HUBER, huber_delta=0.05, lambda_m=1.0,
-                 wheel_offset=0.0, mesh=None, r_kd=0.1, min_count=1, refine_sweeps=0, inverse_max=0):
+                 wheel_offset=0.0, mesh=None, r_kd=0.1, min_count=1, refine_sweeps=0, inverse_max=0,
+                 exact=False):
         self.lib = load()
         cfg = RbfConfig()
         cfg.kernel = kernel
@@ -184,6 +187,7 @@ class Terrain:
         cfg.r_kd = r_kd
         cfg.refine_sweeps = refine_sweeps
         cfg.inverse_max = inverse_max
+        cfg.exact = 1 if exact else 0
         self.cfg = cfg
         self.device = torch.cuda.current_device()
         h_ = ctypes.c_void_p()

@@ -232,6 +232,51 @@ def test_update_config5_full_size(N, prec):
     assert rel_inf(T.cov(ids).cpu().numpy(), P_ref) < F64_TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_mode_equals_exact_recursion_config1(N, prec):
+    """Exact mode (every center updated every time, Eq. kf_w_update /
+    H_inverse_update on the full matrices): ten batches of the config-1
+    points against the oracle's full-covariance recursion, and the end
+    result against batch ridge over all points."""
+    c1 = W.config1()
+    p32 = c1.points.astype(np.float32)
+    T = N.Terrain(rho=0.6, update_precision=prec, exact=True)
+    T.set_centers(dev(c1.centers, torch.float64))
+    st = O.ExactState(c1.centers, 1e-3, O.WENDLAND, rho=0.6)
+    ids = np.arange(0, 256, 5)
+    for b in range(10):
+        chunk = p32[b * 200:(b + 1) * 200]
+        T.update(dev(chunk), noise=0.02)
+        O.exact_update(st, chunk.astype(np.float64))
+        assert T.active().numel() == 256
+        assert rel_inf(T.weights().cpu().numpy(), st.w) < F64_TOL
+    assert rel_inf(T.cov(ids).cpu().numpy(), st.P[np.ix_(ids, ids)]) < F64_TOL
+    ref = O.batch_ridge(p32.astype(np.float64), c1.centers, 1e-3, O.WENDLAND, rho=0.6)
+    assert rel_inf(T.weights().cpu().numpy(), ref) < F64_TOL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_mode_config2_frames_equal_batch_ridge(N, prec):
+    """Exact mode over three staircase frames on the 64x64 grid (M = 4096):
+    weights and a covariance block equal the ridge estimate over all the
+    points of the three frames (sparse-design oracle)."""
+    c = W.config2_centers()
+    T = N.Terrain(rho=0.6, update_precision=prec, exact=True)
+    T.set_centers(dev(c, torch.float64))
+    allp = []
+    for k in (0, 30, 60):
+        pts, _, _ = W.config2_frame(k)
+        p32 = pts.astype(np.float32)
+        T.update(dev(p32), noise=0.03)
+        allp.append(p32)
+    p64 = np.concatenate(allp).astype(np.float64)
+    rng = np.random.default_rng(3)
+    ids = np.sort(rng.choice(4096, 40, replace=False))
+    w_ref, P_ref = O.ridge_sparse(p64, c, 1e-3, O.WENDLAND, rho=0.6, cov_ids=ids)
+    assert rel_inf(T.weights().cpu().numpy(), w_ref) < F64_TOL
+    assert rel_inf(T.cov(ids).cpu().numpy(), P_ref) < F64_TOL
+
+
 def test_update_gaussian_moment_rows(N):
     rng = np.random.default_rng(9)
     c = W.grid_centers(12, 12, 0.0, 0.0, 0.07)
