@@ -149,6 +149,21 @@ rbf_status rbf_eval(rbf_ctx* ctx, const float* q, int64_t Q, float* h, float* gr
 rbf_status rbf_soft_cost(rbf_ctx* ctx, const double* R, const double* t, const float* pts,
                          int64_t n, double* cost, double* grad6, float* resid, void* stream);
 
+/* The soft-constraint cost, its gradient and the Gauss-Newton matrix of the
+ * pose, for a Levenberg-Marquardt step on the 6-DoF pose (Sec. IV-C: the
+ * cost J_M is minimised by LM; here over all points of the frame).
+ * out28 (device, 28 doubles): out28[0] = cost, out28[1..6] = gradient g (as
+ * rbf_soft_cost), out28[7..27] = A = sum_i omega_i J_i J_i^T, the upper
+ * triangle row by row (A00 A01 .. A05 A11 .. A55), with J_i the pose
+ * Jacobian row of point i (same perturbation as the gradient) and the
+ * iteratively reweighted least-squares weight omega_i = psi(r_i) / r_i
+ * (1 inside the Huber zone, delta / |r_i| outside; 2 lambda_M for the L2
+ * loss).  An LM step solves (A + mu diag(A)) delta = -g on the host.
+ * Asynchronous on stream.  Errors: RBF_EINVAL (negative n, null output,
+ * null points with n > 0, non-finite pose), RBF_ESTATE (no centers). */
+rbf_status rbf_soft_cost_normal(rbf_ctx* ctx, const double* R, const double* t, const float* pts,
+                                int64_t n, double* out28, void* stream);
+
 /* rbf_soft_cost that allocates nothing, for callers that cannot allocate
  * device memory while they run: a scan-matching loop with a hard per-frame
  * deadline (cudaMalloc / cudaFree can synchronize the device and take

@@ -63,7 +63,7 @@ __all__ = [
     "support_radius_assembly", "fl32", "member_f32", "neighbors", "eval_h",
     "select_centers", "design_rows", "batch_ridge", "ridge_sparse", "CovStore", "BlockState",
     "block_update", "ExactState", "exact_update", "skew", "huber", "huber_psi",
-    "soft_cost", "soft_cost_backward",
+    "soft_cost", "soft_cost_backward", "soft_cost_normal", "so3_exp", "lm_step",
 ]
 
 
@@ -504,6 +504,43 @@ def soft_cost(R, t, body_xyz, c_xy, w, kind, rho=0.6, sigma=0.04, cutoff_mult=4.
         psi = huber_psi(r, delta)
     grad6 = psi @ J
     return dict(cost=cost, grad6=grad6, r=r, J=J, psi=psi, q=q)
+
+
+def soft_cost_normal(R, t, body_xyz, c_xy, w, kind, rho=0.6, sigma=0.04, cutoff_mult=4.0,
+                     delta=0.05, wheel_offset=0.0, loss="huber", lam_m=1.0):
+    """Gauss-Newton matrix of the pose for a Levenberg-Marquardt step on the
+    soft-constraint cost (Sec. IV-C minimises J_M by LM):
+    A = sum_i omega_i J_i^T J_i with the iteratively reweighted least-squares
+    weight omega_i = psi(r_i) / r_i (1 inside the Huber zone, delta / |r_i|
+    outside; 2 lam_m for the L2 loss).  Returns dict(cost, grad6, A)."""
+    d = soft_cost(R, t, body_xyz, c_xy, w, kind, rho, sigma, cutoff_mult, delta, wheel_offset, loss, lam_m)
+    r, J = d["r"], d["J"]
+    if loss == "l2":
+        om = np.full(r.shape, 2.0 * lam_m)
+    else:
+        a = np.abs(r)
+        om = np.where(a <= delta, 1.0, delta / np.maximum(a, 1e-300))
+    A = (J * om[:, None]).T @ J
+    return dict(cost=d["cost"], grad6=d["grad6"], A=A)
+
+
+def so3_exp(v):
+    """exp([v]_x) by Rodrigues' formula (the right perturbation R <- R Exp(dtheta))."""
+    v = np.asarray(v, dtype=np.float64)
+    a = float(np.linalg.norm(v))
+    K = skew(v)
+    if a < 1e-12:
+        return np.eye(3) + K
+    return np.eye(3) + math.sin(a) / a * K + (1.0 - math.cos(a)) / (a * a) * (K @ K)
+
+
+def lm_step(R, t, body_xyz, c_xy, w, kind, mu=1e-3, **kw):
+    """One Levenberg-Marquardt step on the pose: (A + mu diag(A)) d = -g,
+    R <- R Exp(d_theta), t <- t + d_t."""
+    d = soft_cost_normal(R, t, body_xyz, c_xy, w, kind, **kw)
+    A = d["A"]
+    step = np.linalg.solve(A + mu * np.diag(np.diag(A)), -d["grad6"])
+    return np.asarray(R) @ so3_exp(step[:3]), np.asarray(t) + step[3:], d["cost"]
 
 
 def soft_cost_backward(R, t, body_xyz, c_xy, w, kind, rho=0.6, sigma=0.04,

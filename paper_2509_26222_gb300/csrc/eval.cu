@@ -447,13 +447,21 @@ __device__ __forceinline__ void point_terms(const EvalParams& P, const int32_t* 
 
 constexpr int SC_THREADS = 256;
 
-template <int KERNEL>
+// NV = 7: cost and gradient.  NV = 28: also the Gauss-Newton matrix
+// A = sum_i omega_i J_i J_i^T (upper triangle, row-major, 21 entries) with
+// the iteratively reweighted least-squares weight omega_i = psi(r_i) / r_i
+// (1 inside the Huber zone, delta / |r_i| outside; 2 lambda_M for the L2 loss).
+constexpr int SC_NORMAL = 28;
+
+template <int KERNEL, int NV>
 __global__ void __launch_bounds__(SC_THREADS) k_soft_cost(EvalParams P, const int32_t* __restrict__ cell_start,
                                                           const float4* __restrict__ xyw, Pose T,
                                                           CostParams CP, const float* __restrict__ pts,
                                                           int64_t n, float* __restrict__ resid,
                                                           double* __restrict__ partials) {
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float qx, qy, r, loss, psi, J[6];
@@ -462,37 +470,58 @@ __global__ void __launch_bounds__(SC_THREADS) k_soft_cost(EvalParams P, const in
     acc[0] += (double)loss;
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k + 1] += (double)(psi * J[k]);
+    if (NV == SC_NORMAL) {
+      float om;
+      if (CP.loss == RBF_LOSS_HUBER) {
+        float a = fabsf(r);
+        om = a <= CP.delta ? 1.f : CP.delta / a;
+      } else {
+        om = 2.f * CP.lam_m;
+      }
+      int q = 7;
+#pragma unroll
+      for (int u = 0; u < 6; ++u)
+#pragma unroll
+        for (int v = u; v < 6; ++v) acc[q++] += (double)(om * J[u] * J[v]);
+    }
   }
-  __shared__ double red[SC_THREADS / 32][7];
+  __shared__ double red[SC_THREADS / 32][NV];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < NV; ++k) {
     double v = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) red[wid][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < NV) {
     double v = 0;
     for (int w = 0; w < SC_THREADS / 32; ++w) v += red[w][threadIdx.x];
-    partials[blockIdx.x * 8 + threadIdx.x] = v;
+    partials[blockIdx.x * (NV == 7 ? 8 : 32) + threadIdx.x] = v;
   }
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ partials, int nblk,
+// out[0] = cost, out[1..6] = gradient, out[7..27] = A (when nv = 28); the
+// first seven scaled by *gout when given.
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblk, int nv,
                                   const double* __restrict__ gout, double* __restrict__ cost,
-                                  double* __restrict__ grad6) {
+                                  double* __restrict__ grad6, double* __restrict__ normal21) {
   int k = threadIdx.x;
-  if (k >= 7) return;
+  if (k >= nv) return;
+  const int stride = nv == 7 ? 8 : 32;
   double v = 0;
-  for (int b = 0; b < nblk; ++b) v += partials[b * 8 + k];
-  double g = gout ? *gout : 1.0;
-  v *= g;
+  for (int b = 0; b < nblk; ++b) v += partials[b * stride + k];
+  if (k < 7) {
+    double g = gout ? *gout : 1.0;
+    v *= g;
+  }
   if (k == 0) {
     if (cost) *cost = v;
-  } else if (grad6) {
-    grad6[k - 1] = v;
+  } else if (k < 7) {
+    if (grad6) grad6[k - 1] = v;
+  } else if (normal21) {
+    normal21[k - 7] = v;
   }
 }
 
@@ -520,22 +549,25 @@ static CostParams cost_params(const rbf_config& cfg) {
 
 static rbf_status soft_cost_forward(Ctx* x, const Pose& T, const float* pts, int64_t n,
                                     const double* gout, double* cost, double* grad6, float* resid,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, double* normal21 = nullptr) {
   EvalParams P = make_eval_params(x);
   CostParams CP = cost_params(x->cfg);
   unsigned nb = grid_for(n, SC_THREADS, x->device, 4);
   Buf& part = x->scratch(20);
-  RBF_TRY(part.ensure((size_t)nb * 8 * sizeof(double)));
-  if (x->cfg.kernel == RBF_KERNEL_WENDLAND)
-    { k_soft_cost<RBF_KERNEL_WENDLAND><<<nb, SC_THREADS, 0, s>>>(
-        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid,
-        part.as<double>()); ::rbf::note_launch(); }
-  else
-    { k_soft_cost<RBF_KERNEL_GAUSSIAN><<<nb, SC_THREADS, 0, s>>>(
-        P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid,
-        part.as<double>()); ::rbf::note_launch(); }
+  RBF_TRY(part.ensure((size_t)nb * 32 * sizeof(double)));
+  const int nv = normal21 ? SC_NORMAL : 7;
+  const int32_t* cs = x->cell_start.as<int32_t>();
+  const float4* xyw = x->sorted_xyw.as<float4>();
+  double* pp = part.as<double>();
+  if (x->cfg.kernel == RBF_KERNEL_WENDLAND) {
+    if (normal21) { k_soft_cost<RBF_KERNEL_WENDLAND, SC_NORMAL><<<nb, SC_THREADS, 0, s>>>(P, cs, xyw, T, CP, pts, n, resid, pp); ::rbf::note_launch(); }
+    else { k_soft_cost<RBF_KERNEL_WENDLAND, 7><<<nb, SC_THREADS, 0, s>>>(P, cs, xyw, T, CP, pts, n, resid, pp); ::rbf::note_launch(); }
+  } else {
+    if (normal21) { k_soft_cost<RBF_KERNEL_GAUSSIAN, SC_NORMAL><<<nb, SC_THREADS, 0, s>>>(P, cs, xyw, T, CP, pts, n, resid, pp); ::rbf::note_launch(); }
+    else { k_soft_cost<RBF_KERNEL_GAUSSIAN, 7><<<nb, SC_THREADS, 0, s>>>(P, cs, xyw, T, CP, pts, n, resid, pp); ::rbf::note_launch(); }
+  }
   RBF_CUDA(cudaGetLastError());
-  { k_reduce_partials<<<1, 32, 0, s>>>(part.as<double>(), (int)nb, gout, cost, grad6); ::rbf::note_launch(); }
+  { k_reduce_partials<<<1, 32, 0, s>>>(pp, (int)nb, nv, gout, cost, grad6, normal21); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
@@ -755,6 +787,24 @@ extern "C" rbf_status rbf_soft_cost(rbf_ctx* c, const double* R, const double* t
   return soft_cost_forward(x, T, pts, n, nullptr, cost, grad6, resid, s);
 }
 
+extern "C" rbf_status rbf_soft_cost_normal(rbf_ctx* c, const double* R, const double* t, const float* pts,
+                                           int64_t n, double* out28, void* stream) {
+  RBF_TRY(check_ctx(c, true));
+  if (n < 0) return fail(RBF_EINVAL, "negative n");
+  if (!out28) return fail(RBF_EINVAL, "null output");
+  if (n > 0 && !pts) return fail(RBF_EINVAL, "null points");
+  Pose T;
+  RBF_TRY(load_pose(R, t, &T));
+  Ctx* x = C(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    RBF_CUDA(cudaMemsetAsync(out28, 0, 28 * sizeof(double), s));
+    return RBF_OK;
+  }
+  StageTimer st(x, RBF_STAGE_SOFTCOST, s, 12.0 * (double)n);
+  return soft_cost_forward(x, T, pts, n, nullptr, out28, out28 + 1, nullptr, s, out28 + 7);
+}
+
 extern "C" rbf_status rbf_soft_cost_backward(rbf_ctx* c, const double* R, const double* t,
                                              const float* pts, int64_t n, const double* gout,
                                              float* dw, float* dc, double* dpose6, void* stream) {
@@ -885,16 +935,16 @@ extern "C" rbf_status rbf_soft_cost_noalloc(rbf_ctx* c, const double* R, const d
   // every block writes all 8 of its partial-sum slots, and the reduction reads
   // only the nb blocks of this launch: nothing left by an earlier call is used
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND) {
-    k_soft_cost<RBF_KERNEL_WENDLAND><<<nb, SC_THREADS, 0, s>>>(
+    k_soft_cost<RBF_KERNEL_WENDLAND, 7><<<nb, SC_THREADS, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid, part);
     ::rbf::note_launch();
   } else {
-    k_soft_cost<RBF_KERNEL_GAUSSIAN><<<nb, SC_THREADS, 0, s>>>(
+    k_soft_cost<RBF_KERNEL_GAUSSIAN, 7><<<nb, SC_THREADS, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid, part);
     ::rbf::note_launch();
   }
   RBF_CUDA(cudaGetLastError());
-  k_reduce_partials<<<1, 32, 0, s>>>(part, (int)nb, nullptr, cost, grad6);
+  k_reduce_partials<<<1, 32, 0, s>>>(part, (int)nb, 7, nullptr, cost, grad6, nullptr);
   ::rbf::note_launch();
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;

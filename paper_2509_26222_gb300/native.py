@@ -8,7 +8,10 @@ fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
+
+import numpy as np
 
 import torch
 
@@ -98,11 +101,22 @@ _SIGS = {
     "rbf_profile_enable": [_P, ctypes.c_int],
     "rbf_profile_read": [_P, _P, _P, _P, ctypes.c_int],
     "rbf_launch_count": [ctypes.POINTER(_I64)],
+    "rbf_soft_cost_normal": [_P, _P, _P, _P, _I64, _P, _P],
     "rbf_batch_update_eval": [_P, _P, ctypes.c_int32, _P],
 }
 
 STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward",
           "trsm32", "inverse", "invapply", "covblock", "schur", "enter"]
+
+
+def _so3_exp(v):
+    """Rotation matrix exp([v]_x) (Rodrigues)."""
+    v = np.asarray(v, dtype=np.float64)
+    a = float(np.linalg.norm(v))
+    K = np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
+    if a < 1e-12:
+        return np.eye(3) + K
+    return np.eye(3) + math.sin(a) / a * K + (1.0 - math.cos(a)) / (a * a) * (K @ K)
 
 
 def launch_count() -> int:
@@ -264,6 +278,30 @@ class Terrain:
         _check(self.lib.rbf_soft_cost(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], _ptr(buf[:1]),
                                       ctypes.c_void_p(buf.data_ptr() + 8), _ptr(resid), _stream()))
         return buf[0], buf[1:7], resid
+
+    def soft_cost_normal(self, R, t, pts, out=None):
+        """(cost, gradient (6), Gauss-Newton matrix A (6 x 6)) of the pose, device tensors."""
+        R = torch.as_tensor(R, dtype=torch.float64).cpu().contiguous()
+        t = torch.as_tensor(t, dtype=torch.float64).cpu().contiguous()
+        p = _dev_tensor(pts, torch.float32, 3)
+        buf = out if out is not None else torch.empty(28, dtype=torch.float64, device=p.device)
+        _check(self.lib.rbf_soft_cost_normal(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], _ptr(buf), _stream()))
+        iu = torch.triu_indices(6, 6, device=p.device)
+        A = torch.zeros(6, 6, dtype=torch.float64, device=p.device)
+        A[iu[0], iu[1]] = buf[7:28]
+        A = A + A.T - torch.diag(torch.diagonal(A))
+        return buf[0], buf[1:7], A
+
+    def lm_step(self, R, t, pts, mu=1e-3):
+        """One Levenberg-Marquardt step on the pose: solves (A + mu diag(A)) d = -g
+        (6 x 6, host) and returns the updated (R Exp(d_theta), t + d_t) and the cost
+        at the input pose."""
+        cost, g, A = self.soft_cost_normal(R, t, pts)
+        A = A.cpu().numpy()
+        g = g.cpu().numpy()
+        d = np.linalg.solve(A + mu * np.diag(np.diag(A)), -g)
+        R = np.asarray(R, dtype=np.float64)
+        return R @ _so3_exp(d[:3]), np.asarray(t, dtype=np.float64) + d[3:], float(cost)
 
     def soft_cost_backward(self, R, t, pts, gout=None):
         R = torch.as_tensor(R, dtype=torch.float64).cpu().contiguous()

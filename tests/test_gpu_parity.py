@@ -335,6 +335,37 @@ def test_soft_cost_forward_config3(N):
     assert np.any(np.abs(fw["r"]) > 0.05) and np.any(np.abs(fw["r"]) < 0.05)
 
 
+@pytest.mark.parametrize("loss", ["huber", "l2"])
+def test_soft_cost_normal_matrix_config3(N, loss):
+    """Cost, gradient and the Gauss-Newton matrix of the pose (LM step of
+    Sec. IV-C) on the 65,536 config-3 points, against the oracle."""
+    kw = dict(loss=N.LOSS_L2, lambda_m=0.5) if loss == "l2" else {}
+    cfg, T = _c3_terrain(N, **kw)
+    p32 = cfg["body"].astype(np.float32)
+    cost, g6, A = T.soft_cost_normal(cfg["R"], cfg["t"], dev(p32))
+    ref = O.soft_cost_normal(cfg["R"], cfg["t"], p32.astype(np.float64), cfg["centers"], cfg["w"], O.WENDLAND,
+                             rho=0.6, delta=cfg["delta"], loss=loss, lam_m=0.5)
+    assert abs(float(cost) - ref["cost"]) <= 1e-4 * abs(ref["cost"])
+    assert rel_inf(g6.cpu().numpy(), ref["grad6"]) < 1e-3
+    assert rel_inf(A.cpu().numpy(), ref["A"]) < 1e-3
+
+
+def test_lm_steps_recover_pose_on_gpu(N):
+    """Ten GPU LM steps from a perturbed pose recover the pose of points that
+    lie on the terrain (no noise, no outliers)."""
+    cfg, T = _c3_terrain(N)
+    rng = np.random.default_rng(4)
+    xy = rng.uniform(-5.0, 5.0, (20000, 2))
+    z = O.eval_h(xy, cfg["centers"], cfg["w"], O.WENDLAND, rho=0.6)[0]
+    R, t = cfg["R"], cfg["t"]
+    body = dev(((np.c_[xy, z] - t) @ R).astype(np.float32))
+    Rp = R @ O.so3_exp([0.01, -0.01, 0.02])
+    tp = t + np.array([0.03, -0.02, 0.02])
+    for _ in range(10):
+        Rp, tp, cost = T.lm_step(Rp, tp, body, mu=1e-4)
+    assert np.max(np.abs(Rp - R)) < 2e-4 and np.max(np.abs(tp - t)) < 2e-4
+
+
 def test_soft_cost_backward_config3(N):
     cfg, T = _c3_terrain(N)
     p32 = cfg["body"].astype(np.float32)

@@ -82,3 +82,49 @@ def test_flat_terrain_closed_form():
     assert np.allclose(fw["grad6"][3:], [0, 0, psi.sum()])
     gth = sum(psi[i] * (-(R @ O.skew(body[i])))[2] for i in range(50))
     assert np.allclose(fw["grad6"][:3], gth)
+
+
+def _on_surface(seed=1, n=400, kind=O.WENDLAND):
+    """Points lying exactly on the surface f under a known pose (zero residuals)."""
+    rng = np.random.default_rng(seed)
+    c = W.grid_centers(8, 8, 0, 0, 0.25)
+    w = rng.normal(0, 0.1, 64)
+    kw = dict(rho=0.6, sigma=0.15, cutoff_mult=40.0)
+    R, t = W.random_pose(rng)
+    xy = rng.uniform(0.4, 1.6, (n, 2))
+    z = O.eval_h(xy, c, w, kind, rho=kw["rho"], sigma=kw["sigma"], cutoff_mult=kw["cutoff_mult"])[0]
+    world = np.c_[xy, z]
+    body = (world - t) @ R
+    return R, t, body, c, w, kw
+
+
+@pytest.mark.parametrize("kind", [O.WENDLAND, O.GAUSSIAN])
+@pytest.mark.parametrize("loss", ["huber", "l2"])
+def test_gauss_newton_matrix_is_the_hessian_at_zero_residual(kind, loss):
+    """With every residual zero, the Hessian of the cost is sum psi'(0) J^T J,
+    which is the Gauss-Newton matrix A; checked against central differences
+    of the (finite-difference-pinned) pose gradient."""
+    R, t, body, c, w, kw = _on_surface(kind=kind)
+    nm = O.soft_cost_normal(R, t, body, c, w, kind, delta=0.05, loss=loss, lam_m=0.7, **kw)
+    assert nm["cost"] < 1e-20
+    e = 1e-6
+    Hfd = np.zeros((6, 6))
+    for k in range(6):
+        d = np.zeros(6); d[k] = e
+        gp = O.soft_cost(R @ expm(O.skew(d[:3])), t + d[3:], body, c, w, kind, delta=0.05, loss=loss,
+                         lam_m=0.7, **kw)["grad6"]
+        gm = O.soft_cost(R @ expm(O.skew(-d[:3])), t - d[3:], body, c, w, kind, delta=0.05, loss=loss,
+                         lam_m=0.7, **kw)["grad6"]
+        Hfd[:, k] = (gp - gm) / (2 * e)
+    Hfd = 0.5 * (Hfd + Hfd.T)
+    assert np.allclose(nm["A"], Hfd, rtol=1e-5, atol=1e-6 * np.abs(Hfd).max())
+
+
+@pytest.mark.parametrize("loss", ["huber", "l2"])
+def test_lm_steps_recover_the_pose(loss):
+    R, t, body, c, w, kw = _on_surface(seed=2)
+    Rp = R @ O.so3_exp([0.02, -0.015, 0.03])
+    tp = t + np.array([0.04, -0.03, 0.02])
+    for _ in range(12):
+        Rp, tp, cost = O.lm_step(Rp, tp, body, c, w, O.WENDLAND, mu=1e-4, delta=0.05, loss=loss, **kw)
+    assert np.max(np.abs(Rp - R)) < 1e-7 and np.max(np.abs(tp - t)) < 1e-7
