@@ -266,6 +266,12 @@ def run_ours(args, ws, rank, local):
     launches = N.launch_count() - l0
     total_ms = max_over_ranks(float(sum(times)), dev)
     a_last = int(T.active().numel())
+    # terrain fit on the timed frames (the paper's histogram statistic,
+    # Sec. VI-B: share of |p_z - f(p_xy)| < 0.05 m after dropping the largest 10 %)
+    res = torch.cat([(g[:, 2] - T.eval(g[:, :2])[0]).abs() for g, _, _ in dev_frames[args.warmup:]])
+    res = torch.sort(res).values[: int(0.9 * res.numel())]
+    fit = {"share_below_5cm_after_dropping_top10pct": float((res < 0.05).float().mean()),
+           "rms_m": float(torch.sqrt(torch.mean(res * res))), "points": int(res.numel())}
 
     # ----- the same frames again with the library's per-stage event timing on -----
     Tp = make_terrain()
@@ -441,7 +447,7 @@ def run_ours(args, ws, rank, local):
         c5["speedup_mixed_over_fp64"] = c5["fp64"]["ms_per_update"] / c5["mixed"]["ms_per_update"]
     return dict(times=times, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, prof=prof,
                 launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch,
-                other=other_line, exact=exact_line, c5=c5)
+                other=other_line, exact=exact_line, c5=c5, fit=fit)
 
 
 # ---------------------------------------------------------------------------
@@ -603,6 +609,7 @@ def main():
         "stage_ms_per_step": stage_ms,
         "other_precision_same_frames": r["other"],
         "exact_mode_same_frames": r["exact"],
+        "terrain_fit": r["fit"],
         "update_65536_centers": c5,
         "batch": r["batch"],
         "clocks": r["clocks"],

@@ -862,8 +862,9 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   Buf& Zdn = c->scratch(63);
   Buf& Zin = c->scratch(64);
   const int64_t ldw = (an + 3) & ~(int64_t)3;
-  // the inverse of a banded factor is dense: banded blocks keep the substitution
-  const bool use_inv = mixed && an <= c->inv_max && bw == BW_DENSE;
+  // (the inverse of a banded factor is dense, but for blocks this small the
+  // products with it still beat the chain of substitution steps)
+  const bool use_inv = mixed && an <= c->inv_max;
   if (mixed) {
     RBF_TRY(Wn.ensure((size_t)an * ldw * sizeof(float)));
     RBF_TRY(Zdn.ensure((size_t)((an + 63) / 64) * 64 * 64 * sizeof(float)));
