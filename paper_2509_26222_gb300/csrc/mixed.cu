@@ -68,7 +68,8 @@ __device__ __forceinline__ void mx_chol32(float* T, float* rd, float* col, int o
   for (int p = 0; p < 32; ++p) a[p] = (p <= lane) ? T[(o + lane) * MXS_LD + o + p] : 0.f;
   col[32 + lane] = 0.f;
   bool bad = false;
-#pragma unroll 1
+  // unrolled by 4: the pivot of step k + 1 overlaps the update of step k
+#pragma unroll 4
   for (int k = 0; k < 32; ++k) {
     float d = __shfl_sync(0xffffffffu, a[0], k);
     bad |= !(d > 0.f);
