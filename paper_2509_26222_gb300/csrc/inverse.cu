@@ -95,8 +95,11 @@ __device__ __forceinline__ void tile_mma(float (&acc)[4][4], const Mat A, const 
   }
 }
 
+// C = alpha acc, or C += alpha acc with atomics (the two halves of a K range
+// split in two: 0 + a + b equals 0 + b + a exactly, so the result does not
+// depend on which half lands first)
 __device__ __forceinline__ void tile_store(const float (&acc)[4][4], float alpha, float* C, int64_t ldc, int64_t i0,
-                                           int64_t j0, int64_t M, int64_t N) {
+                                           int64_t j0, int64_t M, int64_t N, bool add = false) {
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -105,7 +108,10 @@ __device__ __forceinline__ void tile_store(const float (&acc)[4][4], float alpha
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int64_t j = j0 + tx * 4 + v;
-      if (j < N) C[i * ldc + j] = alpha * acc[u][v];
+      if (j < N) {
+        if (add) atomicAdd(C + i * ldc + j, alpha * acc[u][v]);
+        else C[i * ldc + j] = alpha * acc[u][v];
+      }
     }
   }
 }
@@ -125,29 +131,45 @@ __global__ void k_inv_diag(const float* __restrict__ Zd, int64_t n, float* __res
 // half has h1 = b/2 rows, its lower half h2 = min(b/2, n - p b - b/2).
 // kind 0: T21 = L21 Z11 (Z11 lower: only k >= j contributes);
 // kind 1: Z21 = -Z22 T21 (Z22 lower: only k <= i contributes).
+// split = 2: blockIdx.z = 2 p + half, each half of the K range adds its
+// partial product into the (zeroed) output.
 __global__ void __launch_bounds__(256) k_trtri_level(int kind, int64_t b, int64_t n, const float* __restrict__ W,
                                                      int64_t ldw, float* __restrict__ Z, int64_t ldz,
-                                                     float* __restrict__ T) {
+                                                     float* __restrict__ T, int split) {
   __shared__ __align__(16) float As[TK][TLD];
   __shared__ __align__(16) float Bs[TK][TLD];
-  const int64_t p = blockIdx.z;
+  const int64_t p = split == 2 ? (blockIdx.z >> 1) : blockIdx.z;
+  const int half = split == 2 ? (int)(blockIdx.z & 1) : -1;
   const int64_t r1 = p * b, h1 = b / 2, r2 = r1 + h1;
   const int64_t h2 = (n - r2) < h1 ? (n - r2) : h1;
   if (h2 <= 0) return;
   const int64_t i0 = (int64_t)blockIdx.y * TG, j0 = (int64_t)blockIdx.x * TG;
   if (i0 >= h2 || j0 >= h1) return;
   float acc[4][4] = {};
+  int64_t kb, ke;
+  if (kind == 0) {
+    kb = j0;
+    ke = h1;
+  } else {
+    kb = 0;
+    ke = (i0 + TG) < h2 ? (i0 + TG) : h2;
+  }
+  if (half >= 0) {
+    int64_t mid = kb + ((ke - kb) / 2 + TK - 1) / TK * TK;
+    if (mid > ke) mid = ke;
+    if (half == 0) ke = mid;
+    else kb = mid;
+  }
   if (kind == 0) {
     Mat A{W + r2 * ldw + r1, ldw, false};
     Mat B{Z + r1 * ldz + r1, ldz, false};
-    tile_mma(acc, A, B, i0, j0, h2, h1, j0, h1, As, Bs);
-    tile_store(acc, 1.f, T + r2 * ldz + r1, ldz, i0, j0, h2, h1);
+    tile_mma(acc, A, B, i0, j0, h2, h1, kb, ke, As, Bs);
+    tile_store(acc, 1.f, T + r2 * ldz + r1, ldz, i0, j0, h2, h1, half >= 0);
   } else {
     Mat A{Z + r2 * ldz + r2, ldz, false};
     Mat B{T + r2 * ldz + r1, ldz, false};
-    int64_t ke = (i0 + TG) < h2 ? (i0 + TG) : h2;
-    tile_mma(acc, A, B, i0, j0, h2, h1, 0, ke, As, Bs);
-    tile_store(acc, -1.f, Z + r2 * ldz + r1, ldz, i0, j0, h2, h1);
+    tile_mma(acc, A, B, i0, j0, h2, h1, kb, ke, As, Bs);
+    tile_store(acc, -1.f, Z + r2 * ldz + r1, ldz, i0, j0, h2, h1, half >= 0);
   }
 }
 
@@ -257,13 +279,17 @@ rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const flo
   float* T = tb.as<float>();
   StageTimer st(c, RBF_STAGE_INVERSE, s, (double)n * n * n / 3.0);
   RBF_CUDA(cudaMemsetAsync(Z, 0, (size_t)n * ldz * sizeof(float), s));
+  RBF_CUDA(cudaMemsetAsync(T, 0, (size_t)n * ldz * sizeof(float), s));  // levels write disjoint blocks
   { k_inv_diag<<<cdiv(n, 64), 256, 0, s>>>(Zd, n, Z, ldz); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   for (int64_t b = 128; b / 2 < n; b *= 2) {
     int64_t h = b / 2;
-    dim3 grid(cdiv(h, TG), cdiv(h, TG), cdiv(n, b));
+    // levels whose tiles do not fill the GPU twice split K in two halves
+    const int64_t tiles = (int64_t)cdiv(h, TG) * cdiv(h, TG) * cdiv(n, b);
+    const int split = (tiles < 2 * 152 && h >= 256) ? 2 : 1;
+    dim3 grid(cdiv(h, TG), cdiv(h, TG), (unsigned)(cdiv(n, b) * split));
     for (int kind = 0; kind < 2; ++kind) {
-      { k_trtri_level<<<grid, 256, 0, s>>>(kind, b, n, W, ldw, Z, ldz, T); ::rbf::note_launch(); }
+      { k_trtri_level<<<grid, 256, 0, s>>>(kind, b, n, W, ldw, Z, ldz, T, split); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
     }
   }
