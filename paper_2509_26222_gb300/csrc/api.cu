@@ -591,6 +591,10 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
                  &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Hs.rp, &x->Hs.col, &x->Hs.val, &x->Hs_next.rp, &x->Hs_next.col, &x->Hs_next.val, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
+  for (auto& st : x->bs)
+    if (st) cudaStreamDestroy(st);
+  for (auto& ev : x->bev)
+    if (ev) cudaEventDestroy(ev);
   if (x->la_stream) cudaStreamDestroy(x->la_stream);
   for (auto& ev : x->la_ev)
     if (ev) cudaEventDestroy(ev);

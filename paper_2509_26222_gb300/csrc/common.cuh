@@ -109,6 +109,8 @@ struct Ctx {
   int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
   int64_t bw_lf = BW_DENSE_CTX;  // half-bandwidth of the float32 factor Lf
+  cudaStream_t bs[2] = {};           // side streams of the block stage
+  cudaEvent_t bev[3] = {};           // fork and joins of the block stage
   bool la_ok = true;                 // look-ahead factorization allowed
   cudaStream_t la_stream = nullptr;  // side stream of the look-ahead factorization
   cudaEvent_t la_ev[5] = {};          // panel ready (2), trailing done (2), join
@@ -270,7 +272,7 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
                       int64_t ldb, bool transpose, cudaStream_t s, int64_t bw = BW_DENSE);
 rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
-                    double* Cm, int64_t ldc, cudaStream_t s);
+                    double* Cm, int64_t ldc, cudaStream_t s, int slot = 28);
 // mixed precision (mixed.cu)
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
                        cudaStream_t s, int64_t bw = BW_DENSE);

@@ -486,7 +486,7 @@ __global__ void k_gemm_reduce(int64_t m, int64_t n, int nsplit, const double* __
 
 rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
                     int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc,
-                    cudaStream_t s) {
+                    cudaStream_t s, int slot) {
   if (m <= 0 || n <= 0) return RBF_OK;
   int64_t tiles = ((m + GT - 1) / GT) * ((n + GT - 1) / GT);
   if (tiles < 64 && k > 512) {
@@ -497,7 +497,7 @@ rbf_status gemm_f64(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, d
       kchunk = (k + nsplit - 1) / nsplit;
       nsplit = (k + kchunk - 1) / kchunk;
     }
-    Buf& part = c->scratch(28);
+    Buf& part = c->scratch(slot);
     RBF_TRY(part.ensure((size_t)nsplit * m * n * sizeof(double)));
     dim3 grid((unsigned)((m * n + 255) / 256), (unsigned)nsplit);
     { k_gemm_splitk<<<grid, 256, 0, s>>>(ta, tb, m, n, k, kchunk, A, lda, B, ldb, part.as<double>()); ::rbf::note_launch(); }

@@ -686,18 +686,36 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_TRY(u.ensure((size_t)an * sizeof(double)));
   RBF_CUDA(cudaMemsetAsync(Hn.p, 0, (size_t)an * an * sizeof(double), s));
   Buf& Pdd = c->scratch(38);
+  // The covariance block of the leaving centers, the information of the
+  // entering ones and the Schur complement of the staying ones read only the
+  // previous state and write disjoint outputs: they run on three streams.
+  // (The FP64 path and large returning blocks keep one stream: their
+  // cooperative substitution solves share one set of ready flags.)
+  const bool par = mixed && e_returning <= SPD_SMALL_MAX && (d > 0 || e > 0);
+  cudaStream_t sA = s, sC = s;
+  if (par) {
+    for (int q = 0; q < 2; ++q)
+      if (!c->bs[q]) RBF_CUDA(cudaStreamCreateWithFlags(&c->bs[q], cudaStreamNonBlocking));
+    for (auto& ev : c->bev)
+      if (!ev) RBF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    sA = c->bs[0];
+    sC = c->bs[1];
+    RBF_CUDA(cudaEventRecord(c->bev[0], s));
+    RBF_CUDA(cudaStreamWaitEvent(sA, c->bev[0], 0));
+    RBF_CUDA(cudaStreamWaitEvent(sC, c->bev[0], 0));
+  }
   if (d > 0) {
     Buf& Y = c->scratch(39);
     RBF_TRY(Y.ensure((size_t)ap * d * sizeof(double)));
     RBF_TRY(Pdd.ensure((size_t)d * d * sizeof(double)));
-    { k_unit_rhs<<<nblk(ap * d), 256, 0, s>>>(Y.as<double>(), ap, d, Dl.as<int32_t>()); ::rbf::note_launch(); }
+    { k_unit_rhs<<<nblk(ap * d), 256, 0, sA>>>(Y.as<double>(), ap, d, Dl.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    StageTimer st_cb(c, RBF_STAGE_COVBLOCK, s, 0.0);
+    StageTimer st_cb(c, RBF_STAGE_COVBLOCK, sA, 0.0);
     if (mixed) {
       // X = H_prev^{-1} E_D by refined solves with the float32 factor; P_DD = X[D, :]
       RBF_TRY(mixed_cov(c, c->H.as<double>(), c->ldH, &c->Hs, c->Lf.as<float>(), c->ldw, c->Zd.as<float>(),
                         c->zi_valid ? c->Zi.as<float>() : nullptr, ap, Y.as<double>(), d, Dl.as<int32_t>(),
-                        c->refine_sweeps_cov, Pdd.as<double>(), s, c->bw_lf));
+                        c->refine_sweeps_cov, Pdd.as<double>(), sA, c->bw_lf));
     } else {
       // Y = L_prev^{-1} E_D, P_DD = Y^T Y
       RBF_TRY(trsm_lower(c, c->L.as<double>(), ap, c->ldH, Y.as<double>(), d, d, false, s, c->bw_lf));
@@ -705,6 +723,50 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
                        Pdd.as<double>(), d, s));
     }
   }
+  // 6. entering centers: inverse of their stored covariance block
+  if (e > 0) {
+    StageTimer st_en(c, RBF_STAGE_ENTER, sC, 0.0);
+    if (!c->pg_on || e_returning == 0) {
+      // never-departed centers keep the prior P = I / lambda with no coupling
+      { k_scatter_diag<<<nblk(e), 256, 0, sC>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    } else {
+      // the stored covariance couples the returning centers R only among
+      // themselves (fresh ones F keep the uncoupled prior), so the block's
+      // inverse is diag(P_RR^{-1}, lambda I)
+      const int64_t r = e_returning, f = e - e_returning;
+      Buf& rf = c->scratch(80);
+      Buf& rp = c->scratch(81);
+      Buf& Rl = c->scratch(82);
+      Buf& Fl = c->scratch(83);
+      RBF_TRY(rf.ensure((size_t)(e + 1) * sizeof(int32_t)));
+      RBF_TRY(rp.ensure((size_t)(e + 1) * sizeof(int32_t)));
+      RBF_TRY(Rl.ensure((size_t)(r + 1) * sizeof(int32_t)));
+      RBF_TRY(Fl.ensure((size_t)(f + 1) * sizeof(int32_t)));
+      { k_ret_flags<<<nblk(e), 256, 0, sC>>>(An.as<int32_t>(), El.as<int32_t>(), e, c->departed.as<int32_t>(),
+                                          rf.as<int32_t>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      RBF_TRY(scan_i32(c, rf.as<int32_t>(), rp.as<int32_t>(), e, sC, 88));
+      { k_split_flags<<<nblk(e), 256, 0, sC>>>(rf.as<int32_t>(), rp.as<int32_t>(), e, El.as<int32_t>(),
+                                            Rl.as<int32_t>(), Fl.as<int32_t>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      if (f > 0) {
+        { k_scatter_diag<<<nblk(f), 256, 0, sC>>>(Fl.as<int32_t>(), f, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+      }
+      Buf& Gb = c->scratch(42);
+      RBF_TRY(Gb.ensure((size_t)r * r * sizeof(double)));
+      { k_gather_global<<<nblk(r * r), 256, 0, sC>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
+                                                   Rl.as<int32_t>(), r, Gb.as<double>()); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, sC));
+      else RBF_TRY(spd_inverse(c, Gb.as<double>(), r, sC, 43));
+      { k_scatter_sym<<<nblk(r * r), 256, 0, sC>>>(Gb.as<double>(), r, r, Rl.as<int32_t>(), Hn.as<double>(),
+                                                ld); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+    }
+  }
+
   if (d > 0) {
     StageTimer st_sc(c, RBF_STAGE_SCHUR, s, 0.0);
     if (sN > 0) {
@@ -756,9 +818,9 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
           RBF_CUDA(cudaGetLastError());
           RBF_TRY(spd_inverse_small(c, Gd.as<double>(), d, s));
           RBF_TRY(gemm_f64(c, false, false, d, nN, d, 1.0, Gd.as<double>(), d, T.as<double>() + d, t, 0.0,
-                           Yb.as<double>(), nN, s));
+                           Yb.as<double>(), nN, s, 87));
           RBF_TRY(gemm_f64(c, false, false, nN, nN, d, -1.0, T.as<double>() + d * t, t, Yb.as<double>(), nN, 1.0,
-                           T.as<double>() + d * t + d, t, s));
+                           T.as<double>() + d * t + d, t, s, 87));
         } else {
           RBF_TRY(potrf_lower(c, T.as<double>(), t, t, d, false, s));
         }
@@ -774,50 +836,12 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaGetLastError());
   }
 
-  // 6. entering centers: inverse of their stored covariance block
-  if (e > 0) {
-    StageTimer st_en(c, RBF_STAGE_ENTER, s, 0.0);
-    if (!c->pg_on || e_returning == 0) {
-      // never-departed centers keep the prior P = I / lambda with no coupling
-      { k_scatter_diag<<<nblk(e), 256, 0, s>>>(El.as<int32_t>(), e, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-    } else {
-      // the stored covariance couples the returning centers R only among
-      // themselves (fresh ones F keep the uncoupled prior), so the block's
-      // inverse is diag(P_RR^{-1}, lambda I)
-      const int64_t r = e_returning, f = e - e_returning;
-      Buf& rf = c->scratch(80);
-      Buf& rp = c->scratch(81);
-      Buf& Rl = c->scratch(82);
-      Buf& Fl = c->scratch(83);
-      RBF_TRY(rf.ensure((size_t)(e + 1) * sizeof(int32_t)));
-      RBF_TRY(rp.ensure((size_t)(e + 1) * sizeof(int32_t)));
-      RBF_TRY(Rl.ensure((size_t)(r + 1) * sizeof(int32_t)));
-      RBF_TRY(Fl.ensure((size_t)(f + 1) * sizeof(int32_t)));
-      { k_ret_flags<<<nblk(e), 256, 0, s>>>(An.as<int32_t>(), El.as<int32_t>(), e, c->departed.as<int32_t>(),
-                                          rf.as<int32_t>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      RBF_TRY(scan_i32(c, rf.as<int32_t>(), rp.as<int32_t>(), e, s, 77));
-      { k_split_flags<<<nblk(e), 256, 0, s>>>(rf.as<int32_t>(), rp.as<int32_t>(), e, El.as<int32_t>(),
-                                            Rl.as<int32_t>(), Fl.as<int32_t>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      if (f > 0) {
-        { k_scatter_diag<<<nblk(f), 256, 0, s>>>(Fl.as<int32_t>(), f, c->cfg.lambda, Hn.as<double>(), ld); ::rbf::note_launch(); }
-        RBF_CUDA(cudaGetLastError());
-      }
-      Buf& Gb = c->scratch(42);
-      RBF_TRY(Gb.ensure((size_t)r * r * sizeof(double)));
-      { k_gather_global<<<nblk(r * r), 256, 0, s>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
-                                                   Rl.as<int32_t>(), r, Gb.as<double>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, s));
-      else RBF_TRY(spd_inverse(c, Gb.as<double>(), r, s, 43));
-      { k_scatter_sym<<<nblk(r * r), 256, 0, s>>>(Gb.as<double>(), r, r, Rl.as<int32_t>(), Hn.as<double>(),
-                                                ld); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-    }
+  if (par) {
+    RBF_CUDA(cudaEventRecord(c->bev[1], sA));
+    RBF_CUDA(cudaEventRecord(c->bev[2], sC));
+    RBF_CUDA(cudaStreamWaitEvent(s, c->bev[1], 0));
+    RBF_CUDA(cudaStreamWaitEvent(s, c->bev[2], 0));
   }
-
   delete st_blk;
   // 7. + m~ m~^T and u = m~ e
   {
