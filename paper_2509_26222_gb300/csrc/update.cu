@@ -691,7 +691,19 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   // previous state and write disjoint outputs: they run on three streams.
   // (The FP64 path and large returning blocks keep one stream: their
   // cooperative substitution solves share one set of ready flags.)
-  const bool par = mixed && e_returning <= SPD_SMALL_MAX && (d > 0 || e > 0);
+  {
+    Buf& G0 = c->scratch(68);
+    Buf& U0 = c->scratch(69);
+    size_t gbytes = (size_t)an * an * sizeof(unsigned long long);
+    size_t ubytes = (size_t)2 * an * sizeof(unsigned long long);
+    if (G0.bytes < gbytes || U0.bytes < ubytes || c->gacc_dirty) {
+      RBF_TRY(G0.ensure(gbytes));
+      RBF_TRY(U0.ensure(ubytes));
+      RBF_CUDA(cudaMemsetAsync(G0.p, 0, G0.bytes, s));
+      RBF_CUDA(cudaMemsetAsync(U0.p, 0, U0.bytes, s));
+    }
+  }
+  const bool par = mixed && e_returning <= SPD_SMALL_MAX;
   cudaStream_t sA = s, sC = s;
   if (par) {
     for (int q = 0; q < 2; ++q)
@@ -723,6 +735,22 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
                        Pdd.as<double>(), d, s));
     }
   }
+  // m~ m~^T and m~ e: exact integer accumulation into cleared accumulators
+  // (added to H' once the block stage has written it)
+  if (an > 65535) return fail(RBF_EINVAL, "active block of %lld centers exceeds 65535", (long long)an);
+  Buf& G = c->scratch(68);
+  Buf& U = c->scratch(69);
+  const int gs = 62 - (int)ceil(log2((double)n + 1.0));
+  const double gscale = ldexp(1.0, gs);
+  {
+    StageTimer st(c, RBF_STAGE_ASSEMBLY, sC, 0.0);
+    c->gacc_dirty = true;
+    { k_gram_atomic<<<nblk(n * 32), 256, 0, sC>>>(n, row_ptr.as<int64_t>(), lcol.as<int32_t>(), val.as<double>(),
+                                                ev.as<double>(), an, gscale, G.as<unsigned long long>(),
+                                                U.as<unsigned long long>()); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  }
+
   // 6. entering centers: inverse of their stored covariance block
   if (e > 0) {
     StageTimer st_en(c, RBF_STAGE_ENTER, sC, 0.0);
@@ -843,39 +871,34 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaStreamWaitEvent(s, c->bev[2], 0));
   }
   delete st_blk;
-  // 7. + m~ m~^T and u = m~ e
+  // 7. + m~ m~^T and u = m~ e (accumulated above, beside the block stage)
   {
     StageTimer st(c, RBF_STAGE_ASSEMBLY, s, 0.0);
-    if (an > 65535) return fail(RBF_EINVAL, "active block of %lld centers exceeds 65535", (long long)an);
-    Buf& G = c->scratch(68);
-    Buf& U = c->scratch(69);
-    size_t gbytes = (size_t)an * an * sizeof(unsigned long long);
-    size_t ubytes = (size_t)2 * an * sizeof(unsigned long long);
-    if (G.bytes < gbytes || U.bytes < ubytes || c->gacc_dirty) {
-      RBF_TRY(G.ensure(gbytes));
-      RBF_TRY(U.ensure(ubytes));
-      RBF_CUDA(cudaMemsetAsync(G.p, 0, G.bytes, s));
-      RBF_CUDA(cudaMemsetAsync(U.p, 0, U.bytes, s));
-    }
-    int gs = 62 - (int)ceil(log2((double)n + 1.0));
-    double gscale = ldexp(1.0, gs);
-    c->gacc_dirty = true;
-    { k_gram_atomic<<<nblk(n * 32), 256, 0, s>>>(n, row_ptr.as<int64_t>(), lcol.as<int32_t>(), val.as<double>(),
-                                               ev.as<double>(), an, gscale, G.as<unsigned long long>(),
-                                               U.as<unsigned long long>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
     dim3 mg((unsigned)((an + 255) / 256 < 8 ? (an + 255) / 256 : 8), (unsigned)an);
     { k_gram_merge<<<mg, 256, 0, s>>>(an, 1.0 / gscale, G.as<unsigned long long>(), U.as<unsigned long long>(),
                                       Hn.as<double>(), ld, u.as<double>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     c->gacc_dirty = false;
-    if (mixed) RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, s));
   }
   // Until a center has left some block there is no Schur-complement fill and
   // H' has the band structure of m~ m~^T: read its half-bandwidth then, and
   // skip the zero blocks outside the band in the factorization and solves.
+  // Otherwise the compressed rows of H' (needed from the first residual of
+  // the solve on) are built on a side stream beside the factorization.
   int64_t bw = BW_DENSE;
-  if (!c->pg_on && d == 0) {
+  const bool band_probe = !c->pg_on && d == 0;
+  const bool csr_side = mixed && par && !band_probe;
+  if (mixed) {
+    if (csr_side) {
+      RBF_CUDA(cudaEventRecord(c->bev[0], s));
+      RBF_CUDA(cudaStreamWaitEvent(sA, c->bev[0], 0));
+      RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, sA));
+      RBF_CUDA(cudaEventRecord(c->bev[1], sA));
+    } else {
+      RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, s));
+    }
+  }
+  if (band_probe) {
     if (mixed && c->Hs_next.valid) RBF_TRY(csr_bandwidth(c, an, &bw, s));
     else RBF_TRY(dense_bandwidth(c, Hn.as<double>(), ld, an, &bw, s));
     if (3 * bw >= an) bw = BW_DENSE;
@@ -901,6 +924,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s, bw));
   }
+  if (csr_side) RBF_CUDA(cudaStreamWaitEvent(s, c->bev[1], 0));
   int flag = 0;
   {
     StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 2.0 * c->refine_sweeps + 2.0 * (c->refine_sweeps - 1) : 2.0) *
