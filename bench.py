@@ -141,6 +141,11 @@ class Clocks:
 # DRAM bytes per query of the lattice evaluation kernel, from one ncu capture
 # (2^24 uniform queries on the 64x64 lattice: 134.31 MB read + 141.67 MB written).
 EVAL_DRAM_BYTES_PER_QUERY = (134.307840e6 + 141.672192e6) / (1 << 24)
+# DRAM bytes (read + write) per launch of k_mx_step, the mean over 400 launches
+# of the frame sequence (ncu dram__bytes_read.sum + dram__bytes_write.sum on
+# `bench.py --steps 2 --warmup 3 --no-cpu --eval-log2 20 --batch-patches 0
+# --c5-reps 0 --no-other`); the writes of the step stay in L2.
+MX_STEP_DRAM_BYTES_PER_LAUNCH = 537914.24 + 0.0
 
 
 def frame_arrays(k):
@@ -561,6 +566,10 @@ def main():
         roof = {"kernel": kname, "stage": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                 "frac": ach / peak, "traffic": None, "peak_kind": pkind, "launches": int(cnt),
                 "ms_per_launch": ms / max(cnt, 1), "work_per_launch": mult * work / max(cnt, 1)}
+        if dom == "panel":
+            roof["traffic"] = MX_STEP_DRAM_BYTES_PER_LAUNCH
+            roof["traffic_source"] = ("ncu dram__bytes_read+write per k_mx_step launch, mean of 400 launches "
+                                      "of the same frame sequence")
     trail = prof["trailing"]
     roof_tc = None
     if trail[0] > 0:
