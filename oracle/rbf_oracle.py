@@ -48,6 +48,11 @@ in the design notes with its justification):
 * G17 Huber_delta(r) = r^2/2 if |r| <= delta else delta (|r| - delta/2);
       loss "l2" gives the paper's lambda_M r^2.
 * G18 residual r_i = (R p_i + t)_z - wheel_offset - f((R p_i + t)_xy).
+* G21 evaluation on a regular raster (the separable form of the Gaussian on a
+      lattice): the truncation is per axis, |dx| < r and |dy| < r with
+      r = cutoff_mult * sigma, each decided by the float32 rule of G14.  It keeps
+      every term of the circular rule of G9 and adds corner terms, each below
+      exp(-cutoff_mult^2 / 2) |w_j|.
 """
 from __future__ import annotations
 
@@ -60,7 +65,7 @@ GAUSSIAN = 1
 
 __all__ = [
     "WENDLAND", "GAUSSIAN", "phi", "grad_coef", "support_radius_eval",
-    "support_radius_assembly", "fl32", "member_f32", "neighbors", "eval_h",
+    "support_radius_assembly", "fl32", "member_f32", "neighbors", "eval_h", "raster_coords", "eval_grid",
     "select_centers", "design_rows", "batch_ridge", "ridge_sparse", "CovStore", "BlockState",
     "block_update", "ExactState", "exact_update", "skew", "huber", "huber_psi",
     "soft_cost", "soft_cost_backward", "soft_cost_normal", "so3_exp", "lm_step",
@@ -191,6 +196,63 @@ def eval_h(q_xy, c_xy, w, kind, rho=0.6, sigma=0.04, cutoff_mult=4.0,
         out[3][s:s + chunk] = np.abs(th).sum(1)
         out[4][s:s + chunk] = np.abs(tx).sum(1)
         out[5][s:s + chunk] = np.abs(ty).sum(1)
+    return tuple(out)
+
+
+def raster_coords(q0, dq, nq):
+    """Raster coordinates q0 + k dq, k = 0..nq-1, in float64 (the product and
+    the sum each rounded once); the membership rule uses their float32 copies."""
+    k = np.arange(nq, dtype=np.float64)
+    return q0 + k * dq
+
+
+def eval_grid(qx0, qy0, dq, nqx, nqy, c_xy, w, sigma=0.04, cutoff_mult=4.0, chunk=256):
+    """Gaussian h and grad h on the raster (qx0 + k dq, qy0 + l dq),
+    k < nqx, l < nqy, truncated per axis (reading G21): center j contributes
+    to raster point q iff |q_x - c_x| < r and |q_y - c_y| < r with
+    r = cutoff_mult * sigma, each axis decided by the float32 rule of G14
+    (dx = q_x - c_x and dx * dx rounded to float32, member iff dx*dx < r*r).
+    The terms are Eq. RBF_fml with Eq. RBF_def and their gradients
+    (Eq. manidolf_grad_detail, sign per G5), summed in FP64 over every center.
+
+    Returns arrays of shape (nqy, nqx), row l = y index:
+    (h, gx, gy, abs_h, abs_gx, abs_gy), abs_* the sums of |term| (the scale of
+    the cancellation-safe tolerance).
+    """
+    c = np.asarray(c_xy, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    xs = raster_coords(qx0, dq, nqx)
+    ys = raster_coords(qy0, dq, nqy)
+    r32 = np.float32(cutoff_mult * sigma)
+    r2 = np.float32(r32 * r32)
+    cx32, cy32 = fl32(c[:, 0]), fl32(c[:, 1])
+    out = [np.zeros((nqy, nqx)) for _ in range(6)]
+    inv_s2 = 1.0 / (sigma * sigma)
+    for l in range(nqy):
+        y = ys[l]
+        dy32 = (np.float32(y) - cy32).astype(np.float32)
+        in_y = (dy32 * dy32).astype(np.float32) < r2
+        if not in_y.any():
+            continue
+        cj = c[in_y]
+        wj = w[in_y]
+        dy = y - cj[:, 1]
+        cx32j = cx32[in_y]
+        for s in range(0, nqx, chunk):
+            x = xs[s:s + chunk]
+            dx32 = (fl32(x)[:, None] - cx32j[None, :]).astype(np.float32)
+            in_x = (dx32 * dx32).astype(np.float32) < r2
+            dx = x[:, None] - cj[None, :, 0]
+            k = np.exp(-(dx * dx + dy[None, :] * dy[None, :]) * (0.5 * inv_s2))
+            th = np.where(in_x, wj[None, :] * k, 0.0)
+            tx = -th * dx * inv_s2
+            ty = -th * dy[None, :] * inv_s2
+            out[0][l, s:s + chunk] = th.sum(1)
+            out[1][l, s:s + chunk] = tx.sum(1)
+            out[2][l, s:s + chunk] = ty.sum(1)
+            out[3][l, s:s + chunk] = np.abs(th).sum(1)
+            out[4][l, s:s + chunk] = np.abs(tx).sum(1)
+            out[5][l, s:s + chunk] = np.abs(ty).sum(1)
     return tuple(out)
 
 
