@@ -138,6 +138,27 @@ rbf_status rbf_update(rbf_ctx* ctx, const float* pts, int64_t n, double noise, v
  * cutoff_mult*sigma (Gaussian), in float32. */
 rbf_status rbf_eval(rbf_ctx* ctx, const float* q, int64_t Q, float* h, float* grad, void* stream);
 
+/* h and grad h on the regular raster q_kl = (qx0 + k dq, qy0 + l dq),
+ * k < nqx, l < nqy (Eq. RBF_fml, Eq. manidolf_grad_detail), for the Gaussian
+ * kernel with the centers on a square lattice: the Gaussian factorises per
+ * axis, and the sums over a tile of 128 x 128 raster points become products
+ * of small matrices, run on the tensor cores with every float32 operand split
+ * into two bfloat16 parts (float32 accuracy of each term, about 2^-16).
+ * Truncation is per axis: center j contributes iff |q_x - c_x| < r and
+ * |q_y - c_y| < r, r = cutoff_mult * sigma, each decided in float32 as for
+ * rbf_eval.  This keeps every term rbf_eval keeps plus the corners of the
+ * square, each below exp(-cutoff_mult^2 / 2) |w_j|.
+ * h: nqy x nqx float32, row l = raster row (device); grad: nqy x nqx x 2
+ * float32 (d/dx, d/dy), may be NULL (device).  The coordinates are rounded to
+ * float32 after qx0 + k dq is formed in float64.
+ * RBF_EINVAL: not the Gaussian kernel, centers not on a lattice, dq <= 0 or
+ * non-finite arguments.  RBF_ERANGE: 127 dq + 2 r exceeds 60.5 lattice
+ * spacings (a tile's window must fit in 64 nodes; evaluate coarser rasters
+ * with rbf_eval).  Asynchronous; a tile whose bounded wait for the tensor
+ * cores gives up (which a correct launch never does) is written as NaN. */
+rbf_status rbf_eval_grid(rbf_ctx* ctx, double qx0, double qy0, double dq, int64_t nqx, int64_t nqy, float* h,
+                         float* grad, void* stream);
+
 /* Soft-constraint cost (Sec. IV-C) over n body-frame points (pts: n x 3
  * float32) under the pose R (host, 3x3 row-major float64), t (host, 3 float64):
  * q_i = R p_i + t, r_i = q_z - wheel_offset - f(q_xy),
@@ -264,7 +285,8 @@ enum {
   RBF_STAGE_COVBLOCK = 12,  /* covariance block of the leaving centers (nested inside BLOCK) */
   RBF_STAGE_SCHUR = 13,     /* information of the staying centers (nested inside BLOCK) */
   RBF_STAGE_ENTER = 14,     /* information of the entering centers (nested inside BLOCK) */
-  RBF_NSTAGE = 15
+  RBF_STAGE_EVAL_GRID = 15, /* rbf_eval_grid (bytes: 4 out per raster point, 12 with the gradient) */
+  RBF_NSTAGE = 16
 };
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int on);
 /* Number of CUDA kernels librbfgb.so has launched since it was loaded (all

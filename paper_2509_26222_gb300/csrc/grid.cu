@@ -1,0 +1,379 @@
+// Gaussian terrain and gradient on a regular raster, on the tensor cores.
+//
+// With the centers on the square lattice c_ij = (x_i, y_j) the Gaussian of
+// Eq. RBF_def factorises per axis, exp(-(dx^2 + dy^2) / 2 s^2) = g(dx) g(dy),
+// and so does the truncation when the window is taken per axis (|dx| < r and
+// |dy| < r, r = cutoff_mult * s).  On a tile of 128 x 128 raster points
+// (x_k, y_l) the terrain and its gradient (Eq. RBF_fml, Eq. manidolf_grad_detail
+// with the sign of reading G5) are then products of small matrices over a
+// window of 64 x 64 lattice nodes:
+//     T1 = W Ex^T,   T2 = W Ex'^T                       (stage 1)
+//     H = Ey T1,     Gx = Ey T2,     Gy = Ey' T1        (stage 2)
+// with Ex[k][i] = g(x_k - x_i), Ex'[k][i] = -(x_k - x_i) / s^2 g(x_k - x_i), and
+// Ey, Ey' likewise.  Both stages run as tcgen05 MMAs (M = 128, K = 64) with
+// every float32 operand split into two bfloat16 parts, a = a_hi + a_lo, and the
+// three products a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in float32 in
+// tensor memory (relative error about 2^-16 per term).  The stage-1 results
+// are read back from tensor memory, split the same way and written to shared
+// memory as the K-major B operands of stage 2.
+//
+// Operand tiles are K-major with the 128-byte swizzle: one row of 64 bfloat16
+// per matrix row, written by the CTA's threads with 16-byte shared stores.
+// Thread 0 issues the MMAs and commits them to an mbarrier; every wait is
+// bounded, and a tile whose wait gives up is written as NaN.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "tc_util.cuh"
+
+namespace rbf {
+namespace {
+
+constexpr int GT = 128;                 // raster points per tile side (M and N of stage 2)
+constexpr int GK = 64;                  // lattice nodes per window side (K of both stages, N of stage 1)
+constexpr int OP_ROWS128 = GT * GK * 2; // 16 KiB: 128 rows x 64 bfloat16
+constexpr int OP_ROWS64 = GK * GK * 2;  // 8 KiB: 64 rows x 64 bfloat16
+// shared-memory map (offsets from the 1024-byte aligned base)
+constexpr int S_EX_HI = 0, S_EX_LO = 1 * OP_ROWS128, S_EXD_HI = 2 * OP_ROWS128, S_EXD_LO = 3 * OP_ROWS128;
+constexpr int S_W_HI = 4 * OP_ROWS128, S_W_LO = S_W_HI + OP_ROWS64;
+constexpr int S_EY_HI = S_W_LO + OP_ROWS64, S_EY_LO = S_EY_HI + OP_ROWS128;
+constexpr int S_EYD_HI = S_EY_LO + OP_ROWS128, S_EYD_LO = S_EYD_HI + OP_ROWS128;
+constexpr int S_END = S_EYD_LO + OP_ROWS128;  // 144 KiB
+// stage 2 reuses the stage-1 A tiles for T1^T and T2^T (hi and lo)
+constexpr int S_T1_HI = S_EX_HI, S_T1_LO = S_EX_LO, S_T2_HI = S_EXD_HI, S_T2_LO = S_EXD_LO;
+constexpr int GRID_SMEM = S_END + 1024;
+// tensor-memory columns
+constexpr uint32_t TM_D1 = 0, TM_D2 = 64, TM_H = 128, TM_GX = 256, TM_GY = 384, TM_COLS = 512;
+
+// Instruction descriptor, kind::f16: D float32, A = B = bfloat16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(GT >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_n(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum,
+                                           uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %3, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(accum), "r"(idesc));
+}
+
+// D (+)= A B^T over K = 64 as the three split products, A and B given as
+// (hi, lo) shared-memory tiles.
+__device__ __forceinline__ void mma_split(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                          uint32_t b_lo, uint32_t idesc) {
+  const uint32_t as[3] = {a_hi, a_hi, a_lo};
+  const uint32_t bs[3] = {b_hi, b_lo, b_hi};
+  uint32_t accum = 0;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const uint64_t ad = tc::sdesc_sw128(as[p]), bd = tc::sdesc_sw128(bs[p]);
+#pragma unroll
+    for (int kk = 0; kk < GK / 16; ++kk) {
+      mma_bf16_n(tmem_d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), accum, idesc);
+      accum = 1;
+    }
+  }
+}
+
+// (hi, lo) bfloat16 parts of two floats, packed as the pair (v0, v1).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  float2 hf = __bfloat1622float2(h);
+  __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+  hi = *reinterpret_cast<uint32_t*>(&h);
+  lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void st_chunk(uint8_t* tile, int row, int chunk, const uint32_t (&v)[4]) {
+  *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row, chunk)) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+struct GridParams {
+  double qx0, qy0, dq;  // raster point (k, l) = (qx0 + k dq, qy0 + l dq)
+  int64_t nqx, nqy;
+  double lx0, ly0, lh;  // lattice node i at lx0 + (i + 1/2) lh
+  double r;             // window radius (float64, for the window origins)
+  int nx, ny;
+  float r2;             // fl32(r)^2 rounded to float32 (membership rule)
+  float inv2s2, inv_s2; // 1 / (2 s^2), 1 / s^2
+};
+
+// First lattice node of the window of a tile whose first raster coordinate
+// is q (one node of slack below; the host checks that 64 nodes cover the tile).
+__device__ __forceinline__ int window_origin(double q, double r, double l0, double lh, int n) {
+  double t = (q - r - l0) / lh - 0.5;
+  if (!(t > -2.0)) t = -2.0;
+  if (t > (double)n) t = (double)n;
+  int i = (int)floor(t) - 1;
+  return i < 0 ? 0 : i;
+}
+
+// Rows of g and g' for one raster coordinate q over the window nodes
+// o .. o + 63 (nodes >= n, and raster points outside the raster, give zeros).
+__device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int s_dhi, int s_dlo, int row,
+                                          bool in, float q, const float* __restrict__ nodes, int o, int n,
+                                          const GridParams& P) {
+#pragma unroll 1
+  for (int c = 0; c < GK / 8; ++c) {
+    uint32_t hv[4], lv[4], dhv[4], dlv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float g[2], gd[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = o + c * 8 + 2 * e + u;
+        g[u] = 0.f;
+        gd[u] = 0.f;
+        if (in && i < n) {
+          const float d = __fsub_rn(q, nodes[i]);
+          const float d2 = __fmul_rn(d, d);
+          if (d2 < P.r2) {
+            g[u] = __expf(-d2 * P.inv2s2);
+            gd[u] = -(d * P.inv_s2) * g[u];
+          }
+        }
+      }
+      split2(g[0], g[1], hv[e], lv[e]);
+      split2(gd[0], gd[1], dhv[e], dlv[e]);
+    }
+    st_chunk(smem + s_hi, row, c, hv);
+    st_chunk(smem + s_lo, row, c, lv);
+    st_chunk(smem + s_dhi, row, c, dhv);
+    st_chunk(smem + s_dlo, row, c, dlv);
+  }
+}
+
+// Bounded wait of thread 0 for the MMAs committed to `mbar` (phase `ph`);
+// the verdict goes to every thread through shared memory.
+__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t ph, int* done_s) {
+  if (threadIdx.x == 0) {
+    long long it = 0;
+    bool ok;
+    while (!(ok = tc::mbar_try_wait(mbar, ph)) && ++it < tc::WAIT_LIMIT) {
+    }
+    *done_s = ok ? 1 : 0;
+  }
+  __syncthreads();
+  tc::fence_after();
+  return *done_s != 0;
+}
+
+__global__ void __launch_bounds__(GT) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
+                                                     const float* __restrict__ ys, const float* __restrict__ W,
+                                                     float* __restrict__ hout, float* __restrict__ gout, int vec) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int done_s;
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t k0 = (int64_t)blockIdx.x * GT, l0 = (int64_t)blockIdx.y * GT;
+  const int io = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.lh, P.nx);
+  const int jo = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.lh, P.ny);
+
+  // operands: row t of Ex, Ex' (raster column k0 + t) and of Ey, Ey' (raster row l0 + t)
+  {
+    const int64_t k = k0 + t, l = l0 + t;
+    const bool kin = k < P.nqx, lin = l < P.nqy;
+    const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
+    const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
+    axis_rows(sm, S_EX_HI, S_EX_LO, S_EXD_HI, S_EXD_LO, t, kin, qx, xs, io, P.nx, P);
+    axis_rows(sm, S_EY_HI, S_EY_LO, S_EYD_HI, S_EYD_LO, t, lin, qy, ys, jo, P.ny, P);
+    // window weights: row j = t / 2 (N of stage 1), nodes i (K), half a row per thread
+    const int j = t >> 1, jg = jo + j;
+#pragma unroll 1
+    for (int c = (t & 1) * 4; c < (t & 1) * 4 + 4; ++c) {
+      uint32_t hv[4], lv[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int ig = io + c * 8 + 2 * e + u;
+          v[u] = (jg < P.ny && ig < P.nx) ? W[(int64_t)jg * P.nx + ig] : 0.f;
+        }
+        split2(v[0], v[1], hv[e], lv[e]);
+      }
+      st_chunk(sm + S_W_HI, j, c, hv);
+      st_chunk(sm + S_W_LO, j, c, lv);
+    }
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, TM_COLS);
+  if (t == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t base = tc::smem_u32(sm);
+
+  // stage 1: T1^T = Ex W^T and T2^T = Ex' W^T (rows = raster columns k, columns = window rows j)
+  if (t == 0) {
+    mma_split(tmem + TM_D1, base + S_EX_HI, base + S_EX_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(GK));
+    mma_split(tmem + TM_D2, base + S_EXD_HI, base + S_EXD_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(GK));
+    tc::mma_commit(&mbar);
+  }
+  bool ok = wait_mma(&mbar, 0, &done_s);
+  int committed = 1;  // phases committed to the barrier (thread 0's view is the one used)
+
+  if (ok) {
+    // T1^T and T2^T back from tensor memory (row t = raster column k0 + t), split
+    // and stored as the K-major B operands of stage 2 over the stage-1 A tiles
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll 1
+      for (int which = 0; which < 2; ++which) {
+        float v[32];
+        tc::tmem_ld32(lane_base + (which ? TM_D2 : TM_D1) + (uint32_t)(half * 32), v);
+        uint8_t* thi = sm + (which ? S_T2_HI : S_T1_HI);
+        uint8_t* tlo = sm + (which ? S_T2_LO : S_T1_LO);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t hv[4], lv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
+          st_chunk(thi, t, half * 4 + c, hv);
+          st_chunk(tlo, t, half * 4 + c, lv);
+        }
+      }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    // stage 2: H = Ey T1, Gx = Ey T2, Gy = Ey' T1 (rows = raster rows l, columns = raster columns k)
+    if (t == 0) {
+      mma_split(tmem + TM_H, base + S_EY_HI, base + S_EY_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT));
+      mma_split(tmem + TM_GX, base + S_EY_HI, base + S_EY_LO, base + S_T2_HI, base + S_T2_LO, idesc_bf16(GT));
+      mma_split(tmem + TM_GY, base + S_EYD_HI, base + S_EYD_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT));
+      tc::mma_commit(&mbar);
+    }
+    committed = 2;
+    ok = wait_mma(&mbar, 1, &done_s);
+  }
+
+  // epilogue: thread t writes raster row l0 + t.  The tensor-memory loads are
+  // warp-wide (.sync.aligned): every lane issues them, only the stores are
+  // limited to the raster.
+  {
+    const int64_t l = l0 + t;
+    const bool lin = l < P.nqy;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    float* hrow = hout + (lin ? l : 0) * P.nqx;
+    float* grow = gout ? gout + 2 * (lin ? l : 0) * P.nqx : nullptr;
+#pragma unroll 1
+    for (int cb = 0; cb < GT / 32; ++cb) {
+      const int64_t kb = k0 + cb * 32;
+      if (kb >= P.nqx) break;  // uniform over the CTA
+      float vh[32], vx[32], vy[32];
+      if (ok) {
+        tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
+        if (grow) {
+          tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
+          tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
+      }
+      if (!lin) continue;
+      const int ncol = (P.nqx - kb) < 32 ? (int)(P.nqx - kb) : 32;
+      if (vec && ncol == 32) {
+#pragma unroll
+        for (int e = 0; e < 32; e += 4)
+          *reinterpret_cast<float4*>(hrow + kb + e) = make_float4(vh[e], vh[e + 1], vh[e + 2], vh[e + 3]);
+        if (grow) {
+#pragma unroll
+          for (int e = 0; e < 32; e += 2)
+            *reinterpret_cast<float4*>(grow + 2 * (kb + e)) = make_float4(vx[e], vy[e], vx[e + 1], vy[e + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {  // static indices keep v* in registers
+          if (e < ncol) {
+            hrow[kb + e] = vh[e];
+            if (grow) {
+              grow[2 * (kb + e)] = vx[e];
+              grow[2 * (kb + e) + 1] = vy[e];
+            }
+          }
+        }
+      }
+    }
+  }
+  if (!ok && t == 0) {
+    // give the MMAs of the last committed phase one more bounded chance to
+    // drain before tensor memory is freed (a commit arrives once every earlier
+    // MMA of the thread has completed)
+    long long it = 0;
+    while (!tc::mbar_try_wait(&mbar, (uint32_t)(committed - 1)) && ++it < tc::WAIT_LIMIT) {
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TM_COLS);
+}
+
+}  // namespace
+
+}  // namespace rbf
+
+using namespace rbf;
+
+extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double dq, int64_t nqx, int64_t nqy,
+                                    float* h, float* grad, void* stream) {
+  RBF_TRY(check_ctx(cx, true));
+  if (nqx < 0 || nqy < 0) return fail(RBF_EINVAL, "negative raster size");
+  if (!std::isfinite(qx0) || !std::isfinite(qy0) || !std::isfinite(dq) || !(dq > 0.0))
+    return fail(RBF_EINVAL, "raster origin and spacing must be finite, spacing > 0");
+  if (nqx == 0 || nqy == 0) return RBF_OK;
+  if (!h) return fail(RBF_EINVAL, "null h");
+  Ctx* c = C(cx);
+  if (c->cfg.kernel != RBF_KERNEL_GAUSSIAN)
+    return fail(RBF_EINVAL, "the raster evaluation needs the Gaussian kernel (it factorises per axis)");
+  if (!c->lat.on) return fail(RBF_EINVAL, "the raster evaluation needs the centers on a square lattice");
+  const double r = eval_radius(c->cfg);
+  // one tile spans 127 dq + 2 r; with the slack of the window origin it must
+  // fit in 64 lattice nodes
+  if (127.0 * dq + 2.0 * r > 60.5 * c->lat.h)
+    return fail(RBF_ERANGE, "raster spacing %g too coarse for 64-node windows (at most %g); use rbf_eval", dq,
+                (60.5 * c->lat.h - 2.0 * r) / 127.0);
+  const int64_t tx = (nqx + GT - 1) / GT, ty = (nqy + GT - 1) / GT;
+  if (tx > 0x7fffffffLL || ty > 65535) return fail(RBF_ERANGE, "raster too large for one launch");
+  if (!std::isfinite(qx0 + (double)(nqx - 1) * dq) || !std::isfinite(qy0 + (double)(nqy - 1) * dq))
+    return fail(RBF_EINVAL, "raster coordinates overflow");
+  GridParams P;
+  P.qx0 = qx0;
+  P.qy0 = qy0;
+  P.dq = dq;
+  P.nqx = nqx;
+  P.nqy = nqy;
+  P.lx0 = c->lat.x0;
+  P.ly0 = c->lat.y0;
+  P.lh = c->lat.h;
+  P.r = r;
+  P.nx = c->lat.nx;
+  P.ny = c->lat.ny;
+  const float r32 = (float)r;
+  P.r2 = r32 * r32;
+  P.inv2s2 = (float)(1.0 / (2.0 * c->cfg.sigma * c->cfg.sigma));
+  P.inv_s2 = (float)(1.0 / (c->cfg.sigma * c->cfg.sigma));
+  const int vec = (nqx % 4 == 0) && ((uintptr_t)h % 16 == 0) && (!grad || (uintptr_t)grad % 16 == 0);
+  cudaStream_t s = (cudaStream_t)stream;
+  static bool attr_set[64] = {false};
+  if (!attr_set[c->device & 63]) {
+    RBF_CUDA(cudaFuncSetAttribute(k_eval_grid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GRID_SMEM));
+    attr_set[c->device & 63] = true;
+  }
+  StageTimer st(c, RBF_STAGE_EVAL_GRID, s, (grad ? 12.0 : 4.0) * (double)nqx * (double)nqy);
+  { k_eval_grid_tc<<<dim3((unsigned)tx, (unsigned)ty), GT, GRID_SMEM, s>>>(
+        P, c->lat_xs.as<float>(), c->lat_ys.as<float>(), c->wlat.as<float>(), h, grad, vec); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}

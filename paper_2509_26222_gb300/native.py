@@ -93,6 +93,7 @@ _SIGS = {
     "rbf_set_weights": [_P, _P, _P],
     "rbf_update": [_P, _P, _I64, _D, _P],
     "rbf_eval": [_P, _P, _I64, _P, _P, _P],
+    "rbf_eval_grid": [_P, _D, _D, _D, _I64, _I64, _P, _P, _P],
     "rbf_soft_cost": [_P, _P, _P, _P, _I64, _P, _P, _P, _P],
     "rbf_soft_cost_backward": [_P, _P, _P, _P, _I64, _P, _P, _P, _P, _P],
     "rbf_get_cov": [_P, _P, _I64, _P, _P],
@@ -106,7 +107,7 @@ _SIGS = {
 }
 
 STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward",
-          "trsm32", "inverse", "invapply", "covblock", "schur", "enter"]
+          "trsm32", "inverse", "invapply", "covblock", "schur", "enter", "evalgrid"]
 
 
 def _so3_exp(v):
@@ -267,6 +268,18 @@ class Terrain:
         if with_grad:
             g = out_grad if out_grad is not None else torch.empty(Q, 2, dtype=torch.float32, device=q.device)
         _check(self.lib.rbf_eval(self._h, _ptr(q), Q, _ptr(h), _ptr(g), _stream()))
+        return h, g
+
+    def eval_grid(self, qx0, qy0, dq, nqx, nqy, out_h=None, out_grad=None, with_grad=True):
+        """h (nqy x nqx) and grad h (nqy x nqx x 2) on the raster (qx0 + k dq, qy0 + l dq):
+        Gaussian kernel, centers on a lattice, per-axis truncation (rbf_eval_grid)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        h = out_h if out_h is not None else torch.empty(nqy, nqx, dtype=torch.float32, device=dev)
+        g = None
+        if with_grad:
+            g = out_grad if out_grad is not None else torch.empty(nqy, nqx, 2, dtype=torch.float32, device=dev)
+        _check(self.lib.rbf_eval_grid(self._h, float(qx0), float(qy0), float(dq), int(nqx), int(nqy), _ptr(h),
+                                      _ptr(g), _stream()))
         return h, g
 
     def soft_cost(self, R, t, pts, with_resid=False, out=None):

@@ -303,3 +303,19 @@ def config5(seed: int = 0, n: int = 32_768, q: int = 1_048_576, rho: float = 0.3
     block = (i0, i1, j0, j1)
     return dict(centers=centers, points=pts, queries=qs, block=block,
                 kernel=KernelSpec(kind=0, rho=rho), noise=0.02)
+
+
+# ----------------------------------------------------------------------------
+# Raster evaluation of the paper's Gaussian terrain
+# ----------------------------------------------------------------------------
+def raster_gaussian(n_lat: int = 366, h: float = 0.07, sigma: float = 0.04, dq: float = 0.005,
+                    n_q: int = 5120):
+    """The paper's Gaussian parameters (sigma = 0.04 m on a 0.07 m mesh,
+    Sec. VI-B) on an n_lat x n_lat lattice (25.6 m square by default), with
+    the weights of the quasi-interpolant of the staircase surface,
+    w_ij = f(c_ij) h^2 / (2 pi sigma^2) (a smooth stand-in for fitted
+    weights), and an n_q x n_q raster at dq over the same square (5 mm and
+    26.2 M points by default)."""
+    centers = grid_centers(n_lat, n_lat, 0.0, 0.0, h)
+    w = surface_c2(centers[:, 0] - 6.0, centers[:, 1]) * (h * h / (2.0 * np.pi * sigma * sigma))
+    return dict(centers=centers, w=w, sigma=sigma, cutoff_mult=4.0, qx0=0.0, qy0=0.0, dq=dq, nqx=n_q, nqy=n_q)
