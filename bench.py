@@ -55,6 +55,30 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# tensor-core work of one 128 x 128 raster tile of rbf_eval_grid: stage 1, two
+# accumulators of 128 x 64 over K = 64; stage 2, three of 128 x 128 over K = 64;
+# three split bfloat16 products each
+RASTER_TILE_FLOPS = 3 * (2 * 128 * 64 * 64 * 2 + 3 * 128 * 128 * 64 * 2)
+
+
+def raster_line(r, pk, pk_kind):
+    """JSON object of the raster leg: points/s, the HBM roofline of its output
+    (12 bytes per point: h and grad h) and the tensor-core rate."""
+    if r is None:
+        return None
+    sec = r["ms"] * 1e-3
+    gbs = 12.0 * r["points"] / sec / 1e9
+    tf = RASTER_TILE_FLOPS * r["tiles"] / sec / 1e12
+    return {"workload": r["workload"], "points": r["points"], "ms": r["ms"], "points_per_s": r["points"] / sec,
+            "roofline": {"kernel": "k_eval_grid_tc", "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": None, "bytes_per_point": 12,
+                         "peak_kind": pk_kind},
+            "tensor": {"achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tf / pk["bf16_tflops"],
+                       "flops_per_tile": RASTER_TILE_FLOPS, "peak_kind": "bf16 burst (" + pk_kind + ")"},
+            "scattered_eval_same_points_ms": r["scattered_eval_same_points_ms"],
+            "speedup_over_scattered_eval": r["scattered_eval_same_points_ms"] / r["ms"]}
+
+
 def max_over_ranks(value: float, device) -> float:
     """Maximum of a per-rank value over the process group (identity when no
     group is initialized); device None means a CPU (gloo) tensor."""
@@ -366,6 +390,51 @@ def run_ours(args, ws, rank, local):
     eval_ms = float(np.median(ev))
     T.close()
 
+    # ----- Gaussian terrain on a regular raster (rbf_eval_grid, tensor cores) -----
+    raster = None
+    if args.raster_reps > 0:
+        rc = W.raster_gaussian()
+        TR = N.Terrain(kernel=N.KERNEL_GAUSSIAN, sigma=rc["sigma"], cutoff_mult=rc["cutoff_mult"])
+        TR.set_centers(torch.tensor(rc["centers"], device=dev))
+        TR.set_weights(torch.tensor(rc["w"], device=dev))
+        nqx, nqy = rc["nqx"], rc["nqy"]
+        hr = torch.empty(nqy, nqx, device=dev)
+        gr = torch.empty(nqy, nqx, 2, device=dev)
+        ra = (rc["qx0"], rc["qy0"], rc["dq"], nqx, nqy)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for r_ in range(args.raster_reps):
+                flush.fill_(float(r_))
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+
+        grid_ms = timed(lambda: TR.eval_grid(*ra, out_h=hr, out_grad=gr))
+        # the same raster points through the per-query evaluation (disc truncation), for comparison
+        xs = (rc["qx0"] + torch.arange(nqx, device=dev, dtype=torch.float64) * rc["dq"]).float()
+        ys = (rc["qy0"] + torch.arange(nqy, device=dev, dtype=torch.float64) * rc["dq"]).float()
+        qr = torch.stack([xs[None, :].expand(nqy, nqx), ys[:, None].expand(nqy, nqx)], -1).reshape(-1, 2).contiguous()
+        del xs, ys
+        scat_ms = timed(lambda: TR.eval(qr, out_h=hr.view(-1), out_grad=gr.view(-1, 2)))
+        del qr
+        npts = nqx * nqy
+        tiles = ((nqx + 127) // 128) * ((nqy + 127) // 128)
+        raster = dict(workload=(f"Gaussian sigma=0.04 m on a {int(round(math.sqrt(rc['centers'].shape[0])))}^2 lattice at "
+                                f"0.07 m (Sec. VI-B parameters), h + grad h on a {nqx} x {nqy} raster at "
+                                f"{rc['dq'] * 1000:.0f} mm"),
+                      points=npts, ms=grid_ms, tiles=tiles, scattered_eval_same_points_ms=scat_ms)
+        TR.close()
+
     # ----- batched patches (256 independent terrains, update + evaluation) -----
     batch = None
     if args.batch_patches > 0:
@@ -451,7 +520,7 @@ def run_ours(args, ws, rank, local):
                                                   max(np.max(np.abs(ws_["fp64"])), 1e-300))
         c5["speedup_mixed_over_fp64"] = c5["fp64"]["ms_per_update"] / c5["mixed"]["ms_per_update"]
     return dict(times=times, total_ms=total_ms, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, prof=prof,
-                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch,
+                launches=launches, clocks=clk, a_last=a_last, eval_ms=eval_ms, Q=Q, batch=batch, raster=raster,
                 other=other_line, exact=exact_line, c5=c5, fit=fit)
 
 
@@ -519,6 +588,7 @@ def main():
     ap.add_argument("--batch-patches", type=int, default=256, help="patches of the batched measurement (0: skip)")
     ap.add_argument("--no-other", action="store_true", help="skip the other update precision on the same frames")
     ap.add_argument("--c5-reps", type=int, default=3, help="timed updates at 65,536 centers per precision (0: skip)")
+    ap.add_argument("--raster-reps", type=int, default=5, help="timed raster evaluations (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -615,6 +685,7 @@ def main():
                               "traffic_source": "ncu dram__bytes_read+write of k_eval_lattice_win on 2^24 "
                                                 "queries, per query, scaled to Q",
                               "bytes_per_query": 20, "peak_kind": pk_kind}},
+        "eval_grid": raster_line(r["raster"], pk, pk_kind),
         "stage_ms_per_step": stage_ms,
         "other_precision_same_frames": r["other"],
         "exact_mode_same_frames": r["exact"],

@@ -149,7 +149,7 @@ rbf_status rbf_eval(rbf_ctx* ctx, const float* q, int64_t Q, float* h, float* gr
  * rbf_eval.  This keeps every term rbf_eval keeps plus the corners of the
  * square, each below exp(-cutoff_mult^2 / 2) |w_j|.
  * h: nqy x nqx float32, row l = raster row (device); grad: nqy x nqx x 2
- * float32 (d/dx, d/dy), may be NULL (device).  The coordinates are rounded to
+ * float32 (d/dx, d/dy), 8-byte aligned, may be NULL (device).  The coordinates are rounded to
  * float32 after qx0 + k dq is formed in float64.
  * RBF_EINVAL: not the Gaussian kernel, centers not on a lattice, dq <= 0 or
  * non-finite arguments.  RBF_ERANGE: 127 dq + 2 r exceeds 60.5 lattice

@@ -113,11 +113,11 @@ __device__ __forceinline__ int window_origin(double q, double r, double l0, doub
   return i < 0 ? 0 : i;
 }
 
-// Rows of g and g' for one raster coordinate q over the window nodes
-// o .. o + 63 (nodes >= n, and raster points outside the raster, give zeros).
+// Rows of g and g' for one raster coordinate q over the window nodes in
+// shared memory (nodes past the lattice hold NaN, which fails the test;
+// raster points outside the raster give zeros).
 __device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int s_dhi, int s_dlo, int row,
-                                          bool in, float q, const float* __restrict__ nodes, int o, int n,
-                                          const GridParams& P) {
+                                          bool in, float q, const float* nodes, const GridParams& P) {
 #pragma unroll 1
   for (int c = 0; c < GK / 8; ++c) {
     uint32_t hv[4], lv[4], dhv[4], dlv[4];
@@ -126,16 +126,13 @@ __device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int
       float g[2], gd[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int i = o + c * 8 + 2 * e + u;
+        const float d = __fsub_rn(q, nodes[c * 8 + 2 * e + u]);
+        const float d2 = __fmul_rn(d, d);
         g[u] = 0.f;
         gd[u] = 0.f;
-        if (in && i < n) {
-          const float d = __fsub_rn(q, nodes[i]);
-          const float d2 = __fmul_rn(d, d);
-          if (d2 < P.r2) {
-            g[u] = __expf(-d2 * P.inv2s2);
-            gd[u] = -(d * P.inv_s2) * g[u];
-          }
+        if (in && d2 < P.r2) {
+          g[u] = __expf(-d2 * P.inv2s2);
+          gd[u] = -(d * P.inv_s2) * g[u];
         }
       }
       split2(g[0], g[1], hv[e], lv[e]);
@@ -163,45 +160,60 @@ __device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t ph, int* done_
   return *done_s != 0;
 }
 
-__global__ void __launch_bounds__(GT) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
-                                                     const float* __restrict__ ys, const float* __restrict__ W,
-                                                     float* __restrict__ hout, float* __restrict__ gout, int vec) {
+constexpr int GTHREADS = 256;  // 8 warps: two per tensor-memory lane quadrant
+constexpr int TP = 33;         // padded row of the per-warp transpose buffers
+
+__global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
+                                                           const float* __restrict__ ys,
+                                                           const float* __restrict__ W, float* __restrict__ hout,
+                                                           float* __restrict__ gout) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int done_s;
+  __shared__ int org[2];
+  __shared__ float sx[GK], sy[GK];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int quad = warp & 3;  // tensor-memory lanes 32 quad .. 32 quad + 31
   const int64_t k0 = (int64_t)blockIdx.x * GT, l0 = (int64_t)blockIdx.y * GT;
-  const int io = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.lh, P.nx);
-  const int jo = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.lh, P.ny);
-
-  // operands: row t of Ex, Ex' (raster column k0 + t) and of Ey, Ey' (raster row l0 + t)
+  if (t == 0) {
+    org[0] = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.lh, P.nx);
+    org[1] = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.lh, P.ny);
+  }
+  __syncthreads();
+  const int io = org[0], jo = org[1];
+  if (t < GK) sx[t] = (io + t < P.nx) ? xs[io + t] : __int_as_float(0x7fc00000);
+  else if (t < 2 * GK) sy[t - GK] = (jo + t - GK < P.ny) ? ys[jo + t - GK] : __int_as_float(0x7fc00000);
   {
-    const int64_t k = k0 + t, l = l0 + t;
-    const bool kin = k < P.nqx, lin = l < P.nqy;
-    const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
-    const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
-    axis_rows(sm, S_EX_HI, S_EX_LO, S_EXD_HI, S_EXD_LO, t, kin, qx, xs, io, P.nx, P);
-    axis_rows(sm, S_EY_HI, S_EY_LO, S_EYD_HI, S_EYD_LO, t, lin, qy, ys, jo, P.ny, P);
-    // window weights: row j = t / 2 (N of stage 1), nodes i (K), half a row per thread
-    const int j = t >> 1, jg = jo + j;
-#pragma unroll 1
-    for (int c = (t & 1) * 4; c < (t & 1) * 4 + 4; ++c) {
+    // window weights: row j = t / 4 (N of stage 1), 16 nodes i (K) per thread
+    const int j = t >> 2, jg = jo + j, c0 = (t & 3) * 2;
+    float v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int ig = io + c0 * 8 + e;
+      v[e] = (jg < P.ny && ig < P.nx) ? W[(int64_t)jg * P.nx + ig] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
       uint32_t hv[4], lv[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float v[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int ig = io + c * 8 + 2 * e + u;
-          v[u] = (jg < P.ny && ig < P.nx) ? W[(int64_t)jg * P.nx + ig] : 0.f;
-        }
-        split2(v[0], v[1], hv[e], lv[e]);
-      }
-      st_chunk(sm + S_W_HI, j, c, hv);
-      st_chunk(sm + S_W_LO, j, c, lv);
+      for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
+      st_chunk(sm + S_W_HI, j, c0 + c, hv);
+      st_chunk(sm + S_W_LO, j, c0 + c, lv);
     }
+  }
+  __syncthreads();
+  // operands: threads 0-127 row t of Ex, Ex' (raster column k0 + t); threads
+  // 128-255 row t - 128 of Ey, Ey' (raster row l0 + t - 128)
+  if (t < GT) {
+    const int64_t k = k0 + t;
+    const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
+    axis_rows(sm, S_EX_HI, S_EX_LO, S_EXD_HI, S_EXD_LO, t, k < P.nqx, qx, sx, P);
+  } else {
+    const int64_t l = l0 + (t - GT);
+    const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
+    axis_rows(sm, S_EY_HI, S_EY_LO, S_EYD_HI, S_EYD_LO, t - GT, l < P.nqy, qy, sy, P);
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, TM_COLS);
   if (t == 0) tc::mbar_init(&mbar, 1);
@@ -211,6 +223,8 @@ __global__ void __launch_bounds__(GT) k_eval_grid_tc(GridParams P, const float* 
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t base = tc::smem_u32(sm);
+  const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+  const int row = quad * 32 + lane;  // the tile row this thread reads from tensor memory
 
   // stage 1: T1^T = Ex W^T and T2^T = Ex' W^T (rows = raster columns k, columns = window rows j)
   if (t == 0) {
@@ -222,25 +236,22 @@ __global__ void __launch_bounds__(GT) k_eval_grid_tc(GridParams P, const float* 
   int committed = 1;  // phases committed to the barrier (thread 0's view is the one used)
 
   if (ok) {
-    // T1^T and T2^T back from tensor memory (row t = raster column k0 + t), split
-    // and stored as the K-major B operands of stage 2 over the stage-1 A tiles
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // T1^T (warps 0-3) and T2^T (warps 4-7) back from tensor memory, split and
+    // stored as the K-major B operands of stage 2 over the stage-1 A tiles
+    const int which = warp >> 2;
+    uint8_t* thi = sm + (which ? S_T2_HI : S_T1_HI);
+    uint8_t* tlo = sm + (which ? S_T2_LO : S_T1_LO);
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
-#pragma unroll 1
-      for (int which = 0; which < 2; ++which) {
-        float v[32];
-        tc::tmem_ld32(lane_base + (which ? TM_D2 : TM_D1) + (uint32_t)(half * 32), v);
-        uint8_t* thi = sm + (which ? S_T2_HI : S_T1_HI);
-        uint8_t* tlo = sm + (which ? S_T2_LO : S_T1_LO);
+      float v[32];
+      tc::tmem_ld32(lane_base + (which ? TM_D2 : TM_D1) + (uint32_t)(half * 32), v);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t hv[4], lv[4];
+      for (int c = 0; c < 4; ++c) {
+        uint32_t hv[4], lv[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
-          st_chunk(thi, t, half * 4 + c, hv);
-          st_chunk(tlo, t, half * 4 + c, lv);
-        }
+        for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
+        st_chunk(thi, row, half * 4 + c, hv);
+        st_chunk(tlo, row, half * 4 + c, lv);
       }
     }
     tc::fence_proxy_async();
@@ -258,23 +269,26 @@ __global__ void __launch_bounds__(GT) k_eval_grid_tc(GridParams P, const float* 
     ok = wait_mma(&mbar, 1, &done_s);
   }
 
-  // epilogue: thread t writes raster row l0 + t.  The tensor-memory loads are
-  // warp-wide (.sync.aligned): every lane issues them, only the stores are
-  // limited to the raster.
+  // epilogue: warp w takes tile rows 32 (w % 4) .. + 31 and columns
+  // 64 (w / 4) .. + 63 in two blocks of 32.  The tensor-memory loads are
+  // warp-wide (.sync.aligned); each block goes through a padded per-warp
+  // buffer so that the global stores write whole rows: 128 contiguous bytes of
+  // h and 256 of grad h per warp instruction.  The operand tiles are free once
+  // the stage-2 MMAs have completed.
   {
-    const int64_t l = l0 + t;
-    const bool lin = l < P.nqy;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    float* hrow = hout + (lin ? l : 0) * P.nqx;
-    float* grow = gout ? gout + 2 * (lin ? l : 0) * P.nqx : nullptr;
+    float* th = reinterpret_cast<float*>(sm) + warp * (3 * 32 * TP);
+    float* tx = th + 32 * TP;
+    float* ty = tx + 32 * TP;
+    const bool want_g = gout != nullptr;
 #pragma unroll 1
-    for (int cb = 0; cb < GT / 32; ++cb) {
+    for (int b = 0; b < 2; ++b) {
+      const int cb = (warp >> 2) * 2 + b;
       const int64_t kb = k0 + cb * 32;
-      if (kb >= P.nqx) break;  // uniform over the CTA
+      if (kb >= P.nqx) break;  // uniform over the warp
       float vh[32], vx[32], vy[32];
       if (ok) {
         tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
-        if (grow) {
+        if (want_g) {
           tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
           tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
         }
@@ -282,29 +296,29 @@ __global__ void __launch_bounds__(GT) k_eval_grid_tc(GridParams P, const float* 
 #pragma unroll
         for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
       }
-      if (!lin) continue;
-      const int ncol = (P.nqx - kb) < 32 ? (int)(P.nqx - kb) : 32;
-      if (vec && ncol == 32) {
 #pragma unroll
-        for (int e = 0; e < 32; e += 4)
-          *reinterpret_cast<float4*>(hrow + kb + e) = make_float4(vh[e], vh[e + 1], vh[e + 2], vh[e + 3]);
-        if (grow) {
+      for (int e = 0; e < 32; ++e) th[lane * TP + e] = vh[e];
+      if (want_g) {
 #pragma unroll
-          for (int e = 0; e < 32; e += 2)
-            *reinterpret_cast<float4*>(grow + 2 * (kb + e)) = make_float4(vx[e], vy[e], vx[e + 1], vy[e + 1]);
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {  // static indices keep v* in registers
-          if (e < ncol) {
-            hrow[kb + e] = vh[e];
-            if (grow) {
-              grow[2 * (kb + e)] = vx[e];
-              grow[2 * (kb + e) + 1] = vy[e];
-            }
-          }
+        for (int e = 0; e < 32; ++e) {
+          tx[lane * TP + e] = vx[e];
+          ty[lane * TP + e] = vy[e];
         }
       }
+      __syncwarp();
+      const int64_t k = kb + lane;
+      const bool kin = k < P.nqx;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int64_t l = l0 + quad * 32 + r;
+        if (l >= P.nqy) break;  // uniform over the warp
+        if (kin) {
+          hout[l * P.nqx + k] = th[r * TP + lane];
+          if (want_g)
+            *reinterpret_cast<float2*>(gout + 2 * (l * P.nqx + k)) = make_float2(tx[r * TP + lane], ty[r * TP + lane]);
+        }
+      }
+      __syncwarp();
     }
   }
   if (!ok && t == 0) {
@@ -334,6 +348,8 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
     return fail(RBF_EINVAL, "raster origin and spacing must be finite, spacing > 0");
   if (nqx == 0 || nqy == 0) return RBF_OK;
   if (!h) return fail(RBF_EINVAL, "null h");
+  if ((uintptr_t)h % 4 != 0 || (grad && (uintptr_t)grad % 8 != 0))
+    return fail(RBF_EINVAL, "h must be 4-byte and grad 8-byte aligned");
   Ctx* c = C(cx);
   if (c->cfg.kernel != RBF_KERNEL_GAUSSIAN)
     return fail(RBF_EINVAL, "the raster evaluation needs the Gaussian kernel (it factorises per axis)");
@@ -364,7 +380,6 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
   P.r2 = r32 * r32;
   P.inv2s2 = (float)(1.0 / (2.0 * c->cfg.sigma * c->cfg.sigma));
   P.inv_s2 = (float)(1.0 / (c->cfg.sigma * c->cfg.sigma));
-  const int vec = (nqx % 4 == 0) && ((uintptr_t)h % 16 == 0) && (!grad || (uintptr_t)grad % 16 == 0);
   cudaStream_t s = (cudaStream_t)stream;
   static bool attr_set[64] = {false};
   if (!attr_set[c->device & 63]) {
@@ -372,8 +387,8 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
     attr_set[c->device & 63] = true;
   }
   StageTimer st(c, RBF_STAGE_EVAL_GRID, s, (grad ? 12.0 : 4.0) * (double)nqx * (double)nqy);
-  { k_eval_grid_tc<<<dim3((unsigned)tx, (unsigned)ty), GT, GRID_SMEM, s>>>(
-        P, c->lat_xs.as<float>(), c->lat_ys.as<float>(), c->wlat.as<float>(), h, grad, vec); ::rbf::note_launch(); }
+  { k_eval_grid_tc<<<dim3((unsigned)tx, (unsigned)ty), GTHREADS, GRID_SMEM, s>>>(
+        P, c->lat_xs.as<float>(), c->lat_ys.as<float>(), c->wlat.as<float>(), h, grad); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
