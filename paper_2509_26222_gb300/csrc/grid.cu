@@ -21,10 +21,12 @@
 // per matrix row, written by the CTA's threads with 16-byte shared stores.
 // Thread 0 issues the MMAs and commits them to an mbarrier; every wait is
 // bounded, and a tile whose wait gives up is written as NaN.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
 #include "tc_util.cuh"
@@ -98,6 +100,7 @@ struct GridParams {
   int64_t nqx, nqy;
   double lx0, ly0, lh;  // lattice node i at lx0 + (i + 1/2) lh
   double r;             // window radius (float64, for the window origins)
+  double inv_lh;        // 1 / lh
   int nx, ny;
   float r2;             // fl32(r)^2 rounded to float32 (membership rule)
   float inv2s2, inv_s2; // 1 / (2 s^2), 1 / s^2
@@ -105,8 +108,8 @@ struct GridParams {
 
 // First lattice node of the window of a tile whose first raster coordinate
 // is q (one node of slack below; the host checks that 64 nodes cover the tile).
-__device__ __forceinline__ int window_origin(double q, double r, double l0, double lh, int n) {
-  double t = (q - r - l0) / lh - 0.5;
+__device__ __forceinline__ int window_origin(double q, double r, double l0, double inv_lh, int n) {
+  double t = (q - r - l0) * inv_lh - 0.5;
   if (!(t > -2.0)) t = -2.0;
   if (t > (double)n) t = (double)n;
   int i = (int)floor(t) - 1;
@@ -160,13 +163,33 @@ __device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t ph, int* done_
   return *done_s != 0;
 }
 
+// Bulk tensor store of a 32 x 32 float32 box (128-byte swizzled in shared
+// memory) at element coordinates (x, y) of the map; the hardware clips what
+// lies outside the tensor.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(tc::smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void st16(uint8_t* box, int row, int chunk, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(box + tc::sw128_offset(row, chunk)) = make_float4(a, b, c, d);
+}
+
 constexpr int GTHREADS = 256;  // 8 warps: two per tensor-memory lane quadrant
+constexpr int BOX = 32 * 128;  // one 32 x 32 float32 box
 constexpr int TP = 33;         // padded row of the per-warp transpose buffers
 
 __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
                                                            const float* __restrict__ ys,
                                                            const float* __restrict__ W, float* __restrict__ hout,
-                                                           float* __restrict__ gout) {
+                                                           float* __restrict__ gout,
+                                                           const __grid_constant__ CUtensorMap map_h,
+                                                           const __grid_constant__ CUtensorMap map_g, int use_tma) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -178,8 +201,8 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
   const int quad = warp & 3;  // tensor-memory lanes 32 quad .. 32 quad + 31
   const int64_t k0 = (int64_t)blockIdx.x * GT, l0 = (int64_t)blockIdx.y * GT;
   if (t == 0) {
-    org[0] = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.lh, P.nx);
-    org[1] = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.lh, P.ny);
+    org[0] = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.inv_lh, P.nx);
+    org[1] = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.inv_lh, P.ny);
   }
   __syncthreads();
   const int io = org[0], jo = org[1];
@@ -275,7 +298,55 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
   // buffer so that the global stores write whole rows: 128 contiguous bytes of
   // h and 256 of grad h per warp instruction.  The operand tiles are free once
   // the stage-2 MMAs have completed.
-  {
+  if (use_tma) {
+    // rows of the warp's 32 x 32 blocks into 128-byte swizzled boxes (row
+    // `lane` of the box is this thread's tensor-memory row), then bulk tensor
+    // stores by one lane: h, and grad h as two boxes of 16 (d/dx, d/dy) pairs
+    uint8_t* bh = sm + warp * (3 * BOX);
+    uint8_t* bg0 = bh + BOX;
+    uint8_t* bg1 = bg0 + BOX;
+    const bool want_g = gout != nullptr;
+    const int64_t y0 = l0 + quad * 32;
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+      const int cb = (warp >> 2) * 2 + b;
+      const int64_t kb = k0 + cb * 32;
+      if (kb >= P.nqx) break;  // uniform over the warp
+      float vh[32], vx[32], vy[32];
+      if (ok) {
+        tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
+        if (want_g) {
+          tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
+          tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
+      }
+      if (b > 0 && lane == 0) bulk_wait_read();  // the previous block's boxes have been read
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < 8; ++c) st16(bh, lane, c, vh[4 * c], vh[4 * c + 1], vh[4 * c + 2], vh[4 * c + 3]);
+      if (want_g) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          st16(bg0, lane, c, vx[2 * c], vy[2 * c], vx[2 * c + 1], vy[2 * c + 1]);
+          st16(bg1, lane, c, vx[16 + 2 * c], vy[16 + 2 * c], vx[17 + 2 * c], vy[17 + 2 * c]);
+        }
+      }
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0 && y0 < P.nqy) {
+        tma_store_2d(&map_h, bh, (int)kb, (int)y0);
+        if (want_g) {
+          tma_store_2d(&map_g, bg0, (int)(2 * kb), (int)y0);
+          if (kb + 16 < P.nqx) tma_store_2d(&map_g, bg1, (int)(2 * kb + 32), (int)y0);  // starts inside the tensor
+        }
+        bulk_commit();
+      }
+    }
+    if (lane == 0) bulk_wait();  // the stores have completed before the CTA ends
+  } else {
     float* th = reinterpret_cast<float*>(sm) + warp * (3 * 32 * TP);
     float* tx = th + 32 * TP;
     float* ty = tx + 32 * TP;
@@ -340,6 +411,27 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
 
 using namespace rbf;
 
+namespace {
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda)
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+}  // namespace
+
 extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double dq, int64_t nqx, int64_t nqy,
                                     float* h, float* grad, void* stream) {
   RBF_TRY(check_ctx(cx, true));
@@ -374,6 +466,7 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
   P.ly0 = c->lat.y0;
   P.lh = c->lat.h;
   P.r = r;
+  P.inv_lh = 1.0 / c->lat.h;
   P.nx = c->lat.nx;
   P.ny = c->lat.ny;
   const float r32 = (float)r;
@@ -386,9 +479,31 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
     RBF_CUDA(cudaFuncSetAttribute(k_eval_grid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GRID_SMEM));
     attr_set[c->device & 63] = true;
   }
+  // bulk tensor stores need 16-byte aligned outputs and row pitches; other
+  // rasters take the transposing stores
+  CUtensorMap map_h, map_g;
+  memset(&map_h, 0, sizeof(map_h));
+  memset(&map_g, 0, sizeof(map_g));
+  int use_tma = (nqx % 4 == 0) && ((uintptr_t)h % 16 == 0) && (!grad || (uintptr_t)grad % 16 == 0);
+  if (use_tma) {
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return fail(RBF_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint32_t box[2] = {32, 32}, estr[2] = {1, 1};
+    const cuuint64_t dh[2] = {(cuuint64_t)nqx, (cuuint64_t)nqy}, sh[1] = {(cuuint64_t)nqx * 4};
+    CUresult e = enc(&map_h, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h, dh, sh, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (e != CUDA_SUCCESS) return fail(RBF_ECUDA, "tensor map of h: error %d", (int)e);
+    if (grad) {
+      const cuuint64_t dg[2] = {(cuuint64_t)(2 * nqx), (cuuint64_t)nqy}, sg[1] = {(cuuint64_t)nqx * 8};
+      e = enc(&map_g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, grad, dg, sg, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (e != CUDA_SUCCESS) return fail(RBF_ECUDA, "tensor map of grad: error %d", (int)e);
+    }
+  }
   StageTimer st(c, RBF_STAGE_EVAL_GRID, s, (grad ? 12.0 : 4.0) * (double)nqx * (double)nqy);
   { k_eval_grid_tc<<<dim3((unsigned)tx, (unsigned)ty), GTHREADS, GRID_SMEM, s>>>(
-        P, c->lat_xs.as<float>(), c->lat_ys.as<float>(), c->wlat.as<float>(), h, grad); ::rbf::note_launch(); }
+        P, c->lat_xs.as<float>(), c->lat_ys.as<float>(), c->wlat.as<float>(), h, grad, map_h, map_g, use_tma);
+    ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
