@@ -6,11 +6,11 @@
 // |dy| < r, r = cutoff_mult * s).  On a tile of 128 x 128 raster points
 // (x_k, y_l) the terrain and its gradient (Eq. RBF_fml, Eq. manidolf_grad_detail
 // with the sign of reading G5) are then products of small matrices over a
-// window of 64 x 64 lattice nodes:
+// window of kw x kw lattice nodes (kw = 32, or 64 for coarse rasters):
 //     T1 = W Ex^T,   T2 = W Ex'^T                       (stage 1)
 //     H = Ey T1,     Gx = Ey T2,     Gy = Ey' T1        (stage 2)
 // with Ex[k][i] = g(x_k - x_i), Ex'[k][i] = -(x_k - x_i) / s^2 g(x_k - x_i), and
-// Ey, Ey' likewise.  Both stages run as tcgen05 MMAs (M = 128, K = 64) with
+// Ey, Ey' likewise.  Both stages run as tcgen05 MMAs (M = 128, K = kw) with
 // every float32 operand split into two bfloat16 parts, a = a_hi + a_lo, and the
 // three products a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in float32 in
 // tensor memory (relative error about 2^-16 per term).  The stage-1 results
@@ -35,7 +35,7 @@ namespace rbf {
 namespace {
 
 constexpr int GT = 128;                 // raster points per tile side (M and N of stage 2)
-constexpr int GK = 64;                  // lattice nodes per window side (K of both stages, N of stage 1)
+constexpr int GK = 64;                  // largest window: lattice nodes per side (K of both stages, N of stage 1)
 constexpr int OP_ROWS128 = GT * GK * 2; // 16 KiB: 128 rows x 64 bfloat16
 constexpr int OP_ROWS64 = GK * GK * 2;  // 8 KiB: 64 rows x 64 bfloat16
 // shared-memory map (offsets from the 1024-byte aligned base)
@@ -64,18 +64,18 @@ __device__ __forceinline__ void mma_bf16_n(uint32_t tmem_d, uint64_t adesc, uint
       "l"(adesc), "l"(bdesc), "r"(accum), "r"(idesc));
 }
 
-// D (+)= A B^T over K = 64 as the three split products, A and B given as
+// D = A B^T over K = 16 nk as the three split products, A and B given as
 // (hi, lo) shared-memory tiles.
 __device__ __forceinline__ void mma_split(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                          uint32_t b_lo, uint32_t idesc) {
+                                          uint32_t b_lo, uint32_t idesc, int nk) {
   const uint32_t as[3] = {a_hi, a_hi, a_lo};
   const uint32_t bs[3] = {b_hi, b_lo, b_hi};
   uint32_t accum = 0;
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const uint64_t ad = tc::sdesc_sw128(as[p]), bd = tc::sdesc_sw128(bs[p]);
-#pragma unroll
-    for (int kk = 0; kk < GK / 16; ++kk) {
+#pragma unroll 1
+    for (int kk = 0; kk < nk; ++kk) {
       mma_bf16_n(tmem_d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), accum, idesc);
       accum = 1;
     }
@@ -104,6 +104,7 @@ struct GridParams {
   int nx, ny;
   float r2;             // fl32(r)^2 rounded to float32 (membership rule)
   float inv2s2, inv_s2; // 1 / (2 s^2), 1 / s^2
+  int kw;               // window width in nodes: 32 or 64 (K of both stages, N of stage 1)
 };
 
 // First lattice node of the window of a tile whose first raster coordinate
@@ -116,13 +117,13 @@ __device__ __forceinline__ int window_origin(double q, double r, double l0, doub
   return i < 0 ? 0 : i;
 }
 
-// Rows of g and g' for one raster coordinate q over the window nodes in
+// Rows of g and g' for one raster coordinate q over the kw window nodes in
 // shared memory (nodes past the lattice hold NaN, which fails the test;
 // raster points outside the raster give zeros).
 __device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int s_dhi, int s_dlo, int row,
                                           bool in, float q, const float* nodes, const GridParams& P) {
 #pragma unroll 1
-  for (int c = 0; c < GK / 8; ++c) {
+  for (int c = 0; c < P.kw / 8; ++c) {
     uint32_t hv[4], lv[4], dhv[4], dlv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -184,12 +185,17 @@ constexpr int GTHREADS = 256;  // 8 warps: two per tensor-memory lane quadrant
 constexpr int BOX = 32 * 128;  // one 32 x 32 float32 box
 constexpr int TP = 33;         // padded row of the per-warp transpose buffers
 
+// Persistent: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// (tile = ty * ntx + tx).  The bulk stores of a tile drain while the next
+// tile's operands are generated; only their reads of shared memory are waited
+// for before the operands overwrite the boxes.
 __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
                                                            const float* __restrict__ ys,
                                                            const float* __restrict__ W, float* __restrict__ hout,
                                                            float* __restrict__ gout,
                                                            const __grid_constant__ CUtensorMap map_h,
-                                                           const __grid_constant__ CUtensorMap map_g, int use_tma) {
+                                                           const __grid_constant__ CUtensorMap map_g, int use_tma,
+                                                           int64_t ntx, int64_t ntiles) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -199,45 +205,6 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int quad = warp & 3;  // tensor-memory lanes 32 quad .. 32 quad + 31
-  const int64_t k0 = (int64_t)blockIdx.x * GT, l0 = (int64_t)blockIdx.y * GT;
-  if (t == 0) {
-    org[0] = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.inv_lh, P.nx);
-    org[1] = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.inv_lh, P.ny);
-  }
-  __syncthreads();
-  const int io = org[0], jo = org[1];
-  if (t < GK) sx[t] = (io + t < P.nx) ? xs[io + t] : __int_as_float(0x7fc00000);
-  else if (t < 2 * GK) sy[t - GK] = (jo + t - GK < P.ny) ? ys[jo + t - GK] : __int_as_float(0x7fc00000);
-  {
-    // window weights: row j = t / 4 (N of stage 1), 16 nodes i (K) per thread
-    const int j = t >> 2, jg = jo + j, c0 = (t & 3) * 2;
-    float v[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int ig = io + c0 * 8 + e;
-      v[e] = (jg < P.ny && ig < P.nx) ? W[(int64_t)jg * P.nx + ig] : 0.f;
-    }
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      uint32_t hv[4], lv[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
-      st_chunk(sm + S_W_HI, j, c0 + c, hv);
-      st_chunk(sm + S_W_LO, j, c0 + c, lv);
-    }
-  }
-  __syncthreads();
-  // operands: threads 0-127 row t of Ex, Ex' (raster column k0 + t); threads
-  // 128-255 row t - 128 of Ey, Ey' (raster row l0 + t - 128)
-  if (t < GT) {
-    const int64_t k = k0 + t;
-    const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
-    axis_rows(sm, S_EX_HI, S_EX_LO, S_EXD_HI, S_EXD_LO, t, k < P.nqx, qx, sx, P);
-  } else {
-    const int64_t l = l0 + (t - GT);
-    const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
-    axis_rows(sm, S_EY_HI, S_EY_LO, S_EYD_HI, S_EYD_LO, t - GT, l < P.nqy, qy, sy, P);
-  }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, TM_COLS);
   if (t == 0) tc::mbar_init(&mbar, 1);
   tc::fence_proxy_async();
@@ -248,156 +215,219 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
   const uint32_t base = tc::smem_u32(sm);
   const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
   const int row = quad * 32 + lane;  // the tile row this thread reads from tensor memory
+  const bool want_g = gout != nullptr;
+  bool healthy = true;     // false once a wait has given up: no further MMAs are issued
+  uint32_t phase = 0;      // parity of the barrier phase the next commit completes
+  uint32_t last = 0;       // parity of the last committed phase
+  bool any = false;        // something was committed
 
-  // stage 1: T1^T = Ex W^T and T2^T = Ex' W^T (rows = raster columns k, columns = window rows j)
-  if (t == 0) {
-    mma_split(tmem + TM_D1, base + S_EX_HI, base + S_EX_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(GK));
-    mma_split(tmem + TM_D2, base + S_EXD_HI, base + S_EXD_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(GK));
-    tc::mma_commit(&mbar);
-  }
-  bool ok = wait_mma(&mbar, 0, &done_s);
-  int committed = 1;  // phases committed to the barrier (thread 0's view is the one used)
-
-  if (ok) {
-    // T1^T (warps 0-3) and T2^T (warps 4-7) back from tensor memory, split and
-    // stored as the K-major B operands of stage 2 over the stage-1 A tiles
-    const int which = warp >> 2;
-    uint8_t* thi = sm + (which ? S_T2_HI : S_T1_HI);
-    uint8_t* tlo = sm + (which ? S_T2_LO : S_T1_LO);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t k0 = (tile % ntx) * GT, l0 = (tile / ntx) * GT;
+    if (use_tma && lane == 0) bulk_wait_read();  // the previous tile's boxes have been read
+    if (t == 0) {
+      org[0] = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.inv_lh, P.nx);
+      org[1] = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.inv_lh, P.ny);
+    }
+    __syncthreads();
+    const int io = org[0], jo = org[1];
+    if (t < GK) sx[t] = (io + t < P.nx) ? xs[io + t] : __int_as_float(0x7fc00000);
+    else if (t < 2 * GK) sy[t - GK] = (jo + t - GK < P.ny) ? ys[jo + t - GK] : __int_as_float(0x7fc00000);
+    {
+      // window weights, kw x kw: row j (N of stage 1), nodes i (K); 8 nodes
+      // per chunk, kw * kw / 8 chunks over the threads
+      const int cpr = P.kw / 8;  // chunks per row
 #pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      float v[32];
-      tc::tmem_ld32(lane_base + (which ? TM_D2 : TM_D1) + (uint32_t)(half * 32), v);
+      for (int q = t; q < P.kw * cpr; q += GTHREADS) {
+        const int j = q / cpr, c = q % cpr, jg = jo + j;
+        float v[8];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+        for (int e = 0; e < 8; ++e) {
+          const int ig = io + c * 8 + e;
+          v[e] = (jg < P.ny && ig < P.nx) ? W[(int64_t)jg * P.nx + ig] : 0.f;
+        }
         uint32_t hv[4], lv[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
-        st_chunk(thi, row, half * 4 + c, hv);
-        st_chunk(tlo, row, half * 4 + c, lv);
+        for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], hv[e], lv[e]);
+        st_chunk(sm + S_W_HI, j, c, hv);
+        st_chunk(sm + S_W_LO, j, c, lv);
       }
+    }
+    __syncthreads();
+    // operands: threads 0-127 row t of Ex, Ex' (raster column k0 + t); threads
+    // 128-255 row t - 128 of Ey, Ey' (raster row l0 + t - 128)
+    if (t < GT) {
+      const int64_t k = k0 + t;
+      const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
+      axis_rows(sm, S_EX_HI, S_EX_LO, S_EXD_HI, S_EXD_LO, t, k < P.nqx, qx, sx, P);
+    } else {
+      const int64_t l = l0 + (t - GT);
+      const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
+      axis_rows(sm, S_EY_HI, S_EY_LO, S_EYD_HI, S_EYD_LO, t - GT, l < P.nqy, qy, sy, P);
     }
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    // stage 2: H = Ey T1, Gx = Ey T2, Gy = Ey' T1 (rows = raster rows l, columns = raster columns k)
-    if (t == 0) {
-      mma_split(tmem + TM_H, base + S_EY_HI, base + S_EY_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT));
-      mma_split(tmem + TM_GX, base + S_EY_HI, base + S_EY_LO, base + S_T2_HI, base + S_T2_LO, idesc_bf16(GT));
-      mma_split(tmem + TM_GY, base + S_EYD_HI, base + S_EYD_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT));
-      tc::mma_commit(&mbar);
-    }
-    committed = 2;
-    ok = wait_mma(&mbar, 1, &done_s);
-  }
 
-  // epilogue: warp w takes tile rows 32 (w % 4) .. + 31 and columns
-  // 64 (w / 4) .. + 63 in two blocks of 32.  The tensor-memory loads are
-  // warp-wide (.sync.aligned); each block goes through a padded per-warp
-  // buffer so that the global stores write whole rows: 128 contiguous bytes of
-  // h and 256 of grad h per warp instruction.  The operand tiles are free once
-  // the stage-2 MMAs have completed.
-  if (use_tma) {
-    // rows of the warp's 32 x 32 blocks into 128-byte swizzled boxes (row
-    // `lane` of the box is this thread's tensor-memory row), then bulk tensor
-    // stores by one lane: h, and grad h as two boxes of 16 (d/dx, d/dy) pairs
-    uint8_t* bh = sm + warp * (3 * BOX);
-    uint8_t* bg0 = bh + BOX;
-    uint8_t* bg1 = bg0 + BOX;
-    const bool want_g = gout != nullptr;
-    const int64_t y0 = l0 + quad * 32;
-#pragma unroll 1
-    for (int b = 0; b < 2; ++b) {
-      const int cb = (warp >> 2) * 2 + b;
-      const int64_t kb = k0 + cb * 32;
-      if (kb >= P.nqx) break;  // uniform over the warp
-      float vh[32], vx[32], vy[32];
-      if (ok) {
-        tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
-        if (want_g) {
-          tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
-          tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
+    bool ok = healthy;
+    if (ok) {
+      // stage 1: T1^T = Ex W^T and T2^T = Ex' W^T (rows = raster columns k, columns = window rows j)
+      if (t == 0) {
+        const int nk = P.kw / 16;
+        mma_split(tmem + TM_D1, base + S_EX_HI, base + S_EX_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(P.kw), nk);
+        mma_split(tmem + TM_D2, base + S_EXD_HI, base + S_EXD_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(P.kw), nk);
+        tc::mma_commit(&mbar);
       }
-      if (b > 0 && lane == 0) bulk_wait_read();  // the previous block's boxes have been read
-      __syncwarp();
+      last = phase;
+      any = true;
+      ok = wait_mma(&mbar, phase, &done_s);
+      phase ^= 1u;
+    }
+    if (ok) {
+      // T1^T (warps 0-3) and T2^T (warps 4-7) back from tensor memory, split and
+      // stored as the K-major B operands of stage 2 over the stage-1 A tiles
+      const int which = warp >> 2;
+      uint8_t* thi = sm + (which ? S_T2_HI : S_T1_HI);
+      uint8_t* tlo = sm + (which ? S_T2_LO : S_T1_LO);
+#pragma unroll 1
+      for (int half = 0; half < P.kw / 32; ++half) {
+        float v[32];
+        tc::tmem_ld32(lane_base + (which ? TM_D2 : TM_D1) + (uint32_t)(half * 32), v);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) st16(bh, lane, c, vh[4 * c], vh[4 * c + 1], vh[4 * c + 2], vh[4 * c + 3]);
-      if (want_g) {
+        for (int c = 0; c < 4; ++c) {
+          uint32_t hv[4], lv[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          st16(bg0, lane, c, vx[2 * c], vy[2 * c], vx[2 * c + 1], vy[2 * c + 1]);
-          st16(bg1, lane, c, vx[16 + 2 * c], vy[16 + 2 * c], vx[17 + 2 * c], vy[17 + 2 * c]);
+          for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
+          st_chunk(thi, row, half * 4 + c, hv);
+          st_chunk(tlo, row, half * 4 + c, lv);
         }
       }
       tc::fence_proxy_async();
-      __syncwarp();
-      if (lane == 0 && y0 < P.nqy) {
-        tma_store_2d(&map_h, bh, (int)kb, (int)y0);
-        if (want_g) {
-          tma_store_2d(&map_g, bg0, (int)(2 * kb), (int)y0);
-          if (kb + 16 < P.nqx) tma_store_2d(&map_g, bg1, (int)(2 * kb + 32), (int)y0);  // starts inside the tensor
-        }
-        bulk_commit();
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      // stage 2: H = Ey T1, Gx = Ey T2, Gy = Ey' T1 (rows = raster rows l, columns = raster columns k)
+      if (t == 0) {
+        const int nk = P.kw / 16;
+        mma_split(tmem + TM_H, base + S_EY_HI, base + S_EY_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT), nk);
+        mma_split(tmem + TM_GX, base + S_EY_HI, base + S_EY_LO, base + S_T2_HI, base + S_T2_LO, idesc_bf16(GT), nk);
+        mma_split(tmem + TM_GY, base + S_EYD_HI, base + S_EYD_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT), nk);
+        tc::mma_commit(&mbar);
       }
+      last = phase;
+      ok = wait_mma(&mbar, phase, &done_s);
+      phase ^= 1u;
     }
-    if (lane == 0) bulk_wait();  // the stores have completed before the CTA ends
-  } else {
-    float* th = reinterpret_cast<float*>(sm) + warp * (3 * 32 * TP);
-    float* tx = th + 32 * TP;
-    float* ty = tx + 32 * TP;
-    const bool want_g = gout != nullptr;
+    if (!ok) healthy = false;
+
+    // epilogue: warp w takes tile rows 32 (w % 4) .. + 31 and columns
+    // 64 (w / 4) .. + 63 in two blocks of 32; the tensor-memory loads are
+    // warp-wide (.sync.aligned).  The operand tiles are free once the stage-2
+    // MMAs have completed.
+    if (use_tma) {
+      // rows of the blocks into 128-byte swizzled boxes (row `lane` of a box is
+      // this thread's tensor-memory row), then bulk tensor stores by one lane:
+      // h, and grad h as two boxes of 16 (d/dx, d/dy) pairs
+      uint8_t* bh = sm + warp * (3 * BOX);
+      uint8_t* bg0 = bh + BOX;
+      uint8_t* bg1 = bg0 + BOX;
+      const int64_t y0 = l0 + quad * 32;
 #pragma unroll 1
-    for (int b = 0; b < 2; ++b) {
-      const int cb = (warp >> 2) * 2 + b;
-      const int64_t kb = k0 + cb * 32;
-      if (kb >= P.nqx) break;  // uniform over the warp
-      float vh[32], vx[32], vy[32];
-      if (ok) {
-        tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
+      for (int b = 0; b < 2; ++b) {
+        const int cb = (warp >> 2) * 2 + b;
+        const int64_t kb = k0 + cb * 32;
+        if (kb >= P.nqx) break;  // uniform over the warp
+        float vh[32], vx[32], vy[32];
+        if (ok) {
+          tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
+          if (want_g) {
+            tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
+            tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
+        }
+        if (b > 0 && lane == 0) bulk_wait_read();  // the previous block's boxes have been read
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) st16(bh, lane, c, vh[4 * c], vh[4 * c + 1], vh[4 * c + 2], vh[4 * c + 3]);
         if (want_g) {
-          tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
-          tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            st16(bg0, lane, c, vx[2 * c], vy[2 * c], vx[2 * c + 1], vy[2 * c + 1]);
+            st16(bg1, lane, c, vx[16 + 2 * c], vy[16 + 2 * c], vx[17 + 2 * c], vy[17 + 2 * c]);
+          }
         }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
-      }
-#pragma unroll
-      for (int e = 0; e < 32; ++e) th[lane * TP + e] = vh[e];
-      if (want_g) {
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          tx[lane * TP + e] = vx[e];
-          ty[lane * TP + e] = vy[e];
+        tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0 && y0 < P.nqy) {
+          tma_store_2d(&map_h, bh, (int)kb, (int)y0);
+          if (want_g) {
+            tma_store_2d(&map_g, bg0, (int)(2 * kb), (int)y0);
+            if (kb + 16 < P.nqx) tma_store_2d(&map_g, bg1, (int)(2 * kb + 32), (int)y0);  // starts inside the tensor
+          }
+          bulk_commit();
         }
       }
-      __syncwarp();
-      const int64_t k = kb + lane;
-      const bool kin = k < P.nqx;
+    } else {
+      // each block goes through a padded per-warp buffer so that the global
+      // stores write whole rows: 128 contiguous bytes of h and 256 of grad h
+      float* th = reinterpret_cast<float*>(sm) + warp * (3 * 32 * TP);
+      float* tx = th + 32 * TP;
+      float* ty = tx + 32 * TP;
+#pragma unroll 1
+      for (int b = 0; b < 2; ++b) {
+        const int cb = (warp >> 2) * 2 + b;
+        const int64_t kb = k0 + cb * 32;
+        if (kb >= P.nqx) break;  // uniform over the warp
+        float vh[32], vx[32], vy[32];
+        if (ok) {
+          tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
+          if (want_g) {
+            tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
+            tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
+        }
+#pragma unroll
+        for (int e = 0; e < 32; ++e) th[lane * TP + e] = vh[e];
+        if (want_g) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            tx[lane * TP + e] = vx[e];
+            ty[lane * TP + e] = vy[e];
+          }
+        }
+        __syncwarp();
+        const int64_t k = kb + lane;
+        const bool kin = k < P.nqx;
 #pragma unroll 4
-      for (int r = 0; r < 32; ++r) {
-        const int64_t l = l0 + quad * 32 + r;
-        if (l >= P.nqy) break;  // uniform over the warp
-        if (kin) {
-          hout[l * P.nqx + k] = th[r * TP + lane];
-          if (want_g)
-            *reinterpret_cast<float2*>(gout + 2 * (l * P.nqx + k)) = make_float2(tx[r * TP + lane], ty[r * TP + lane]);
+        for (int r = 0; r < 32; ++r) {
+          const int64_t l = l0 + quad * 32 + r;
+          if (l >= P.nqy) break;  // uniform over the warp
+          if (kin) {
+            hout[l * P.nqx + k] = th[r * TP + lane];
+            if (want_g)
+              *reinterpret_cast<float2*>(gout + 2 * (l * P.nqx + k)) = make_float2(tx[r * TP + lane], ty[r * TP + lane]);
+          }
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
+    tc::fence_before();  // tensor-memory loads of this tile before the next tile's MMAs
+    __syncthreads();
+    tc::fence_after();
   }
-  if (!ok && t == 0) {
+  if (use_tma && lane == 0) bulk_wait();  // the stores have completed before the CTA ends
+  if (!healthy && any && t == 0) {
     // give the MMAs of the last committed phase one more bounded chance to
     // drain before tensor memory is freed (a commit arrives once every earlier
     // MMA of the thread has completed)
     long long it = 0;
-    while (!tc::mbar_try_wait(&mbar, (uint32_t)(committed - 1)) && ++it < tc::WAIT_LIMIT) {
+    while (!tc::mbar_try_wait(&mbar, last) && ++it < tc::WAIT_LIMIT) {
     }
   }
   tc::fence_before();
@@ -453,7 +483,7 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
     return fail(RBF_ERANGE, "raster spacing %g too coarse for 64-node windows (at most %g); use rbf_eval", dq,
                 (60.5 * c->lat.h - 2.0 * r) / 127.0);
   const int64_t tx = (nqx + GT - 1) / GT, ty = (nqy + GT - 1) / GT;
-  if (tx > 0x7fffffffLL || ty > 65535) return fail(RBF_ERANGE, "raster too large for one launch");
+  if (tx > 0x7fffffffLL || ty > 0x7fffffffLL) return fail(RBF_ERANGE, "raster too large");
   if (!std::isfinite(qx0 + (double)(nqx - 1) * dq) || !std::isfinite(qy0 + (double)(nqy - 1) * dq))
     return fail(RBF_EINVAL, "raster coordinates overflow");
   GridParams P;
@@ -473,6 +503,8 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
   P.r2 = r32 * r32;
   P.inv2s2 = (float)(1.0 / (2.0 * c->cfg.sigma * c->cfg.sigma));
   P.inv_s2 = (float)(1.0 / (c->cfg.sigma * c->cfg.sigma));
+  // windows of 32 nodes where they cover a tile (half the operands and MMAs)
+  P.kw = (127.0 * dq + 2.0 * r <= 28.5 * c->lat.h) ? 32 : 64;
   cudaStream_t s = (cudaStream_t)stream;
   static bool attr_set[64] = {false};
   if (!attr_set[c->device & 63]) {
@@ -500,9 +532,14 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
       if (e != CUDA_SUCCESS) return fail(RBF_ECUDA, "tensor map of grad: error %d", (int)e);
     }
   }
+  // one persistent CTA per SM (the shared memory allows one)
+  static int sms[64] = {0};
+  if (!sms[c->device & 63]) RBF_CUDA(cudaDeviceGetAttribute(&sms[c->device & 63], cudaDevAttrMultiProcessorCount, c->device));
+  const int64_t ntiles = tx * ty;
+  const unsigned nblk = (unsigned)(ntiles < sms[c->device & 63] ? ntiles : sms[c->device & 63]);
   StageTimer st(c, RBF_STAGE_EVAL_GRID, s, (grad ? 12.0 : 4.0) * (double)nqx * (double)nqy);
-  { k_eval_grid_tc<<<dim3((unsigned)tx, (unsigned)ty), GTHREADS, GRID_SMEM, s>>>(
-        P, c->lat_xs.as<float>(), c->lat_ys.as<float>(), c->wlat.as<float>(), h, grad, map_h, map_g, use_tma);
+  { k_eval_grid_tc<<<nblk, GTHREADS, GRID_SMEM, s>>>(P, c->lat_xs.as<float>(), c->lat_ys.as<float>(),
+                                                     c->wlat.as<float>(), h, grad, map_h, map_g, use_tma, tx, ntiles);
     ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
