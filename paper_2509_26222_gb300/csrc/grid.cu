@@ -177,10 +177,6 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ void st16(uint8_t* box, int row, int chunk, float a, float b, float c, float d) {
-  *reinterpret_cast<float4*>(box + tc::sw128_offset(row, chunk)) = make_float4(a, b, c, d);
-}
-
 constexpr int GTHREADS = 256;  // 8 warps: two per tensor-memory lane quadrant
 constexpr int BOX = 32 * 128;  // one 32 x 32 float32 box
 constexpr int TP = 33;         // padded row of the per-warp transpose buffers
@@ -337,26 +333,36 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
         const int cb = (warp >> 2) * 2 + b;
         const int64_t kb = k0 + cb * 32;
         if (kb >= P.nqx) break;  // uniform over the warp
-        float vh[32], vx[32], vy[32];
+        uint32_t rh[32], rx[32], ry[32];  // float32 bit patterns
         if (ok) {
-          tc::tmem_ld32(lane_base + TM_H + (uint32_t)(cb * 32), vh);
+          // the three loads in flight together, one wait
+          tc::tmem_ld32_nowait(lane_base + TM_H + (uint32_t)(cb * 32), rh);
           if (want_g) {
-            tc::tmem_ld32(lane_base + TM_GX + (uint32_t)(cb * 32), vx);
-            tc::tmem_ld32(lane_base + TM_GY + (uint32_t)(cb * 32), vy);
+            tc::tmem_ld32_nowait(lane_base + TM_GX + (uint32_t)(cb * 32), rx);
+            tc::tmem_ld32_nowait(lane_base + TM_GY + (uint32_t)(cb * 32), ry);
+          }
+          tc::tmem_wait_ld(rh);
+          if (want_g) {
+            tc::tmem_wait_ld(rx);
+            tc::tmem_wait_ld(ry);
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) vh[e] = vx[e] = vy[e] = __int_as_float(0x7fc00000);
+          for (int e = 0; e < 32; ++e) rh[e] = rx[e] = ry[e] = 0x7fc00000u;
         }
         if (b > 0 && lane == 0) bulk_wait_read();  // the previous block's boxes have been read
         __syncwarp();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) st16(bh, lane, c, vh[4 * c], vh[4 * c + 1], vh[4 * c + 2], vh[4 * c + 3]);
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<uint4*>(bh + tc::sw128_offset(lane, c)) =
+              make_uint4(rh[4 * c], rh[4 * c + 1], rh[4 * c + 2], rh[4 * c + 3]);
         if (want_g) {
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            st16(bg0, lane, c, vx[2 * c], vy[2 * c], vx[2 * c + 1], vy[2 * c + 1]);
-            st16(bg1, lane, c, vx[16 + 2 * c], vy[16 + 2 * c], vx[17 + 2 * c], vy[17 + 2 * c]);
+            *reinterpret_cast<uint4*>(bg0 + tc::sw128_offset(lane, c)) =
+                make_uint4(rx[2 * c], ry[2 * c], rx[2 * c + 1], ry[2 * c + 1]);
+            *reinterpret_cast<uint4*>(bg1 + tc::sw128_offset(lane, c)) =
+                make_uint4(rx[16 + 2 * c], ry[16 + 2 * c], rx[17 + 2 * c], ry[17 + 2 * c]);
           }
         }
         tc::fence_proxy_async();
