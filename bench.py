@@ -59,6 +59,12 @@ def peaks():
 # accumulators of 128 x 64 over K = 64; stage 2, three of 128 x 128 over K = 64;
 # three split bfloat16 products each
 RASTER_TILE_FLOPS = 3 * (2 * 128 * 64 * 64 * 2 + 3 * 128 * 128 * 64 * 2)
+# DRAM bytes (read + write) of one k_eval_grid_tc launch on the 5120 x 5120
+# raster of workloads.raster_gaussian (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum on `bench.py --steps 2 --warmup 3 --no-cpu
+# --eval-log2 20 --batch-patches 0 --c5-reps 0 --no-other`); below the 12 B per
+# point written because part of the output is still in L2 when the kernel ends
+RASTER_DRAM_BYTES = 930048.0 + 253547264.0
 
 
 def raster_line(r, pk, pk_kind):
@@ -71,8 +77,10 @@ def raster_line(r, pk, pk_kind):
     tf = RASTER_TILE_FLOPS * r["tiles"] / sec / 1e12
     return {"workload": r["workload"], "points": r["points"], "ms": r["ms"], "points_per_s": r["points"] / sec,
             "roofline": {"kernel": "k_eval_grid_tc", "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
-                         "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": None, "bytes_per_point": 12,
-                         "peak_kind": pk_kind},
+                         "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                         "traffic": RASTER_DRAM_BYTES if r["points"] == 5120 * 5120 else None,
+                         "traffic_source": "ncu dram__bytes_read+write of one launch on the same raster",
+                         "bytes_per_point": 12, "peak_kind": pk_kind},
             "tensor": {"achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": tf / pk["bf16_tflops"],
                        "flops_per_tile": RASTER_TILE_FLOPS, "peak_kind": "bf16 burst (" + pk_kind + ")"},
             "scattered_eval_same_points_ms": r["scattered_eval_same_points_ms"],
