@@ -36,17 +36,40 @@ namespace {
 
 constexpr int GT = 128;                 // raster points per tile side (M and N of stage 2)
 constexpr int GK = 64;                  // largest window: lattice nodes per side (K of both stages, N of stage 1)
-constexpr int OP_ROWS128 = GT * GK * 2; // 16 KiB: 128 rows x 64 bfloat16
-constexpr int OP_ROWS64 = GK * GK * 2;  // 8 KiB: 64 rows x 64 bfloat16
-// shared-memory map (offsets from the 1024-byte aligned base)
-constexpr int S_EX_HI = 0, S_EX_LO = 1 * OP_ROWS128, S_EXD_HI = 2 * OP_ROWS128, S_EXD_LO = 3 * OP_ROWS128;
-constexpr int S_W_HI = 4 * OP_ROWS128, S_W_LO = S_W_HI + OP_ROWS64;
-constexpr int S_EY_HI = S_W_LO + OP_ROWS64, S_EY_LO = S_EY_HI + OP_ROWS128;
-constexpr int S_EYD_HI = S_EY_LO + OP_ROWS128, S_EYD_LO = S_EYD_HI + OP_ROWS128;
-constexpr int S_END = S_EYD_LO + OP_ROWS128;  // 144 KiB
-// stage 2 reuses the stage-1 A tiles for T1^T and T2^T (hi and lo)
-constexpr int S_T1_HI = S_EX_HI, S_T1_LO = S_EX_LO, S_T2_HI = S_EXD_HI, S_T2_LO = S_EXD_LO;
-constexpr int GRID_SMEM = S_END + 1024;
+constexpr int BOX = 32 * 128;           // one 32 x 32 float32 output box (128-byte swizzle)
+constexpr int NBOXES = 8 * 3;           // three per warp
+
+// Shared-memory map for windows of KW nodes (offsets from the 1024-byte aligned
+// base).  Operand rows hold KW bfloat16: 64 bytes with the 64-byte swizzle for
+// KW = 32, 128 bytes with the 128-byte swizzle for KW = 64.  Stage 2 reuses the
+// stage-1 A tiles for T1^T and T2^T.  With KW = 32 the operands take 68 KiB
+// and the output boxes have their own space, so a tile's bulk stores drain
+// during the next tile; with KW = 64 (144 KiB of operands) the boxes reuse the
+// operand space and the next tile waits for their reads.
+template <int KW>
+struct Lay {
+  static constexpr int RB = 2 * KW;       // bytes per operand row
+  static constexpr int A = 128 * RB;      // 128-row operand tile
+  static constexpr int B = KW * RB;       // KW-row weight tile
+  static constexpr int EX_HI = 0, EX_LO = A, EXD_HI = 2 * A, EXD_LO = 3 * A;
+  static constexpr int W_HI = 4 * A, W_LO = 4 * A + B;
+  static constexpr int EY_HI = 4 * A + 2 * B, EY_LO = EY_HI + A, EYD_HI = EY_LO + A, EYD_LO = EYD_HI + A;
+  static constexpr int T1_HI = EX_HI, T1_LO = EX_LO, T2_HI = EXD_HI, T2_LO = EXD_LO;
+  static constexpr int OPS = EYD_LO + A;
+  static constexpr bool SEPARATE = KW == 32;
+  static constexpr int BOXES = SEPARATE ? (OPS + 1023) / 1024 * 1024 : 0;
+  static constexpr int END = (BOXES + NBOXES * BOX > OPS) ? BOXES + NBOXES * BOX : OPS;
+  static constexpr int SMEM = END + 1024;  // alignment slack
+  static __device__ __forceinline__ uint32_t off(int r, int c) {
+    return KW == 32 ? tc::sw64_offset(r, c) : tc::sw128_offset(r, c);
+  }
+  static __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+    return KW == 32 ? tc::sdesc_sw64(saddr) : tc::sdesc_sw128(saddr);
+  }
+};
+static_assert(Lay<32>::SMEM <= 227 * 1024 && Lay<64>::SMEM <= 227 * 1024, "shared memory per CTA");
+static_assert(Lay<32>::W_LO % 512 == 0 && Lay<64>::W_LO % 1024 == 0, "swizzle atoms of the weight tiles");
+
 // tensor-memory columns
 constexpr uint32_t TM_D1 = 0, TM_D2 = 64, TM_H = 128, TM_GX = 256, TM_GY = 384, TM_COLS = 512;
 
@@ -64,18 +87,19 @@ __device__ __forceinline__ void mma_bf16_n(uint32_t tmem_d, uint64_t adesc, uint
       "l"(adesc), "l"(bdesc), "r"(accum), "r"(idesc));
 }
 
-// D = A B^T over K = 16 nk as the three split products, A and B given as
+// D = A B^T over K = KW as the three split products, A and B given as
 // (hi, lo) shared-memory tiles.
+template <int KW>
 __device__ __forceinline__ void mma_split(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                          uint32_t b_lo, uint32_t idesc, int nk) {
+                                          uint32_t b_lo, uint32_t idesc) {
   const uint32_t as[3] = {a_hi, a_hi, a_lo};
   const uint32_t bs[3] = {b_hi, b_lo, b_hi};
   uint32_t accum = 0;
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    const uint64_t ad = tc::sdesc_sw128(as[p]), bd = tc::sdesc_sw128(bs[p]);
-#pragma unroll 1
-    for (int kk = 0; kk < nk; ++kk) {
+    const uint64_t ad = Lay<KW>::desc(as[p]), bd = Lay<KW>::desc(bs[p]);
+#pragma unroll
+    for (int kk = 0; kk < KW / 16; ++kk) {
       mma_bf16_n(tmem_d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), accum, idesc);
       accum = 1;
     }
@@ -91,8 +115,9 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_
   lo = *reinterpret_cast<uint32_t*>(&l);
 }
 
+template <int KW>
 __device__ __forceinline__ void st_chunk(uint8_t* tile, int row, int chunk, const uint32_t (&v)[4]) {
-  *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row, chunk)) = make_uint4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<uint4*>(tile + Lay<KW>::off(row, chunk)) = make_uint4(v[0], v[1], v[2], v[3]);
 }
 
 struct GridParams {
@@ -120,10 +145,11 @@ __device__ __forceinline__ int window_origin(double q, double r, double l0, doub
 // Rows of g and g' for one raster coordinate q over the kw window nodes in
 // shared memory (nodes past the lattice hold NaN, which fails the test;
 // raster points outside the raster give zeros).
+template <int KW>
 __device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int s_dhi, int s_dlo, int row,
                                           bool in, float q, const float* nodes, const GridParams& P) {
 #pragma unroll 1
-  for (int c = 0; c < P.kw / 8; ++c) {
+  for (int c = 0; c < KW / 8; ++c) {
     uint32_t hv[4], lv[4], dhv[4], dlv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -142,10 +168,10 @@ __device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int
       split2(g[0], g[1], hv[e], lv[e]);
       split2(gd[0], gd[1], dhv[e], dlv[e]);
     }
-    st_chunk(smem + s_hi, row, c, hv);
-    st_chunk(smem + s_lo, row, c, lv);
-    st_chunk(smem + s_dhi, row, c, dhv);
-    st_chunk(smem + s_dlo, row, c, dlv);
+    st_chunk<KW>(smem + s_hi, row, c, hv);
+    st_chunk<KW>(smem + s_lo, row, c, lv);
+    st_chunk<KW>(smem + s_dhi, row, c, dhv);
+    st_chunk<KW>(smem + s_dlo, row, c, dlv);
   }
 }
 
@@ -178,13 +204,13 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 constexpr int GTHREADS = 256;  // 8 warps: two per tensor-memory lane quadrant
-constexpr int BOX = 32 * 128;  // one 32 x 32 float32 box
 constexpr int TP = 33;         // padded row of the per-warp transpose buffers
 
 // Persistent: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // (tile = ty * ntx + tx).  The bulk stores of a tile drain while the next
 // tile's operands are generated; only their reads of shared memory are waited
 // for before the operands overwrite the boxes.
+template <int KW>
 __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
                                                            const float* __restrict__ ys,
                                                            const float* __restrict__ W, float* __restrict__ hout,
@@ -217,9 +243,11 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
   uint32_t last = 0;       // parity of the last committed phase
   bool any = false;        // something was committed
 
+  using L = Lay<KW>;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t k0 = (tile % ntx) * GT, l0 = (tile / ntx) * GT;
-    if (use_tma && lane == 0) bulk_wait_read();  // the previous tile's boxes have been read
+    // boxes over the operands: the previous tile's boxes have been read
+    if (!L::SEPARATE && use_tma && lane == 0) bulk_wait_read();
     if (t == 0) {
       org[0] = window_origin(P.qx0 + (double)k0 * P.dq, P.r, P.lx0, P.inv_lh, P.nx);
       org[1] = window_origin(P.qy0 + (double)l0 * P.dq, P.r, P.ly0, P.inv_lh, P.ny);
@@ -231,9 +259,9 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
     {
       // window weights, kw x kw: row j (N of stage 1), nodes i (K); 8 nodes
       // per chunk, kw * kw / 8 chunks over the threads
-      const int cpr = P.kw / 8;  // chunks per row
+      constexpr int cpr = KW / 8;  // chunks per row
 #pragma unroll 1
-      for (int q = t; q < P.kw * cpr; q += GTHREADS) {
+      for (int q = t; q < KW * cpr; q += GTHREADS) {
         const int j = q / cpr, c = q % cpr, jg = jo + j;
         float v[8];
 #pragma unroll
@@ -244,8 +272,8 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
         uint32_t hv[4], lv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], hv[e], lv[e]);
-        st_chunk(sm + S_W_HI, j, c, hv);
-        st_chunk(sm + S_W_LO, j, c, lv);
+        st_chunk<KW>(sm + L::W_HI, j, c, hv);
+        st_chunk<KW>(sm + L::W_LO, j, c, lv);
       }
     }
     __syncthreads();
@@ -254,11 +282,11 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
     if (t < GT) {
       const int64_t k = k0 + t;
       const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
-      axis_rows(sm, S_EX_HI, S_EX_LO, S_EXD_HI, S_EXD_LO, t, k < P.nqx, qx, sx, P);
+      axis_rows<KW>(sm, L::EX_HI, L::EX_LO, L::EXD_HI, L::EXD_LO, t, k < P.nqx, qx, sx, P);
     } else {
       const int64_t l = l0 + (t - GT);
       const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
-      axis_rows(sm, S_EY_HI, S_EY_LO, S_EYD_HI, S_EYD_LO, t - GT, l < P.nqy, qy, sy, P);
+      axis_rows<KW>(sm, L::EY_HI, L::EY_LO, L::EYD_HI, L::EYD_LO, t - GT, l < P.nqy, qy, sy, P);
     }
     tc::fence_proxy_async();
     tc::fence_before();
@@ -269,9 +297,9 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
     if (ok) {
       // stage 1: T1^T = Ex W^T and T2^T = Ex' W^T (rows = raster columns k, columns = window rows j)
       if (t == 0) {
-        const int nk = P.kw / 16;
-        mma_split(tmem + TM_D1, base + S_EX_HI, base + S_EX_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(P.kw), nk);
-        mma_split(tmem + TM_D2, base + S_EXD_HI, base + S_EXD_LO, base + S_W_HI, base + S_W_LO, idesc_bf16(P.kw), nk);
+        mma_split<KW>(tmem + TM_D1, base + L::EX_HI, base + L::EX_LO, base + L::W_HI, base + L::W_LO, idesc_bf16(KW));
+        mma_split<KW>(tmem + TM_D2, base + L::EXD_HI, base + L::EXD_LO, base + L::W_HI, base + L::W_LO,
+                      idesc_bf16(KW));
         tc::mma_commit(&mbar);
       }
       last = phase;
@@ -283,10 +311,10 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
       // T1^T (warps 0-3) and T2^T (warps 4-7) back from tensor memory, split and
       // stored as the K-major B operands of stage 2 over the stage-1 A tiles
       const int which = warp >> 2;
-      uint8_t* thi = sm + (which ? S_T2_HI : S_T1_HI);
-      uint8_t* tlo = sm + (which ? S_T2_LO : S_T1_LO);
+      uint8_t* thi = sm + (which ? L::T2_HI : L::T1_HI);
+      uint8_t* tlo = sm + (which ? L::T2_LO : L::T1_LO);
 #pragma unroll 1
-      for (int half = 0; half < P.kw / 32; ++half) {
+      for (int half = 0; half < KW / 32; ++half) {
         float v[32];
         tc::tmem_ld32(lane_base + (which ? TM_D2 : TM_D1) + (uint32_t)(half * 32), v);
 #pragma unroll
@@ -294,8 +322,8 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
           uint32_t hv[4], lv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) split2(v[c * 8 + 2 * e], v[c * 8 + 2 * e + 1], hv[e], lv[e]);
-          st_chunk(thi, row, half * 4 + c, hv);
-          st_chunk(tlo, row, half * 4 + c, lv);
+          st_chunk<KW>(thi, row, half * 4 + c, hv);
+          st_chunk<KW>(tlo, row, half * 4 + c, lv);
         }
       }
       tc::fence_proxy_async();
@@ -304,10 +332,10 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
       tc::fence_after();
       // stage 2: H = Ey T1, Gx = Ey T2, Gy = Ey' T1 (rows = raster rows l, columns = raster columns k)
       if (t == 0) {
-        const int nk = P.kw / 16;
-        mma_split(tmem + TM_H, base + S_EY_HI, base + S_EY_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT), nk);
-        mma_split(tmem + TM_GX, base + S_EY_HI, base + S_EY_LO, base + S_T2_HI, base + S_T2_LO, idesc_bf16(GT), nk);
-        mma_split(tmem + TM_GY, base + S_EYD_HI, base + S_EYD_LO, base + S_T1_HI, base + S_T1_LO, idesc_bf16(GT), nk);
+        mma_split<KW>(tmem + TM_H, base + L::EY_HI, base + L::EY_LO, base + L::T1_HI, base + L::T1_LO, idesc_bf16(GT));
+        mma_split<KW>(tmem + TM_GX, base + L::EY_HI, base + L::EY_LO, base + L::T2_HI, base + L::T2_LO, idesc_bf16(GT));
+        mma_split<KW>(tmem + TM_GY, base + L::EYD_HI, base + L::EYD_LO, base + L::T1_HI, base + L::T1_LO,
+                      idesc_bf16(GT));
         tc::mma_commit(&mbar);
       }
       last = phase;
@@ -324,7 +352,7 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
       // rows of the blocks into 128-byte swizzled boxes (row `lane` of a box is
       // this thread's tensor-memory row), then bulk tensor stores by one lane:
       // h, and grad h as two boxes of 16 (d/dx, d/dy) pairs
-      uint8_t* bh = sm + warp * (3 * BOX);
+      uint8_t* bh = sm + L::BOXES + warp * (3 * BOX);
       uint8_t* bg0 = bh + BOX;
       uint8_t* bg1 = bg0 + BOX;
       const int64_t y0 = l0 + quad * 32;
@@ -350,7 +378,7 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
 #pragma unroll
           for (int e = 0; e < 32; ++e) rh[e] = rx[e] = ry[e] = 0x7fc00000u;
         }
-        if (b > 0 && lane == 0) bulk_wait_read();  // the previous block's boxes have been read
+        if (lane == 0) bulk_wait_read();  // the boxes' previous stores have read them
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < 8; ++c)
@@ -514,7 +542,8 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
   cudaStream_t s = (cudaStream_t)stream;
   static bool attr_set[64] = {false};
   if (!attr_set[c->device & 63]) {
-    RBF_CUDA(cudaFuncSetAttribute(k_eval_grid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GRID_SMEM));
+    RBF_CUDA(cudaFuncSetAttribute(k_eval_grid_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<32>::SMEM));
+    RBF_CUDA(cudaFuncSetAttribute(k_eval_grid_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<64>::SMEM));
     attr_set[c->device & 63] = true;
   }
   // bulk tensor stores need 16-byte aligned outputs and row pitches; other
@@ -544,9 +573,15 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
   const int64_t ntiles = tx * ty;
   const unsigned nblk = (unsigned)(ntiles < sms[c->device & 63] ? ntiles : sms[c->device & 63]);
   StageTimer st(c, RBF_STAGE_EVAL_GRID, s, (grad ? 12.0 : 4.0) * (double)nqx * (double)nqy);
-  { k_eval_grid_tc<<<nblk, GTHREADS, GRID_SMEM, s>>>(P, c->lat_xs.as<float>(), c->lat_ys.as<float>(),
-                                                     c->wlat.as<float>(), h, grad, map_h, map_g, use_tma, tx, ntiles);
-    ::rbf::note_launch(); }
+  if (P.kw == 32)
+    k_eval_grid_tc<32><<<nblk, GTHREADS, Lay<32>::SMEM, s>>>(P, c->lat_xs.as<float>(), c->lat_ys.as<float>(),
+                                                             c->wlat.as<float>(), h, grad, map_h, map_g, use_tma, tx,
+                                                             ntiles);
+  else
+    k_eval_grid_tc<64><<<nblk, GTHREADS, Lay<64>::SMEM, s>>>(P, c->lat_xs.as<float>(), c->lat_ys.as<float>(),
+                                                             c->wlat.as<float>(), h, grad, map_h, map_g, use_tma, tx,
+                                                             ntiles);
+  ::rbf::note_launch();
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }

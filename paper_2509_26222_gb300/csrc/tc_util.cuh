@@ -27,6 +27,18 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for 64-byte rows with the 64-byte swizzle: 8-row groups 512 bytes
+// apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset
+  d |= (uint64_t)1 << 46;               // version
+  d |= (uint64_t)4 << 61;               // 64-byte swizzle
+  return d;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(mbar))
@@ -112,6 +124,13 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
 // Byte offset of element (row r, k) in a 128-byte-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_offset(int r, int chunk) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4));
+}
+
+// Byte offset of 16-byte chunk `chunk` (0..3) of row r in a 64-byte-swizzled
+// K-major tile (rows of 64 bytes; the chunk index is XORed with bits 1-2 of
+// the row).
+__device__ __forceinline__ uint32_t sw64_offset(int r, int chunk) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((chunk ^ ((r >> 1) & 3)) << 4));
 }
 
 }  // namespace tc
