@@ -64,7 +64,7 @@ RASTER_TILE_FLOPS = 3 * (2 * 128 * 64 * 64 * 2 + 3 * 128 * 128 * 64 * 2)
 # dram__bytes_write.sum on `bench.py --steps 2 --warmup 3 --no-cpu
 # --eval-log2 20 --batch-patches 0 --c5-reps 0 --no-other`); below the 12 B per
 # point written because part of the output is still in L2 when the kernel ends
-RASTER_DRAM_BYTES = 930048.0 + 253547264.0
+RASTER_DRAM_BYTES = 921088.0 + 253018112.0
 
 
 def raster_line(r, pk, pk_kind):
@@ -279,6 +279,14 @@ def run_ours(args, ws, rank, local):
         T.soft_cost(eye, s, b, out=out7)
         T.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
 
+    # one untimed pass over every frame of the run sizes the workspaces and
+    # loads every kernel those frames reach; the model is then reset to the
+    # prior (set_centers keeps the workspaces), so the warm-up and the timed
+    # frames start from the state of a fresh context
+    for k in range(nfr):
+        step(dev_frames[k])
+    T.set_centers(centers)
+    torch.cuda.synchronize()
     for k in range(args.warmup):
         step(dev_frames[k])
     torch.cuda.synchronize()
@@ -681,6 +689,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "update_precision": args.precision, "frames_timed": K,
                    "active_block_last": r["a_last"], "l2": "flushed between steps (512 MB write)",
+                   "workspaces": "sized by one untimed pass over the run's frames, model reset to the prior before "
+                                 "the warm-up",
                    "eval_dtype": "f32", "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "e2e": {"value": ws * K / (r["e2e_ms"] * 1e-3), "unit": "frames/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},

@@ -427,7 +427,8 @@ rbf_status reset_update_state(Ctx* c) {
   c->bw_lf = BW_DENSE;
   c->Hs.valid = false;
   c->Hs_next.valid = false;
-  c->Pg.release();
+  // the outside covariance store keeps its allocation: it is zeroed and set to
+  // the prior when the next departure turns it on
   return RBF_OK;
 }
 
