@@ -551,7 +551,9 @@ extern "C" rbf_status rbf_eval_grid(rbf_ctx* cx, double qx0, double qy0, double 
   CUtensorMap map_h, map_g;
   memset(&map_h, 0, sizeof(map_h));
   memset(&map_g, 0, sizeof(map_g));
-  int use_tma = (nqx % 4 == 0) && ((uintptr_t)h % 16 == 0) && (!grad || (uintptr_t)grad % 16 == 0);
+  // (box coordinates are 32-bit: the gradient's x reaches 2 nqx)
+  int use_tma = (nqx % 4 == 0) && ((uintptr_t)h % 16 == 0) && (!grad || (uintptr_t)grad % 16 == 0) &&
+                2 * nqx + 64 < 0x7fffffffLL && nqy < 0x7fffffffLL;
   if (use_tma) {
     EncodeTiled enc = encode_tiled();
     if (!enc) return fail(RBF_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
