@@ -72,12 +72,17 @@ def test_eval_grid_parity_ragged(N, nqx, nqy):
     check(h2, None, ref)
 
 
-def test_eval_grid_coarsest_raster(N):
-    # the largest spacing the 64-node windows accept
+@pytest.mark.parametrize("nqx", [140, 141])
+def test_eval_grid_coarsest_raster(N, nqx):
+    # the largest spacing the 64-node windows accept; nqx = 140 takes the bulk
+    # tensor stores, 141 the transposing stores
     T, c, w = lattice_terrain(N, 50, 50, seed=1)
     dq = (60.5 * MESH - 2.0 * CUT * SIGMA) / 127.0 * 0.999
-    h, g = T.eval_grid(0.02, 0.03, dq, 140, 133)
-    check(h, g, O.eval_grid(0.02, 0.03, dq, 140, 133, c, w, sigma=SIGMA, cutoff_mult=CUT))
+    ref = O.eval_grid(0.02, 0.03, dq, nqx, 133, c, w, sigma=SIGMA, cutoff_mult=CUT)
+    h, g = T.eval_grid(0.02, 0.03, dq, nqx, 133)
+    check(h, g, ref)
+    h2, _ = T.eval_grid(0.02, 0.03, dq, nqx, 133, with_grad=False)
+    check(h2, None, ref)
 
 
 def test_eval_grid_matches_scattered_eval_up_to_corners(N):
