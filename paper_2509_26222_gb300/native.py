@@ -110,6 +110,18 @@ STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval"
           "trsm32", "inverse", "invapply", "covblock", "schur", "enter", "evalgrid"]
 
 
+def _out_tensor(t, n, device):
+    """A caller's output buffer: contiguous float32 on the context's device
+    with room for n values (the kernels write through its raw pointer)."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("output buffers must be contiguous float32 tensors")
+    if t.device != torch.device(device):
+        raise ValueError(f"output buffer on {t.device}, expected {device}")
+    if t.numel() < n:
+        raise ValueError(f"output buffer holds {t.numel()} values, {n} needed")
+    return t
+
+
 def _so3_exp(v):
     """Rotation matrix exp([v]_x) (Rodrigues)."""
     v = np.asarray(v, dtype=np.float64)
@@ -263,10 +275,12 @@ class Terrain:
     def eval(self, q, out_h=None, out_grad=None, with_grad=True):
         q = _dev_tensor(q, torch.float32, 2)
         Q = q.shape[0]
-        h = out_h if out_h is not None else torch.empty(Q, dtype=torch.float32, device=q.device)
+        h = _out_tensor(out_h, Q, q.device) if out_h is not None else torch.empty(Q, dtype=torch.float32,
+                                                                                   device=q.device)
         g = None
         if with_grad:
-            g = out_grad if out_grad is not None else torch.empty(Q, 2, dtype=torch.float32, device=q.device)
+            g = (_out_tensor(out_grad, 2 * Q, q.device) if out_grad is not None
+                 else torch.empty(Q, 2, dtype=torch.float32, device=q.device))
         _check(self.lib.rbf_eval(self._h, _ptr(q), Q, _ptr(h), _ptr(g), _stream()))
         return h, g
 
@@ -274,10 +288,12 @@ class Terrain:
         """h (nqy x nqx) and grad h (nqy x nqx x 2) on the raster (qx0 + k dq, qy0 + l dq):
         Gaussian kernel, centers on a lattice, per-axis truncation (rbf_eval_grid)."""
         dev = torch.device("cuda", torch.cuda.current_device())
-        h = out_h if out_h is not None else torch.empty(nqy, nqx, dtype=torch.float32, device=dev)
+        n = int(nqx) * int(nqy)
+        h = _out_tensor(out_h, n, dev) if out_h is not None else torch.empty(nqy, nqx, dtype=torch.float32, device=dev)
         g = None
         if with_grad:
-            g = out_grad if out_grad is not None else torch.empty(nqy, nqx, 2, dtype=torch.float32, device=dev)
+            g = (_out_tensor(out_grad, 2 * n, dev) if out_grad is not None
+                 else torch.empty(nqy, nqx, 2, dtype=torch.float32, device=dev))
         _check(self.lib.rbf_eval_grid(self._h, float(qx0), float(qy0), float(dq), int(nqx), int(nqy), _ptr(h),
                                       _ptr(g), _stream()))
         return h, g
