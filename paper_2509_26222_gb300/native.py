@@ -110,11 +110,11 @@ STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval"
           "trsm32", "inverse", "invapply", "covblock", "schur", "enter", "evalgrid"]
 
 
-def _out_tensor(t, n, device):
-    """A caller's output buffer: contiguous float32 on the context's device
+def _out_tensor(t, n, device, dtype=torch.float32):
+    """A caller's output buffer: contiguous `dtype` on the context's device
     with room for n values (the kernels write through its raw pointer)."""
-    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous():
-        raise ValueError("output buffers must be contiguous float32 tensors")
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"output buffers must be contiguous {dtype} tensors")
     if t.device != torch.device(device):
         raise ValueError(f"output buffer on {t.device}, expected {device}")
     if t.numel() < n:
@@ -302,7 +302,8 @@ class Terrain:
         R = torch.as_tensor(R, dtype=torch.float64).cpu().contiguous()
         t = torch.as_tensor(t, dtype=torch.float64).cpu().contiguous()
         p = _dev_tensor(pts, torch.float32, 3)
-        buf = out if out is not None else torch.empty(7, dtype=torch.float64, device=p.device)
+        buf = _out_tensor(out, 7, p.device, torch.float64) if out is not None else torch.empty(
+            7, dtype=torch.float64, device=p.device)
         resid = torch.empty(p.shape[0], dtype=torch.float32, device=p.device) if with_resid else None
         _check(self.lib.rbf_soft_cost(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], _ptr(buf[:1]),
                                       ctypes.c_void_p(buf.data_ptr() + 8), _ptr(resid), _stream()))
@@ -313,7 +314,8 @@ class Terrain:
         R = torch.as_tensor(R, dtype=torch.float64).cpu().contiguous()
         t = torch.as_tensor(t, dtype=torch.float64).cpu().contiguous()
         p = _dev_tensor(pts, torch.float32, 3)
-        buf = out if out is not None else torch.empty(28, dtype=torch.float64, device=p.device)
+        buf = _out_tensor(out, 28, p.device, torch.float64) if out is not None else torch.empty(
+            28, dtype=torch.float64, device=p.device)
         _check(self.lib.rbf_soft_cost_normal(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], _ptr(buf), _stream()))
         iu = torch.triu_indices(6, 6, device=p.device)
         A = torch.zeros(6, 6, dtype=torch.float64, device=p.device)
