@@ -41,11 +41,12 @@ constexpr int NBOXES = 8 * 3;           // three per warp
 
 // Shared-memory map for windows of KW nodes (offsets from the 1024-byte aligned
 // base).  Operand rows hold KW bfloat16: 64 bytes with the 64-byte swizzle for
-// KW = 32, 128 bytes with the 128-byte swizzle for KW = 64.  Stage 2 reuses the
-// stage-1 A tiles for T1^T and T2^T.  With KW = 32 the operands take 68 KiB
-// and the output boxes have their own space, so a tile's bulk stores drain
-// during the next tile; with KW = 64 (144 KiB of operands) the boxes reuse the
-// operand space and the next tile waits for their reads.
+// KW = 32, 128 bytes with the 128-byte swizzle for KW = 64.  With KW = 32 the
+// operands (68 KiB), T1^T and T2^T (32 KiB) and the output boxes (96 KiB) have
+// their own space: a tile's bulk stores drain during the next tile, and Ex, Ex'
+// stay for the next tile of the same raster column.  With KW = 64 (144 KiB of
+// operands) stage 2 reuses the stage-1 A tiles for T1^T and T2^T, the boxes
+// reuse the operand space and the next tile waits for their reads.
 template <int KW>
 struct Lay {
   static constexpr int RB = 2 * KW;       // bytes per operand row
@@ -54,11 +55,13 @@ struct Lay {
   static constexpr int EX_HI = 0, EX_LO = A, EXD_HI = 2 * A, EXD_LO = 3 * A;
   static constexpr int W_HI = 4 * A, W_LO = 4 * A + B;
   static constexpr int EY_HI = 4 * A + 2 * B, EY_LO = EY_HI + A, EYD_HI = EY_LO + A, EYD_LO = EYD_HI + A;
-  static constexpr int T1_HI = EX_HI, T1_LO = EX_LO, T2_HI = EXD_HI, T2_LO = EXD_LO;
   static constexpr int OPS = EYD_LO + A;
   static constexpr bool SEPARATE = KW == 32;
-  static constexpr int BOXES = SEPARATE ? (OPS + 1023) / 1024 * 1024 : 0;
-  static constexpr int END = (BOXES + NBOXES * BOX > OPS) ? BOXES + NBOXES * BOX : OPS;
+  static constexpr int T1_HI = SEPARATE ? OPS : EX_HI, T1_LO = SEPARATE ? OPS + A : EX_LO;
+  static constexpr int T2_HI = SEPARATE ? OPS + 2 * A : EXD_HI, T2_LO = SEPARATE ? OPS + 3 * A : EXD_LO;
+  static constexpr int OPS2 = SEPARATE ? OPS + 4 * A : OPS;
+  static constexpr int BOXES = SEPARATE ? (OPS2 + 1023) / 1024 * 1024 : 0;
+  static constexpr int END = (BOXES + NBOXES * BOX > OPS2) ? BOXES + NBOXES * BOX : OPS2;
   static constexpr int SMEM = END + 1024;  // alignment slack
   static __device__ __forceinline__ uint32_t off(int r, int c) {
     return KW == 32 ? tc::sw64_offset(r, c) : tc::sw128_offset(r, c);
@@ -147,9 +150,10 @@ __device__ __forceinline__ int window_origin(double q, double r, double l0, doub
 // raster points outside the raster give zeros).
 template <int KW>
 __device__ __forceinline__ void axis_rows(uint8_t* smem, int s_hi, int s_lo, int s_dhi, int s_dlo, int row,
-                                          bool in, float q, const float* nodes, const GridParams& P) {
+                                          bool in, float q, const float* nodes, const GridParams& P,
+                                          int c_begin = 0, int c_end = KW / 8) {
 #pragma unroll 1
-  for (int c = 0; c < KW / 8; ++c) {
+  for (int c = c_begin; c < c_end; ++c) {
     uint32_t hv[4], lv[4], dhv[4], dlv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -206,10 +210,10 @@ __device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_g
 constexpr int GTHREADS = 256;  // 8 warps: two per tensor-memory lane quadrant
 constexpr int TP = 33;         // padded row of the per-warp transpose buffers
 
-// Persistent: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// (tile = ty * ntx + tx).  The bulk stores of a tile drain while the next
-// tile's operands are generated; only their reads of shared memory are waited
-// for before the operands overwrite the boxes.
+// Persistent: each CTA takes a contiguous run of tiles in column-major order
+// (tile = tx * nty + ty), so that consecutive tiles mostly share a raster
+// column and, with KW = 32 and bulk stores, Ex and Ex' are generated once per
+// column.  The bulk stores of a tile drain while the next tile is computed.
 template <int KW>
 __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const float* __restrict__ xs,
                                                            const float* __restrict__ ys,
@@ -244,8 +248,18 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
   bool any = false;        // something was committed
 
   using L = Lay<KW>;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t k0 = (tile % ntx) * GT, l0 = (tile / ntx) * GT;
+  const int64_t nty = ntiles / ntx;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t_begin = (int64_t)blockIdx.x * per;
+  const int64_t t_end = (t_begin + per) < ntiles ? (t_begin + per) : ntiles;
+  int64_t ex_col = -1;  // raster column of tiles whose Ex, Ex' the operand tiles hold
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int64_t bx = tile / nty, by = tile % nty;
+    const int64_t k0 = bx * GT, l0 = by * GT;
+    // the transposing stores reuse the operand space, so Ex, Ex' stay only
+    // with the bulk stores
+    const bool keep_ex = L::SEPARATE && use_tma && bx == ex_col;
+    ex_col = (L::SEPARATE && use_tma) ? bx : -1;
     // boxes over the operands: the previous tile's boxes have been read
     if (!L::SEPARATE && use_tma && lane == 0) bulk_wait_read();
     if (t == 0) {
@@ -279,7 +293,13 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
     __syncthreads();
     // operands: threads 0-127 row t of Ex, Ex' (raster column k0 + t); threads
     // 128-255 row t - 128 of Ey, Ey' (raster row l0 + t - 128)
-    if (t < GT) {
+    if (keep_ex) {
+      // Ex, Ex' kept: two threads per row of Ey, Ey', half the chunks each
+      const int r = t >> 1, cb = (t & 1) * (KW / 16);
+      const int64_t l = l0 + r;
+      const float qy = (float)__dadd_rn(P.qy0, __dmul_rn((double)l, P.dq));
+      axis_rows<KW>(sm, L::EY_HI, L::EY_LO, L::EYD_HI, L::EYD_LO, r, l < P.nqy, qy, sy, P, cb, cb + KW / 16);
+    } else if (t < GT) {
       const int64_t k = k0 + t;
       const float qx = (float)__dadd_rn(P.qx0, __dmul_rn((double)k, P.dq));
       axis_rows<KW>(sm, L::EX_HI, L::EX_LO, L::EXD_HI, L::EXD_LO, t, k < P.nqx, qx, sx, P);

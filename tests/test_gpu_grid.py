@@ -143,3 +143,17 @@ def test_eval_grid_full_size_sampled_rows(N):
         ref = O.eval_grid(cfg["qx0"], y0, cfg["dq"], cfg["nqx"], 1, cfg["centers"], cfg["w"],
                           sigma=cfg["sigma"], cutoff_mult=cfg["cutoff_mult"], chunk=1024)
         check(h[l:l + 1], g[l:l + 1], ref)
+
+
+def test_eval_grid_many_tiles_sampled_rows(N):
+    # more tiles than CTAs, so that each persistent CTA runs through
+    # consecutive tiles of a raster column (Ex, Ex' kept between them) and
+    # across column boundaries; ragged last tiles, bulk stores (nqx % 4 == 0)
+    T, c, w = lattice_terrain(N, 100, 80, seed=6)
+    qx0, qy0, dq, nqx, nqy = -0.1, -0.1, 0.0041, 1752, 1400
+    h, g = T.eval_grid(qx0, qy0, dq, nqx, nqy)
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, nqy - 1], rng.choice(nqy, 28, replace=False)]))
+    for l in rows:
+        ref = O.eval_grid(qx0, qy0 + l * dq, dq, nqx, 1, c, w, sigma=SIGMA, cutoff_mult=CUT, chunk=1024)
+        check(h[l:l + 1], g[l:l + 1], ref)
