@@ -74,7 +74,7 @@ RASTER_TILE_FLOPS = 3 * (2 * 128 * 64 * 64 * 2 + 3 * 128 * 128 * 64 * 2)
 # dram__bytes_write.sum on `bench.py --steps 2 --warmup 3 --no-cpu
 # --eval-log2 20 --batch-patches 0 --c5-reps 0 --no-other`); below the 12 B per
 # point written because part of the output is still in L2 when the kernel ends
-RASTER_DRAM_BYTES = 921088.0 + 253018112.0
+RASTER_DRAM_BYTES = 1027328.0 + 253322752.0
 
 
 def raster_line(r, pk, pk_kind):
