@@ -17,10 +17,14 @@
 // are read back from tensor memory, split the same way and written to shared
 // memory as the K-major B operands of stage 2.
 //
-// Operand tiles are K-major with the 128-byte swizzle: one row of 64 bfloat16
-// per matrix row, written by the CTA's threads with 16-byte shared stores.
-// Thread 0 issues the MMAs and commits them to an mbarrier; every wait is
-// bounded, and a tile whose wait gives up is written as NaN.
+// Operand tiles are K-major, one row of kw bfloat16 per matrix row (64-byte
+// swizzle for kw = 32, 128-byte for kw = 64), written by the CTA's threads with
+// 16-byte shared stores.  Thread 0 issues the MMAs and commits them to an
+// mbarrier; every wait is bounded, and a tile whose wait gives up is written
+// as NaN.  The outputs leave through 128-byte swizzled 32 x 32 boxes and bulk
+// tensor stores (TMA) where the rows are 16-byte pitched, else through per-warp
+// transposes and row stores.  One persistent CTA per SM runs through a
+// contiguous run of tiles.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -136,7 +140,8 @@ struct GridParams {
 };
 
 // First lattice node of the window of a tile whose first raster coordinate
-// is q (one node of slack below; the host checks that 64 nodes cover the tile).
+// is q (one node of slack below; the host picks kw so that kw nodes cover the
+// tile).
 __device__ __forceinline__ int window_origin(double q, double r, double l0, double inv_lh, int n) {
   double t = (q - r - l0) * inv_lh - 0.5;
   if (!(t > -2.0)) t = -2.0;
