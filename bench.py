@@ -374,6 +374,12 @@ def run_ours(args, ws, rank, local):
         grad_host[: g.shape[0]].copy_(grad[: g.shape[0]], non_blocking=True)
         return g.numel() * 4 + b.numel() * 4, 7 * 8 + g.shape[0] * 12
 
+    # the same untimed pass as the device-resident run sizes this context's
+    # workspaces; the model is then reset to the prior
+    for k in range(nfr):
+        e2e_step(host[k])
+    T2.set_centers(centers)
+    torch.cuda.synchronize()
     for k in range(args.warmup):
         e2e_step(host[k])
     torch.cuda.synchronize()
