@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(GTHREADS) k_eval_grid_tc(GridParams P, const f
     }
     if (ok) {
       // T1^T (warps 0-3) and T2^T (warps 4-7) back from tensor memory, split and
-      // stored as the K-major B operands of stage 2 over the stage-1 A tiles
+      // stored as the K-major B operands of stage 2 (over the stage-1 A tiles
+      // for KW = 64, in their own space for KW = 32)
       const int which = warp >> 2;
       uint8_t* thi = sm + (which ? L::T2_HI : L::T1_HI);
       uint8_t* tlo = sm + (which ? L::T2_LO : L::T1_LO);
