@@ -291,6 +291,28 @@ def test_update_gaussian_moment_rows(N):
         assert rel_inf(T.weights().cpu().numpy(), st.w) < F64_TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_update_tiny_degenerate_cases(N, prec):
+    # one point (a handful of active centers), then a second frame that moves
+    # the block (departures); and a model with a single center
+    c1 = W.config1()
+    T = N.Terrain(rho=0.6, update_precision=prec)
+    T.set_centers(dev(c1.centers, torch.float64))
+    st = O.BlockState(c1.centers, 1e-3, O.WENDLAND, rho=0.6)
+    for pts in (np.array([[1.03, 2.07, 0.11]], np.float32), np.array([[3.1, 0.4, -0.05], [3.2, 0.5, 0.02]], np.float32)):
+        T.update(dev(pts), noise=0.02)
+        A = O.block_update(st, pts.astype(np.float64))
+        assert np.array_equal(T.active().cpu().numpy(), A)
+        assert rel_inf(T.weights().cpu().numpy(), st.w) < F64_TOL
+    c = np.array([[0.5, 0.5]])
+    T1 = N.Terrain(rho=0.6, update_precision=prec)
+    T1.set_centers(dev(c, torch.float64))
+    pts = np.array([[0.4, 0.6, 0.3], [0.7, 0.45, 0.2], [0.55, 0.5, 0.25]], np.float32)
+    T1.update(dev(pts), noise=0.02)
+    ref = O.batch_ridge(pts.astype(np.float64), c, 1e-3, O.WENDLAND, rho=0.6)
+    assert rel_inf(T1.weights().cpu().numpy(), ref) < F64_TOL
+
+
 def test_update_empty_and_untouched_are_noops(N):
     c1 = W.config1()
     T = N.Terrain(rho=0.6)
