@@ -128,8 +128,10 @@ rbf_status rbf_set_weights(rbf_ctx* ctx, const double* w, void* stream);
  * Active rows A = sorted union of the points' neighbour lists
  * (Eq. mfk_m_approx); only w_A and the covariance block P[A, A] change and
  * P[A, not A] becomes 0 (block-diagonal form of Eq. H_inverse_update).
- * Synchronizes once (to read the size of A).  RBF_ENOTSPD if a factorization
- * meets a non-positive pivot; the state is then left unchanged. */
+ * Synchronizes a few times per call to read data-dependent sizes (of A, of
+ * the leaving, staying and entering sets, of the coupled rows) and, before
+ * the commit, the status word.  RBF_ENOTSPD if a factorization meets a
+ * non-positive pivot; the state is then left unchanged. */
 rbf_status rbf_update(rbf_ctx* ctx, const float* pts, int64_t n, double noise, void* stream);
 
 /* h(q) and grad h(q) at Q query points (q: Q x 2 float32; h: Q float32;
