@@ -100,7 +100,9 @@ const char* rbf_last_error(void);
 
 /* Install M centers (cxy: M x 2 float64).  Resets the weights to the prior
  * w = 0 and the covariance to P = I / lambda, and rebuilds the center hash
- * grid (a counting sort of the centers by cell).  Synchronizes. */
+ * grid (a counting sort of the centers by cell).  The update's device
+ * workspaces are kept, so calling it again with the same centers restarts the
+ * recursion without new allocations.  Synchronizes. */
 rbf_status rbf_set_centers(rbf_ctx* ctx, const double* cxy, int64_t M, void* stream);
 
 /* Adaptive center selection (Sec. III-A): count the points (pts: n x 3, x and
