@@ -614,6 +614,11 @@ def soft_cost_backward(R, t, body_xyz, c_xy, w, kind, rho=0.6, sigma=0.04,
       dr_i/dw_j = -phi(||q_i - c_j||),
       dr_i/dc_j = +w_j g(||q_i - c_j||) (q_i - c_j)   (chain rule of Eq. manidolf_grad_detail),
     so dC/dw_j = -sum_i psi_i phi_ij and dC/dc_j = sum_i psi_i w_j g_ij (q_i - c_j).
+
+    Also returns, per center, the sums of the absolute values of those terms
+    (dw_abs, dc_abs) and of the terms without psi (phi_abs = sum_i |phi_ij|,
+    gq_abs = sum_i |w_j g_ij (q_i - c_j)|): the scales of a per-entry,
+    cancellation-safe tolerance.
     """
     fw = soft_cost(R, t, body_xyz, c_xy, w, kind, rho, sigma, cutoff_mult, delta,
                    wheel_offset, loss, lam_m)
@@ -623,6 +628,10 @@ def soft_cost_backward(R, t, body_xyz, c_xy, w, kind, rho=0.6, sigma=0.04,
     w = np.asarray(w, dtype=np.float64)
     dw = np.zeros(c.shape[0])
     dc = np.zeros((c.shape[0], 2))
+    dw_abs = np.zeros(c.shape[0])
+    dc_abs = np.zeros((c.shape[0], 2))
+    phi_abs = np.zeros(c.shape[0])
+    gq_abs = np.zeros((c.shape[0], 2))
     radius = support_radius_eval(kind, rho, sigma, cutoff_mult)
     chunk = 1024
     for s in range(0, q.shape[0], chunk):
@@ -640,4 +649,11 @@ def soft_cost_backward(R, t, body_xyz, c_xy, w, kind, rho=0.6, sigma=0.04,
         dw -= (ps * p).sum(0)
         dc[:, 0] += (ps * g * dx).sum(0) * w
         dc[:, 1] += (ps * g * dy).sum(0) * w
-    return dict(dw=dw, dc=dc, dpose6=fw["grad6"] * gout, cost=fw["cost"] * gout, fw=fw)
+        dw_abs += np.abs(ps * p).sum(0)
+        dc_abs[:, 0] += np.abs(ps * g * dx).sum(0) * np.abs(w)
+        dc_abs[:, 1] += np.abs(ps * g * dy).sum(0) * np.abs(w)
+        phi_abs += np.abs(p).sum(0)
+        gq_abs[:, 0] += np.abs(g * dx).sum(0) * np.abs(w)
+        gq_abs[:, 1] += np.abs(g * dy).sum(0) * np.abs(w)
+    return dict(dw=dw, dc=dc, dpose6=fw["grad6"] * gout, cost=fw["cost"] * gout, fw=fw,
+                dw_abs=dw_abs, dc_abs=dc_abs, phi_abs=phi_abs, gq_abs=gq_abs)

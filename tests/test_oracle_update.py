@@ -175,3 +175,23 @@ def test_sparse_ridge_equals_dense_ridge_and_inverse(kind):
     untouched = np.abs(Phi).sum(axis=0) == 0
     assert untouched.any() and np.all(w[untouched] == 0.0)
     assert Pk[-1, -1] == pytest.approx(1e3) and untouched[255]
+
+
+@pytest.mark.parametrize("form,joseph", [("info", False), ("woodbury", False), ("info", True)])
+def test_overlapping_frames_match_hand_derivation(form, joseph):
+    """Three frames whose active sets overlap: a center leaves and later
+    returns, reading back the variance stored when it left with its coupling
+    zeroed (block-diagonal form of Eq. H_inverse_update).  Expected w and P
+    after frames 2 and 3 are worked by hand in golden/block_overlap_hand.txt."""
+    from _fixtures import (OVERLAP_CENTERS, OVERLAP_FRAMES, OVERLAP_LAMBDA, OVERLAP_RHO,
+                           overlap_expected)
+    exp = overlap_expected()
+    st = O.BlockState(OVERLAP_CENTERS, OVERLAP_LAMBDA, O.WENDLAND, rho=OVERLAP_RHO)
+    actives = [[0, 1], [1, 2], [0, 1]]
+    for k, p in enumerate(OVERLAP_FRAMES, start=1):
+        A = O.block_update(st, p, form=form, joseph=joseph)
+        assert list(A) == actives[k - 1]
+        if k in exp:
+            w_ref, P_ref = exp[k]
+            assert np.max(np.abs(st.w - w_ref)) < 1e-14
+            assert np.max(np.abs(st.P.dense() - P_ref)) < 1e-14
