@@ -183,11 +183,29 @@ rbf_status rbf_soft_cost(rbf_ctx* ctx, const double* R, const double* t, const f
  * Jacobian row of point i (same perturbation as the gradient) and the
  * iteratively reweighted least-squares weight omega_i = psi(r_i) / r_i
  * (1 inside the Huber zone, delta / |r_i| outside; 2 lambda_M for the L2
- * loss).  An LM step solves (A + mu diag(A)) delta = -g on the host.
+ * loss).  rbf_lm_step takes the step from these on the device.
  * Asynchronous on stream.  Errors: RBF_EINVAL (negative n, null output,
  * null points with n > 0, non-finite pose), RBF_ESTATE (no centers). */
 rbf_status rbf_soft_cost_normal(rbf_ctx* ctx, const double* R, const double* t, const float* pts,
                                 int64_t n, double* out28, void* stream);
+
+/* One Levenberg-Marquardt step on the 6-DoF pose, entirely on the device
+ * (Sec. IV-C: the soft-constraint cost J_M is minimised by LM; Eq.
+ * manifold_derivative, Eq. manifold_grad_2 give the Jacobian).  Forms the
+ * cost, the gradient g and the Gauss-Newton matrix A at the pose (R, t) as
+ * rbf_soft_cost_normal does, solves (A + mu diag(A)) delta = -g in float64
+ * (Cholesky of the damped 6 x 6 matrix) and applies the step on the manifold:
+ * R_out = R Exp(delta_theta), t_out = t + delta_t.
+ * R: host 3 x 3 row-major float64; t: host 3 float64; pts: device n x 3
+ * float32 body-frame points; mu >= 0 the damping.
+ * out20 (device, 20 float64): [0..8] R_out row-major, [9..11] t_out,
+ * [12] the cost at the input pose, [13] 0, or 1 if the damped matrix was not
+ * positive definite (no step: R_out = R, t_out = t), [14..19] delta
+ * (theta, then t).  Asynchronous on stream.  Errors: RBF_EINVAL (negative n,
+ * null output, null points with n > 0, non-finite pose, mu < 0),
+ * RBF_ESTATE (no centers). */
+rbf_status rbf_lm_step(rbf_ctx* ctx, const double* R, const double* t, const float* pts, int64_t n,
+                       double mu, double* out20, void* stream);
 
 /* rbf_soft_cost that allocates nothing, for callers that cannot allocate
  * device memory while they run: a scan-matching loop with a hard per-frame
@@ -201,7 +219,9 @@ rbf_status rbf_soft_cost_normal(rbf_ctx* ctx, const double* R, const double* t, 
  * with up to 512 SMs; a launch that would need more blocks returns RBF_ERANGE.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: calls whose
+ * before any stream capture.  The address is cached per process and device;
+ * rbf_create drops the cached address of its device, so after a
+ * cudaDeviceReset create the contexts anew before calling this again.  All calls share the one array: calls whose
  * work overlaps on the GPU (other streams, other threads, other contexts)
  * race on it and must be serialized by the caller.  Each call overwrites
  * every slot it later reads, so nothing of an earlier call leaks into a
@@ -297,6 +317,28 @@ rbf_status rbf_profile_enable(rbf_ctx* ctx, int on);
  * contexts and threads; host counter, no synchronization). */
 rbf_status rbf_launch_count(int64_t* n);
 rbf_status rbf_profile_read(rbf_ctx* ctx, double* ms, double* work, int64_t* count, int reset);
+
+/* Test hooks.  They exist so that tests can drive the failure statuses from the
+ * host without faulting the GPU; the paper has no counterpart.  Each setting
+ * holds for the later calls on this context until it is set back to 0.
+ *  RBF_HOOK_DIAG_SHIFT (value: a finite float64): added to every diagonal
+ *    entry of the information matrix of the active block before rbf_update
+ *    factors it.  A large negative shift makes the block indefinite: the
+ *    update returns RBF_ENOTSPD and leaves the state unchanged.
+ *  RBF_HOOK_WAIT_LIMIT (value: iterations in [0, 1e12], 0 = the default of
+ *    about 4 million): limit of the bounded waits of the sync-free triangular
+ *    solves (FP64 solves, and the float32 substitution solves of the mixed
+ *    path used above inverse_max) and of the dataflow factorization.
+ *  RBF_HOOK_WAIT_NEVER (value 0 or 1): with 1 those waits wait for a flag
+ *    value that no block writes, so each runs out after the limit; the call
+ *    then returns RBF_ETIMEOUT and an update leaves the state unchanged.
+ *  RBF_HOOK_FACTOR_CHAIN (value 0 or 1): with 1 the mixed update factors
+ *    with one launch per block column (the path that serves batched patches
+ *    and stream capture) instead of the single dataflow launch, so that the
+ *    two can be compared on the same frames.
+ * RBF_EINVAL for an unknown hook or a value out of range.  Host only. */
+enum { RBF_HOOK_DIAG_SHIFT = 1, RBF_HOOK_WAIT_LIMIT = 2, RBF_HOOK_WAIT_NEVER = 3, RBF_HOOK_FACTOR_CHAIN = 4 };
+rbf_status rbf_test_hook(rbf_ctx* ctx, int32_t hook, double value);
 
 #ifdef __cplusplus
 }

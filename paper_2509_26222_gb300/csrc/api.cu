@@ -411,6 +411,35 @@ rbf_status build_center_grid(Ctx* c, cudaStream_t s) {
       if (ix >= 0 && ix < c->lat.nx) xs[ix] = (float)hc[2 * k];
       if (iy >= 0 && iy < c->lat.ny) ys[iy] = (float)hc[2 * k + 1];
     }
+    if (c->lat_rc > 0) {
+      // float-float node coordinates over the window range of the fixed-window
+      // kernel: the query's offset from its node is then exact to float32
+      // rounding of the offset itself, not of the coordinate
+      const int rc = c->lat_rc;
+      auto tab = [&](int n, double o, int axis) {
+        std::vector<float2> t((size_t)(n + 2 * rc + 1));
+        for (int i = -(rc + 1); i < n + rc; ++i) {
+          double v = o + ((double)i + 0.5) * c->lat.h;
+          float hi = (float)v;
+          t[(size_t)(i + rc + 1)] = make_float2(hi, (float)(v - (double)hi));
+        }
+        for (int64_t k = 0; k < M; ++k) {
+          double v = hc[2 * k + axis];
+          int i = (int)floor((v - o) / c->lat.h);
+          if (i >= 0 && i < n) {
+            float hi = (float)v;
+            t[(size_t)(i + rc + 1)] = make_float2(hi, (float)(v - (double)hi));
+          }
+        }
+        return t;
+      };
+      std::vector<float2> xt = tab(c->lat.nx, c->lat.x0, 0), yt = tab(c->lat.ny, c->lat.y0, 1);
+      RBF_TRY(c->lat_xhl.ensure(xt.size() * sizeof(float2)));
+      RBF_TRY(c->lat_yhl.ensure(yt.size() * sizeof(float2)));
+      RBF_CUDA(cudaMemcpyAsync(c->lat_xhl.p, xt.data(), xt.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+      RBF_CUDA(cudaMemcpyAsync(c->lat_yhl.p, yt.data(), yt.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+      RBF_CUDA(cudaStreamSynchronize(s));
+    }
     RBF_TRY(c->lat_xs.ensure(xs.size() * sizeof(float)));
     RBF_TRY(c->lat_ys.ensure(ys.size() * sizeof(float)));
     RBF_CUDA(cudaMemcpyAsync(c->lat_xs.p, xs.data(), xs.size() * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -579,8 +608,34 @@ extern "C" rbf_status rbf_create(const rbf_config* cfg, rbf_ctx** out) {
     delete c;
     return st;
   }
+  noalloc_forget(x->device);
   *out = c;
   return RBF_OK;
+}
+
+extern "C" rbf_status rbf_test_hook(rbf_ctx* c, int32_t hook, double value) {
+  RBF_TRY(check_ctx(c, false));
+  Ctx* x = C(c);
+  switch (hook) {
+    case RBF_HOOK_DIAG_SHIFT:
+      if (!isfinite(value)) return fail(RBF_EINVAL, "diagonal shift must be finite");
+      x->diag_shift = value;
+      return RBF_OK;
+    case RBF_HOOK_WAIT_LIMIT:
+      if (!(value >= 0 && value <= 1e12)) return fail(RBF_EINVAL, "wait limit must be in [0, 1e12]");
+      x->spin_limit = (long long)value;
+      return RBF_OK;
+    case RBF_HOOK_FACTOR_CHAIN:
+      if (value != 0.0 && value != 1.0) return fail(RBF_EINVAL, "factor-chain takes 0 or 1");
+      x->df_ok = value == 0.0;
+      return RBF_OK;
+    case RBF_HOOK_WAIT_NEVER:
+      if (value != 0.0 && value != 1.0) return fail(RBF_EINVAL, "wait-never takes 0 or 1");
+      x->wait_xor = value != 0.0 ? 0x40000000 : 0;
+      return RBF_OK;
+    default:
+      return fail(RBF_EINVAL, "unknown hook %d", hook);
+  }
 }
 
 extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
@@ -588,8 +643,8 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   Ctx* x = C(c);
   cudaDeviceSynchronize();
   batch_destroy(x);
-  Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2,
-                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Hs.rp, &x->Hs.col, &x->Hs.val, &x->Hs_next.rp, &x->Hs_next.col, &x->Hs_next.val, &x->Pg, &x->departed, &x->dflag, &x->sync_flags};
+  Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2, &x->lat_xhl, &x->lat_yhl,
+                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Hs.rp, &x->Hs.col, &x->Hs.val, &x->Hs_next.rp, &x->Hs_next.col, &x->Hs_next.val, &x->Pg, &x->departed, &x->dflag, &x->sync_flags, &x->df_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   for (auto& st : x->bs)

@@ -93,6 +93,8 @@ struct Ctx {
   Buf wlat;          // float32 lattice weights (lat.ny x lat.nx), 0 where no center
   Buf lat_xs, lat_ys; // float32 lattice node coordinates (fl32 of the float64 centers)
   Buf wlat2;          // padded pairs (W[j][i], W[j][i+1]) for the fixed-window kernel
+  Buf lat_xhl, lat_yhl; // float2 (hi, lo) node coordinates, hi + lo = the float64 coordinate, for
+                        // nodes -(lat_rc + 1) .. n + lat_rc - 1 of each axis (fixed-window kernel)
   int lat_rc = 0;     // window half-width in nodes (0: kernel not applicable)
 
   // recursive update state: the active block is held in information form
@@ -112,6 +114,9 @@ struct Ctx {
   cudaStream_t bs[2] = {};           // side streams of the block stage
   cudaEvent_t bev[3] = {};           // fork and joins of the block stage
   bool la_ok = true;                 // look-ahead factorization allowed
+  bool df_ok = false;                // one-launch dataflow factorization allowed
+  Buf df_flags;                      // its per-tile ready flags and abort word
+  uint32_t df_epoch = 0;
   cudaStream_t la_stream = nullptr;  // side stream of the look-ahead factorization
   cudaEvent_t la_ev[5] = {};          // panel ready (2), trailing done (2), join
   SpH Hs;            // compressed rows of H (mixed update)
@@ -127,6 +132,10 @@ struct Ctx {
   Buf dflag;         // int32[4]
   Buf sync_flags;    // int32 flags for sync-free triangular solves
   uint32_t epoch = 0;
+  // test hooks (rbf_test_hook): failure statuses driven from the host
+  long long spin_limit = 0;  // iterations of the solves' bounded waits (0: default)
+  int wait_xor = 0;          // nonzero: the solves wait for a flag value no block writes
+  double diag_shift = 0.0;   // added to the diagonal of H' before it is factored
 
   // scratch buffers, addressed by slot (slots 48.. are used by the scans)
   static constexpr int NSLOT = 96;
@@ -300,6 +309,8 @@ rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
                       cudaStream_t s, int64_t bw = BW_DENSE);
 void batch_destroy(Ctx* c);
+// forget the cached device address of rbf_soft_cost_noalloc's scratch on `dev`
+void noalloc_forget(int dev);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,
                          const double* b, double* r, cudaStream_t s);
 

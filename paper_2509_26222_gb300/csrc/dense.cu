@@ -212,7 +212,8 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __restrict__ L, int64_t ldl,
                                                               int64_t n, double* B, int64_t ldb,
                                                               int c0, int mc, bool transpose, int64_t bwb,
-                                                              int* flags, int epoch, int* status) {
+                                                              int* flags, int epoch, int* status,
+                                                              long long spin_limit, int wait_xor) {
   __shared__ double acc[NB][TS_MC + 1];
   __shared__ double Xs[NB][TS_MC + 1];
   __shared__ double Dinv[NB][NB + 1];
@@ -271,8 +272,8 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_syncfree(const double* __re
       }
       if (tid == 0) {
         long long it = 0;
-        while (ld_acquire(flags + cb) != epoch) {
-          if (++it > TS_SPIN_LIMIT) {
+        while (ld_acquire(flags + cb) != (epoch ^ wait_xor)) {
+          if (++it > spin_limit) {
             atomicOr(status, DEV_TIMEOUT);
             bail = 1;
             break;
@@ -343,8 +344,11 @@ rbf_status trsm_lower(Ctx* c, const double* L, int64_t n, int64_t ldl, double* B
     int epoch = (int)(++c->epoch);
     int c0i = (int)c0;
     int64_t bwb = bw >= n ? nblk : bw / NB + 2;
+    long long lim = c->spin_limit > 0 ? c->spin_limit : TS_SPIN_LIMIT;
+    int wx = c->wait_xor;
     void* args[] = {(void*)&L, (void*)&ldl, (void*)&n, (void*)&B, (void*)&ldb, (void*)&c0i,
-                    (void*)&mc, (void*)&transpose, (void*)&bwb, (void*)&flags, (void*)&epoch, (void*)&status};
+                    (void*)&mc, (void*)&transpose, (void*)&bwb, (void*)&flags, (void*)&epoch, (void*)&status,
+                    (void*)&lim, (void*)&wx};
     RBF_CUDA(cooperative_launch((const void*)k_trsm_syncfree, dim3((unsigned)grid),
                                          dim3(TS_THREADS), args, 0, s));
   }

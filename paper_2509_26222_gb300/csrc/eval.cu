@@ -273,6 +273,8 @@ struct LatWParams {
 
 template <int RC, bool SMEM>
 __global__ void __launch_bounds__(256) k_eval_lattice_win(LatWParams P, const float2* __restrict__ W2g,
+                                                          const float2* __restrict__ xt,
+                                                          const float2* __restrict__ yt,
                                                           const float2* __restrict__ q, int64_t Q,
                                                           float* __restrict__ h, float2* __restrict__ grad) {
   extern __shared__ float2 sw2[];
@@ -296,19 +298,31 @@ __global__ void __launch_bounds__(256) k_eval_lattice_win(LatWParams P, const fl
       if (grad) grad[qi] = make_float2(nan, nan);
       continue;
     }
-    float u = fmaf(p.x, P.inv_h, -P.u0), v = fmaf(p.y, P.inv_h, -P.v0);
+    const float ur = fmaf(p.x, P.inv_h, -P.u0), vr = fmaf(p.y, P.inv_h, -P.v0);
     // a query farther than RC + 1 nodes outside the lattice meets no support;
     // clamping it there keeps every offset below finite and the terms zero
-    u = fminf(fmaxf(u, (float)(-2 * RC - 2)), (float)(P.nx + 2 * RC + 1));
-    v = fminf(fmaxf(v, (float)(-2 * RC - 2)), (float)(P.ny + 2 * RC + 1));
+    float u = fminf(fmaxf(ur, (float)(-2 * RC - 2)), (float)(P.nx + 2 * RC + 1));
+    float v = fminf(fmaxf(vr, (float)(-2 * RC - 2)), (float)(P.ny + 2 * RC + 1));
     // window origin (node coordinates): floor(u) - RC + 1, clamped into the pad
     float fu = fminf(fmaxf(floorf(u), (float)(-RC - 1)), (float)(P.nx + RC - 1));
     float fv = fminf(fmaxf(floorf(v), (float)(-RC - 1)), (float)(P.ny + RC - 1));
     int ib = (int)fu + RC + 1;  // padded column of the window's first node
     int jb = (int)fv + RC + 1;
+    // offset of the query from node floor(u) in lattice units: u - fu loses the
+    // rounding of u (a few 1e-6 of a spacing far from the origin); the offset
+    // from the node's float-float coordinate is exact up to its own rounding
+    float fx = u - fu, fy = v - fv;
+    if (u == ur && fu == floorf(ur)) {
+      const float2 xn = __ldg(xt + ib);
+      fx = __fmul_rn(__fsub_rn(__fsub_rn(p.x, xn.x), xn.y), P.inv_h);
+    }
+    if (v == vr && fv == floorf(vr)) {
+      const float2 yn = __ldg(yt + jb);
+      fy = __fmul_rn(__fsub_rn(__fsub_rn(p.y, yn.x), yn.y), P.inv_h);
+    }
     // offsets of the window's first node, in units of the support radius
-    float du0 = (u - fu + (float)(RC - 1)) * P.invR;
-    float dv0 = (v - fv + (float)(RC - 1)) * P.invR;
+    float du0 = (fx + (float)(RC - 1)) * P.invR;
+    float dv0 = (fy + (float)(RC - 1)) * P.invR;
     u64 dup[RC], du2p[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) {
@@ -400,9 +414,13 @@ static unsigned grid_for(int64_t n, int threads, int dev, int per_sm) {
 // ---------------------------------------------------------------------------
 // Soft-constraint cost
 // ---------------------------------------------------------------------------
+// Pose of the body frame: q = R p + t is formed in float64, so that large
+// map-frame translations do not lose the residual's precision; the float32
+// copy of R serves the Jacobian rows.
 struct Pose {
-  float R[9];
-  float t[3];
+  double R[9];
+  double t[3];
+  float Rf[9];
 };
 
 struct CostParams {
@@ -418,12 +436,17 @@ __device__ __forceinline__ void point_terms(const EvalParams& P, const int32_t* 
                                             int64_t i, float& qx, float& qy, float& r, float& loss,
                                             float& psi, float J[6]) {
   float px = pts[3 * i], py = pts[3 * i + 1], pz = pts[3 * i + 2];
-  qx = fmaf(T.R[0], px, fmaf(T.R[1], py, fmaf(T.R[2], pz, T.t[0])));
-  qy = fmaf(T.R[3], px, fmaf(T.R[4], py, fmaf(T.R[5], pz, T.t[1])));
-  float qz = fmaf(T.R[6], px, fmaf(T.R[7], py, fmaf(T.R[8], pz, T.t[2])));
+  const double dpx = px, dpy = py, dpz = pz;
+  // q in float64; the evaluation point is its float32 rounding (the query type
+  // of the evaluation), q_z and the residual's difference stay float64
+  double qxd = fma(T.R[0], dpx, fma(T.R[1], dpy, fma(T.R[2], dpz, T.t[0])));
+  double qyd = fma(T.R[3], dpx, fma(T.R[4], dpy, fma(T.R[5], dpz, T.t[1])));
+  double qzd = fma(T.R[6], dpx, fma(T.R[7], dpy, fma(T.R[8], dpz, T.t[2])));
+  qx = (float)qxd;
+  qy = (float)qyd;
   float h, hx, hy;
   eval_one<KERNEL>(P, cell_start, xyw, qx, qy, h, hx, hy);
-  r = qz - CP.off - h;
+  r = (float)(qzd - (double)CP.off - (double)h);
   if (CP.loss == RBF_LOSS_HUBER) {
     float a = fabsf(r);
     loss = a <= CP.delta ? 0.5f * r * r : CP.delta * (a - 0.5f * CP.delta);
@@ -434,9 +457,9 @@ __device__ __forceinline__ void point_terms(const EvalParams& P, const int32_t* 
   }
   // dr/dq = a = (-hx, -hy, 1); dr/dtheta = p x (R^T a); dr/dt = a
   float ax = -hx, ay = -hy, az = 1.f;
-  float bx = T.R[0] * ax + T.R[3] * ay + T.R[6] * az;
-  float by = T.R[1] * ax + T.R[4] * ay + T.R[7] * az;
-  float bz = T.R[2] * ax + T.R[5] * ay + T.R[8] * az;
+  float bx = T.Rf[0] * ax + T.Rf[3] * ay + T.Rf[6] * az;
+  float by = T.Rf[1] * ax + T.Rf[4] * ay + T.Rf[7] * az;
+  float bz = T.Rf[2] * ax + T.Rf[5] * ay + T.Rf[8] * az;
   J[0] = py * bz - pz * by;
   J[1] = pz * bx - px * bz;
   J[2] = px * by - py * bx;
@@ -529,11 +552,12 @@ static rbf_status load_pose(const double* R, const double* t, Pose* T) {
   if (!R || !t) return fail(RBF_EINVAL, "null pose");
   for (int k = 0; k < 9; ++k) {
     if (!isfinite(R[k])) return fail(RBF_EINVAL, "non-finite rotation");
-    T->R[k] = (float)R[k];
+    T->R[k] = R[k];
+    T->Rf[k] = (float)R[k];
   }
   for (int k = 0; k < 3; ++k) {
     if (!isfinite(t[k])) return fail(RBF_EINVAL, "non-finite translation");
-    T->t[k] = (float)t[k];
+    T->t[k] = t[k];
   }
   return RBF_OK;
 }
@@ -715,7 +739,8 @@ extern "C" rbf_status rbf_eval(rbf_ctx* c, const float* q, int64_t Q, float* h, 
       RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm));
       if (occ < 1) occ = 1;
       unsigned nb = grid_for(Q, 256, x->device, occ);
-      kern<<<nb, 256, sm, s>>>(L, W2, (const float2*)q, Q, h, (float2*)grad);
+      kern<<<nb, 256, sm, s>>>(L, W2, x->lat_xhl.as<float2>(), x->lat_yhl.as<float2>(), (const float2*)q, Q, h,
+                               (float2*)grad);
       ::rbf::note_launch();
       RBF_CUDA(cudaGetLastError());
       return RBF_OK;
@@ -803,6 +828,100 @@ extern "C" rbf_status rbf_soft_cost_normal(rbf_ctx* c, const double* R, const do
   }
   StageTimer st(x, RBF_STAGE_SOFTCOST, s, 12.0 * (double)n);
   return soft_cost_forward(x, T, pts, n, nullptr, out28, out28 + 1, nullptr, s, out28 + 7);
+}
+
+// The Levenberg-Marquardt step of the pose from the cost, gradient and
+// Gauss-Newton matrix in v28 (the layout of rbf_soft_cost_normal): one thread
+// forms B = A + mu diag(A), factors it (Cholesky, float64), solves
+// B delta = -g and applies R Exp(delta_theta) (Rodrigues' formula), t + delta_t.
+__global__ void k_lm_solve(const double* __restrict__ v28, double mu, Pose T, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double B[6][6], g[6];
+  int q = 7;
+  for (int u = 0; u < 6; ++u)
+    for (int v = u; v < 6; ++v, ++q) B[u][v] = B[v][u] = v28[q];
+  for (int u = 0; u < 6; ++u) {
+    B[u][u] += mu * B[u][u];
+    g[u] = v28[1 + u];
+  }
+  bool ok = true;
+  for (int j = 0; j < 6 && ok; ++j) {
+    double d = B[j][j];
+    for (int k = 0; k < j; ++k) d -= B[j][k] * B[j][k];
+    if (!(d > 0.0)) {
+      ok = false;
+      break;
+    }
+    const double l = sqrt(d);
+    B[j][j] = l;
+    for (int i = j + 1; i < 6; ++i) {
+      double x = B[i][j];
+      for (int k = 0; k < j; ++k) x -= B[i][k] * B[j][k];
+      B[i][j] = x / l;
+    }
+  }
+  double dl[6] = {0, 0, 0, 0, 0, 0};
+  if (ok) {
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+      double x = -g[i];
+      for (int k = 0; k < i; ++k) x -= B[i][k] * y[k];
+      y[i] = x / B[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+      double x = y[i];
+      for (int k = i + 1; k < 6; ++k) x -= B[k][i] * dl[k];
+      dl[i] = x / B[i][i];
+    }
+  }
+  // E = Exp([theta]_x) = I + (sin a / a) K + ((1 - cos a) / a^2) K^2, a = |theta|
+  const double th[3] = {dl[0], dl[1], dl[2]};
+  const double a2 = th[0] * th[0] + th[1] * th[1] + th[2] * th[2];
+  const double a = sqrt(a2);
+  double c1 = 1.0, c2 = 0.5;
+  if (a > 1e-12) {
+    c1 = sin(a) / a;
+    c2 = (1.0 - cos(a)) / a2;
+  }
+  const double K[3][3] = {{0.0, -th[2], th[1]}, {th[2], 0.0, -th[0]}, {-th[1], th[0], 0.0}};
+  double E[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double k2 = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
+      E[i][j] = (i == j ? 1.0 : 0.0) + c1 * K[i][j] + c2 * k2;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      out[3 * i + j] = T.R[3 * i + 0] * E[0][j] + T.R[3 * i + 1] * E[1][j] + T.R[3 * i + 2] * E[2][j];
+  for (int i = 0; i < 3; ++i) out[9 + i] = T.t[i] + dl[3 + i];
+  out[12] = v28[0];
+  out[13] = ok ? 0.0 : 1.0;
+  for (int i = 0; i < 6; ++i) out[14 + i] = dl[i];
+}
+
+extern "C" rbf_status rbf_lm_step(rbf_ctx* c, const double* R, const double* t, const float* pts, int64_t n,
+                                  double mu, double* out20, void* stream) {
+  RBF_TRY(check_ctx(c, true));
+  if (n < 0) return fail(RBF_EINVAL, "negative n");
+  if (!out20) return fail(RBF_EINVAL, "null output");
+  if (n > 0 && !pts) return fail(RBF_EINVAL, "null points");
+  if (!(mu >= 0.0) || !isfinite(mu)) return fail(RBF_EINVAL, "mu must be finite and >= 0");
+  Pose T;
+  RBF_TRY(load_pose(R, t, &T));
+  Ctx* x = C(c);
+  cudaStream_t s = (cudaStream_t)stream;
+  Buf& v = x->scratch(19);
+  RBF_TRY(v.ensure(SC_NORMAL * sizeof(double)));
+  double* v28 = v.as<double>();
+  if (n == 0) {
+    RBF_CUDA(cudaMemsetAsync(v28, 0, SC_NORMAL * sizeof(double), s));
+  } else {
+    StageTimer st(x, RBF_STAGE_SOFTCOST, s, 12.0 * (double)n);
+    RBF_TRY(soft_cost_forward(x, T, pts, n, nullptr, v28, v28 + 1, nullptr, s, v28 + 7));
+  }
+  { k_lm_solve<<<1, 32, 0, s>>>(v28, mu, T, out20); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
 }
 
 extern "C" rbf_status rbf_soft_cost_backward(rbf_ctx* c, const double* R, const double* t,
@@ -906,6 +1025,14 @@ static rbf_status noalloc_scratch(int dev, double** out) {
   return RBF_OK;
 }
 
+// Drop the cached address of device `dev`: a context is being created there,
+// possibly after cudaDeviceReset invalidated every earlier device address.
+void noalloc_forget(int dev) {
+  if (dev < 0 || dev >= 256) return;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  g_noalloc_addr[dev] = nullptr;
+}
+
 }  // namespace rbf
 
 extern "C" rbf_status rbf_soft_cost_noalloc(rbf_ctx* c, const double* R, const double* t, const float* pts,
@@ -932,8 +1059,9 @@ extern "C" rbf_status rbf_soft_cost_noalloc(rbf_ctx* c, const double* R, const d
   RBF_TRY(noalloc_scratch(x->device, &part));
   EvalParams P = make_eval_params(x);
   CostParams CP = cost_params(x->cfg);
-  // every block writes all 8 of its partial-sum slots, and the reduction reads
-  // only the nb blocks of this launch: nothing left by an earlier call is used
+  // every block writes slots 0..6 of its row of 8 and the reduction reads only
+  // those 7 slots of the nb blocks of this launch: nothing left by an earlier
+  // call is used
   if (x->cfg.kernel == RBF_KERNEL_WENDLAND) {
     k_soft_cost<RBF_KERNEL_WENDLAND, 7><<<nb, SC_THREADS, 0, s>>>(
         P, x->cell_start.as<int32_t>(), x->sorted_xyw.as<float4>(), T, CP, pts, n, resid, part);

@@ -26,6 +26,16 @@ namespace rbf {
 
 constexpr int MB = 64;  // block size of the mixed factorization (= tc::KB)
 
+// flag protocol of the launches whose CTAs wait on one another
+__device__ __forceinline__ int ld_acq(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __global__ void k_mx_to_f32(const double* __restrict__ H, int64_t ldh, int64_t n, float* __restrict__ W,
                             int64_t ldw) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -332,6 +342,352 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The whole factorization in one persistent launch (dataflow over tiles).
+//
+// The band of H' is cut into 64 x 64 tiles (i, l), l <= i <= l + bwb, owned
+// round-robin (column-major order) by the CTAs of one cooperative launch.  A
+// tile's owner applies the updates W_il -= L_ik L_lk^T of the columns k < l
+// as their panels become ready, then finishes the tile:
+//   diagonal tile   D(l): L_ll = chol(W_ll), Z_ll = L_ll^{-1}  (-> Zd, W)
+//   panel tile      P(i,l): L_il = W_il Z_ll^T                  (-> W)
+// and publishes a per-tile ready flag (release store; readers acquire).  All
+// CTAs walk the same global task order
+//   stage s: U(., s+1; s)   D(s+1)   P(., s+1)   U(., l >= s+2; s)
+// -- the updates of the next block column first, so that its factorization
+// overlaps the rest of stage s (look-ahead) -- and every wait is for a task
+// earlier in that order, which some co-resident CTA finishes without waiting
+// on anything later: the launch cannot deadlock.  Waits are bounded; a wait
+// that runs out sets DEV_TIMEOUT and an abort word that ends every other
+// wait, and the CTAs return.
+//
+// Each tile's updates are applied in ascending k by its one owner, so the
+// result does not depend on timing.  The diagonal tile of W receives L_ll
+// (the solves read the diagonal blocks through Zd).
+// ---------------------------------------------------------------------------
+constexpr int DF_THREADS = 256;
+constexpr int DF_MAXOWN = 64;            // band tiles one CTA may own
+constexpr long long DF_SPIN = 1LL << 22;
+// dynamic shared memory (floats): two k-major staged tiles, or the diagonal
+// factorization's T, Z (64 x 65), Y (32 x 33), 1 / L_jj and the column buffer
+constexpr int DF_STAGE_FLOATS = 2 * 64 * 64;
+constexpr int DF_DIAG_FLOATS = 2 * MB * MXS_LD + 32 * 33 + MB + 64;
+constexpr size_t DF_SMEM = (size_t)(DF_STAGE_FLOATS > DF_DIAG_FLOATS ? DF_STAGE_FLOATS : DF_DIAG_FLOATS) *
+                           sizeof(float);
+
+struct DfParams {
+  float* W;
+  int64_t ldw, n;
+  int nb, bwb, ntiles;
+  float* Zd;
+  int* flags;  // ntiles ready flags, then the abort word
+  int epoch;
+  int* status;
+  long long spin;
+  int wait_xor;
+};
+
+// first band tile of block column l (column-major enumeration of the band)
+__device__ __forceinline__ int df_colstart(int l, int nb, int bwb) {
+  const int full = nb - bwb > 0 ? nb - bwb : 0;  // columns holding bwb + 1 tiles
+  if (l <= full) return l * (bwb + 1);
+  const int m = l - full, s0 = nb - full;
+  return full * (bwb + 1) + m * s0 - m * (m - 1) / 2;
+}
+
+// k-major staging with the float4 columns xor-swizzled by k: S[kk][r] holds
+// element (r, kk) of a 64 x 64 row-major tile
+__device__ __forceinline__ int df_swz(int kk, int r) { return kk * 64 + (r ^ (((kk >> 2) & 7) << 2)); }
+
+__device__ __forceinline__ void df_stage(float* S, const float* src, int64_t ld, int nr, int nc) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int q = tid + DF_THREADS * e, r = q >> 4, c4 = (q & 15) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < nr) {
+      const float* p = src + (int64_t)r * ld + c4;
+      if (c4 + 3 < nc) {
+        v = __ldcg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (c4 < nc) v.x = __ldcg(p);
+        if (c4 + 1 < nc) v.y = __ldcg(p + 1);
+        if (c4 + 2 < nc) v.z = __ldcg(p + 2);
+      }
+    }
+    S[df_swz(c4, r)] = v.x;
+    S[df_swz(c4 + 1, r)] = v.y;
+    S[df_swz(c4 + 2, r)] = v.z;
+    S[df_swz(c4 + 3, r)] = v.w;
+  }
+}
+
+// acc[u][v] += sum_kk A(r, kk) B(c, kk), r = 4 ty + u, c = 4 tx + v
+__device__ __forceinline__ void df_mma(float (&acc)[4][4], const float* As, const float* Bs, int ty, int tx) {
+#pragma unroll 8
+  for (int kk = 0; kk < 64; ++kk) {
+    const int sw = ((kk >> 2) & 7) << 2;
+    const float4 a = *reinterpret_cast<const float4*>(As + kk * 64 + ((ty * 4) ^ sw));
+    const float4 b = *reinterpret_cast<const float4*>(Bs + kk * 64 + ((tx * 4) ^ sw));
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+  }
+}
+
+// Bounded wait (thread 0) for flag idx; false if this or another CTA gave up.
+__device__ __forceinline__ bool df_wait(const DfParams& P, int idx, int* bail) {
+  if (threadIdx.x == 0) {
+    const int want = P.epoch ^ P.wait_xor;
+    long long it = 0;
+    while (ld_acq(P.flags + idx) != want) {
+      if (ld_acq(P.flags + P.ntiles) == P.epoch) {
+        *bail = 1;
+        break;
+      }
+      if (++it > P.spin) {
+        atomicOr(P.status, DEV_TIMEOUT);
+        st_rel(P.flags + P.ntiles, P.epoch);
+        *bail = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  __syncthreads();
+  return *bail == 0;
+}
+
+__device__ __forceinline__ void df_publish(const DfParams& P, int idx) {
+  __syncthreads();  // every thread's stores of the tile are done
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_rel(P.flags + idx, P.epoch);
+  }
+}
+
+__global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
+  extern __shared__ float dfs[];
+  __shared__ int own_i[DF_MAXOWN], own_l[DF_MAXOWN];
+  __shared__ int bail;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int nb = P.nb, bwb = P.bwb;
+  if (tid == 0) {
+    bail = 0;
+    int l = 0, no = 0;
+    for (int t = blockIdx.x; t < P.ntiles && no < DF_MAXOWN; t += gridDim.x, ++no) {
+      while (df_colstart(l + 1, nb, bwb) <= t) ++l;
+      own_l[no] = l;
+      own_i[no] = l + (t - df_colstart(l, nb, bwb));
+    }
+  }
+  __syncthreads();
+  int nown = 0;
+  for (int t = blockIdx.x; t < P.ntiles && nown < DF_MAXOWN; t += gridDim.x) ++nown;
+  float* As = dfs;
+  float* Bs = dfs + 64 * 64;
+  auto rows_of = [&](int b) { return (int)min((int64_t)64, P.n - (int64_t)b * 64); };
+  auto tile = [&](int i, int l) { return P.W + (int64_t)i * 64 * P.ldw + (int64_t)l * 64; };
+  auto tid_of = [&](int i, int l) { return df_colstart(l, nb, bwb) + (i - l); };
+
+  // U(i, l; k): W_il -= L_ik L_lk^T (the owner's tile in global memory)
+  auto update = [&](int i, int l, int k) -> bool {
+    if (!df_wait(P, tid_of(i, k), &bail)) return false;
+    if (i != l && !df_wait(P, tid_of(l, k), &bail)) return false;
+    const int ri = rows_of(i), rl = rows_of(l), ck = rows_of(k);
+    df_stage(As, tile(i, k), P.ldw, ri, ck);
+    if (i != l) df_stage(Bs, tile(l, k), P.ldw, rl, ck);
+    __syncthreads();
+    float acc[4][4] = {};
+    df_mma(acc, As, i != l ? Bs : As, ty, tx);
+    float* dst = tile(i, l);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = ty * 4 + u;
+      if (r >= ri) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int cc = tx * 4 + v;
+        if (cc < rl) __stcg(dst + (int64_t)r * P.ldw + cc, __ldcg(dst + (int64_t)r * P.ldw + cc) - acc[u][v]);
+      }
+    }
+    __syncthreads();  // the staged tiles are read before the next task restages them
+    return true;
+  };
+
+  // P(i, l): L_il = W_il Z_ll^T
+  auto panel = [&](int i, int l) -> bool {
+    if (!df_wait(P, tid_of(l, l), &bail)) return false;
+    const int ri = rows_of(i);
+    df_stage(As, tile(i, l), P.ldw, ri, 64);
+    df_stage(Bs, P.Zd + (int64_t)l * 64 * 64, 64, 64, 64);
+    __syncthreads();
+    float acc[4][4] = {};
+    df_mma(acc, As, Bs, ty, tx);
+    float* dst = tile(i, l);
+    const int cl = rows_of(l);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = ty * 4 + u;
+      if (r >= ri) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int cc = tx * 4 + v;
+        if (cc < cl) __stcg(dst + (int64_t)r * P.ldw + cc, acc[u][v]);
+      }
+    }
+    df_publish(P, tid_of(i, l));
+    return true;
+  };
+
+  // D(l): L_ll = chol(W_ll) and Z_ll = L_ll^{-1} (2 x 2 blocks of 32, as k_mx_step)
+  auto diag = [&](int l) {
+    float* T = dfs;
+    float* Z = T + MB * MXS_LD;
+    float* Y = Z + MB * MXS_LD;
+    float* rd = Y + 32 * 33;
+    float* col = rd + MB;
+    const int warp = tid >> 5;
+    const int kb = rows_of(l);
+    const float* src = tile(l, l);
+    for (int e = tid; e < MB * MB; e += DF_THREADS) {
+      const int i = e / MB, j = e % MB;
+      float v = (i < kb && j <= i) ? __ldcg(src + (int64_t)i * P.ldw + j) : 0.f;
+      if (i >= kb && i == j) v = 1.f;  // identity beyond a ragged last block
+      T[i * MXS_LD + j] = v;
+      Z[i * MXS_LD + j] = 0.f;
+    }
+    __syncthreads();
+    if (warp == 0) mx_chol32(T, rd, col, 0, P.status);
+    __syncthreads();
+    if (warp == 0) mx_inv32(T, Z, rd, 0);
+    else if (warp == 1) mx_l21(T, rd);
+    __syncthreads();
+    const int bi = tid >> 3, bj = tid & 7;
+    {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) {
+        const float lv = T[(32 + bi) * MXS_LD + t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, T[(32 + bj + 8 * q) * MXS_LD + t], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = bj + 8 * q;
+        if (j <= bi) T[(32 + bi) * MXS_LD + 32 + j] -= acc[q];
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      mx_chol32(T, rd, col, 32, P.status);
+      mx_inv32(T, Z, rd, 32);
+    }
+    {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) {
+        const float lv = T[(32 + bi) * MXS_LD + t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, Z[t * MXS_LD + bj + 8 * q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Y[bi * 33 + bj + 8 * q] = acc[q];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) {
+        const float zv = Z[(32 + bi) * MXS_LD + 32 + t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(zv, Y[t * 33 + bj + 8 * q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Z[(32 + bi) * MXS_LD + bj + 8 * q] = -acc[q];
+      __syncthreads();
+    }
+    float* zd = P.Zd + (int64_t)l * MB * MB;
+    float* dst = tile(l, l);
+    for (int e = tid; e < MB * MB; e += DF_THREADS) {
+      const int i = e / MB, j = e % MB;
+      __stcg(zd + e, Z[i * MXS_LD + j]);
+      if (i < kb && j < kb) __stcg(dst + (int64_t)i * P.ldw + j, j <= i ? T[i * MXS_LD + j] : 0.f);
+    }
+    df_publish(P, tid_of(l, l));
+  };
+
+  int p0 = 0;  // first owned tile of a block column >= s + 1
+  for (int s = -1; s < nb - 1; ++s) {
+    while (p0 < nown && own_l[p0] < s + 1) ++p0;
+    const int c = s + 1;
+    // U(., s+1; s): the next block column first
+    if (s >= 0)
+      for (int q = p0; q < nown && own_l[q] == c; ++q)
+        if (own_i[q] - s <= bwb && !update(own_i[q], c, s)) return;
+    // D(s+1), then P(., s+1)
+    for (int q = p0; q < nown && own_l[q] == c; ++q)
+      if (own_i[q] == c) diag(c);
+    for (int q = p0; q < nown && own_l[q] == c; ++q)
+      if (own_i[q] > c && !panel(own_i[q], c)) return;
+    // U(., l >= s+2; s)
+    if (s >= 0)
+      for (int q = p0; q < nown && own_l[q] <= s + bwb; ++q) {
+        const int l = own_l[q], i = own_i[q];
+        if (l >= s + 2 && i - s <= bwb && !update(i, l, s)) return;
+      }
+  }
+}
+
+// The factorization by k_chol_df.  Returns RBF_ERANGE (and launches nothing)
+// when the band has more tiles than the co-resident CTAs can own.
+static rbf_status potrf_df(Ctx* c, int64_t n, float* W, int64_t ldw, float* Zd, cudaStream_t s, int64_t bw) {
+  const int nb = (int)((n + MB - 1) / MB);
+  int bwb = nb - 1;
+  if (bw < n) {
+    int64_t b = (bw + MB - 1) / MB + 1;
+    if (b < bwb) bwb = (int)b;
+  }
+  const int full = nb - bwb > 0 ? nb - bwb : 0;
+  const int m = nb - full, s0 = nb - full;
+  const int64_t ntiles = (int64_t)full * (bwb + 1) + (int64_t)m * s0 - (int64_t)m * (m - 1) / 2;
+  static int max_blocks[64] = {0};
+  const int dev = c->device & 63;
+  if (!max_blocks[dev]) {
+    int per_sm = 0, sms = 0;
+    RBF_CUDA(cudaFuncSetAttribute(k_chol_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DF_SMEM));
+    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_df, DF_THREADS, DF_SMEM));
+    RBF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    max_blocks[dev] = (per_sm > 0 ? 1 : 0) * sms;  // one CTA per SM
+  }
+  int64_t grid = ntiles < max_blocks[dev] ? ntiles : max_blocks[dev];
+  if (grid < 1 || (ntiles + grid - 1) / grid > DF_MAXOWN) return RBF_ERANGE;
+  if (c->df_flags.bytes < (size_t)(ntiles + 1) * sizeof(int)) {
+    RBF_TRY(c->df_flags.ensure((size_t)(ntiles + 1) * sizeof(int)));
+    RBF_CUDA(cudaMemsetAsync(c->df_flags.p, 0, c->df_flags.bytes, s));
+    c->df_epoch = 0;
+  }
+  DfParams P;
+  P.W = W;
+  P.ldw = ldw;
+  P.n = n;
+  P.nb = nb;
+  P.bwb = bwb;
+  P.ntiles = (int)ntiles;
+  P.Zd = Zd;
+  P.flags = c->df_flags.as<int>();
+  P.epoch = (int)(++c->df_epoch & 0x3fffffff);
+  if (P.epoch == 0) P.epoch = (int)(++c->df_epoch & 0x3fffffff);
+  P.status = c->dflag.as<int>();
+  P.spin = c->spin_limit > 0 ? c->spin_limit : DF_SPIN;
+  P.wait_xor = c->wait_xor;
+  void* args[] = {(void*)&P};
+  StageTimer st(c, RBF_STAGE_PANEL, s, (double)n * n * n / 3.0);
+  RBF_CUDA(cooperative_launch((const void*)k_chol_df, dim3((unsigned)grid), dim3(DF_THREADS), args, DF_SMEM, s));
+  return RBF_OK;
+}
+
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
                        cudaStream_t s, int64_t bw) {
   if (n <= 0) return RBF_OK;
@@ -340,6 +696,12 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
     int64_t tot = n * n;
     { k_mx_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, ldh, n, W, ldw); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
+  }
+  cudaStreamCaptureStatus cap0 = cudaStreamCaptureStatusNone;
+  RBF_CUDA(cudaStreamIsCapturing(s, &cap0));
+  if (c->la_ok && c->df_ok && cap0 == cudaStreamCaptureStatusNone) {
+    rbf_status st = potrf_df(c, n, W, ldw, Zd, s, bw);
+    if (st != RBF_ERANGE) return st;
   }
   // bf16 slices of the panel, two sets (panel k is read by the trailing
   // update of step k while step k + 1 writes the next one)
@@ -424,19 +786,11 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
 constexpr int T32_MC = 160;
 constexpr long long T32_SPIN = 1LL << 22;
 
-__device__ __forceinline__ int ld_acq(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_rel(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int64_t ldl, int64_t n,
                                                 const float* __restrict__ Zd, float* B, int64_t ldb, int c0,
                                                 int mc, bool transpose, int bwb, int* flags, int epoch,
-                                                int* status) {
+                                                int* status, long long spin_limit, int wait_xor) {
   // acc and Xs (64 x (T32_MC + 1) floats each) in dynamic shared memory
   extern __shared__ float t32_dyn[];
   float (*acc)[T32_MC + 1] = reinterpret_cast<float (*)[T32_MC + 1]>(t32_dyn);
@@ -474,8 +828,8 @@ __global__ void __launch_bounds__(256) k_trsm32(const float* __restrict__ L, int
       }
       if (tid == 0) {
         long long it = 0;
-        while (ld_acq(flags + cb) != epoch) {
-          if (++it > T32_SPIN) {
+        while (ld_acq(flags + cb) != (epoch ^ wait_xor)) {
+          if (++it > spin_limit) {
             atomicOr(status, DEV_TIMEOUT);
             bail = 1;
             break;
@@ -545,8 +899,11 @@ rbf_status trsm32(Ctx* c, const float* L, int64_t n, int64_t ldl, const float* Z
     int epoch = (int)(++c->epoch);
     int c0i = (int)c0;
     int bwb = (int)(bw >= n ? nblk : bw / MB + 2);
+    long long lim = c->spin_limit > 0 ? c->spin_limit : T32_SPIN;
+    int wx = c->wait_xor;
     void* args[] = {(void*)&L, (void*)&ldl, (void*)&n, (void*)&Zd, (void*)&B, (void*)&ldb, (void*)&c0i,
-                    (void*)&mc, (void*)&transpose, (void*)&bwb, (void*)&flags, (void*)&epoch, (void*)&status};
+                    (void*)&mc, (void*)&transpose, (void*)&bwb, (void*)&flags, (void*)&epoch, (void*)&status,
+                    (void*)&lim, (void*)&wx};
     StageTimer st(c, RBF_STAGE_TRSM32, s, (double)n * (double)n * (double)mc);
     RBF_CUDA(cooperative_launch((const void*)k_trsm32, dim3((unsigned)grid), dim3(256), args, dyn, s));
   }

@@ -472,6 +472,12 @@ __global__ void k_w_add(double* __restrict__ w, const int32_t* __restrict__ A, i
   if (l < a) w[A[l]] += delta[l];
 }
 
+// test hook: H'[l][l] += shift
+__global__ void k_diag_add(double* __restrict__ H, int64_t ld, int64_t n, double shift) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) H[l * ld + l] += shift;
+}
+
 __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
@@ -879,6 +885,10 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
                                       Hn.as<double>(), ld, u.as<double>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     c->gacc_dirty = false;
+  }
+  if (c->diag_shift != 0.0) {
+    { k_diag_add<<<nblk(an), 256, 0, s>>>(Hn.as<double>(), ld, an, c->diag_shift); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
   }
   // Until a center has left some block there is no Schur-complement fill and
   // H' has the band structure of m~ m~^T: read its half-bandwidth then, and

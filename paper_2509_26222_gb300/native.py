@@ -8,10 +8,7 @@ fallback.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
-
-import numpy as np
 
 import torch
 
@@ -104,7 +101,11 @@ _SIGS = {
     "rbf_launch_count": [ctypes.POINTER(_I64)],
     "rbf_soft_cost_normal": [_P, _P, _P, _P, _I64, _P, _P],
     "rbf_batch_update_eval": [_P, _P, ctypes.c_int32, _P],
+    "rbf_lm_step": [_P, _P, _P, _P, _I64, _D, _P, _P],
+    "rbf_test_hook": [_P, ctypes.c_int32, _D],
+    "rbf_soft_cost_noalloc": [_P, _P, _P, _P, _I64, _P, _P, _P, _P],
 }
+HOOK_DIAG_SHIFT, HOOK_WAIT_LIMIT, HOOK_WAIT_NEVER, HOOK_FACTOR_CHAIN = 1, 2, 3, 4
 
 STAGES = ["neighbors", "assembly", "block", "panel", "trailing", "solve", "eval", "softcost", "backward",
           "trsm32", "inverse", "invapply", "covblock", "schur", "enter", "evalgrid"]
@@ -120,16 +121,6 @@ def _out_tensor(t, n, device, dtype=torch.float32):
     if t.numel() < n:
         raise ValueError(f"output buffer holds {t.numel()} values, {n} needed")
     return t
-
-
-def _so3_exp(v):
-    """Rotation matrix exp([v]_x) (Rodrigues)."""
-    v = np.asarray(v, dtype=np.float64)
-    a = float(np.linalg.norm(v))
-    K = np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
-    if a < 1e-12:
-        return np.eye(3) + K
-    return np.eye(3) + math.sin(a) / a * K + (1.0 - math.cos(a)) / (a * a) * (K @ K)
 
 
 def launch_count() -> int:
@@ -323,16 +314,22 @@ class Terrain:
         A = A + A.T - torch.diag(torch.diagonal(A))
         return buf[0], buf[1:7], A
 
-    def lm_step(self, R, t, pts, mu=1e-3):
-        """One Levenberg-Marquardt step on the pose: solves (A + mu diag(A)) d = -g
-        (6 x 6, host) and returns the updated (R Exp(d_theta), t + d_t) and the cost
-        at the input pose."""
-        cost, g, A = self.soft_cost_normal(R, t, pts)
-        A = A.cpu().numpy()
-        g = g.cpu().numpy()
-        d = np.linalg.solve(A + mu * np.diag(np.diag(A)), -g)
-        R = np.asarray(R, dtype=np.float64)
-        return R @ _so3_exp(d[:3]), np.asarray(t, dtype=np.float64) + d[3:], float(cost)
+    def lm_step(self, R, t, pts, mu=1e-3, out=None):
+        """One Levenberg-Marquardt step on the pose (rbf_lm_step, on the device).
+        Returns (R_out, t_out, cost at the input pose) as host float64 arrays;
+        the full 20-value result stays in ``out`` when given."""
+        R = torch.as_tensor(R, dtype=torch.float64).cpu().contiguous()
+        t = torch.as_tensor(t, dtype=torch.float64).cpu().contiguous()
+        p = _dev_tensor(pts, torch.float32, 3)
+        buf = _out_tensor(out, 20, p.device, torch.float64) if out is not None else torch.empty(
+            20, dtype=torch.float64, device=p.device)
+        _check(self.lib.rbf_lm_step(self._h, _ptr(R), _ptr(t), _ptr(p), p.shape[0], float(mu), _ptr(buf), _stream()))
+        h = buf.cpu().numpy()
+        return h[:9].reshape(3, 3).copy(), h[9:12].copy(), float(h[12])
+
+    def test_hook(self, hook, value):
+        """Set a test hook of the context (rbf_test_hook)."""
+        _check(self.lib.rbf_test_hook(self._h, int(hook), float(value)))
 
     def soft_cost_backward(self, R, t, pts, gout=None):
         R = torch.as_tensor(R, dtype=torch.float64).cpu().contiguous()
@@ -426,11 +423,19 @@ class SoftCost(torch.autograd.Function):
     float64), c (M x 2, device, float64), pose6 (6, device, float64)).  ``w``,
     ``c`` and ``pose6`` are the differentiable leaves: the weights, the centers
     and a zero pose increment [theta, t] applied as R Exp(theta), t + dt.  The
-    terrain must hold these weights and centers (they are read from it).
+    kernels read the weights and centers from the terrain, so ``w`` and ``c``
+    must equal the terrain's own (checked: ValueError otherwise), and
+    ``pose6`` must be zero (the pose is R, t).
     """
 
     @staticmethod
     def forward(ctx, terrain, R, t, pts, w, c, pose6):
+        if not torch.equal(w.detach().to(torch.float64).reshape(-1), terrain.weights()):
+            raise ValueError("w differs from the terrain's weights: install it with set_weights first")
+        if not torch.equal(c.detach().to(torch.float64).reshape(-1, 2), terrain.centers()):
+            raise ValueError("c differs from the terrain's centers: install them with set_centers first")
+        if torch.count_nonzero(pose6.detach()).item() != 0:
+            raise ValueError("pose6 must be the zero increment; pass the pose as R, t")
         cost, _, _ = terrain.soft_cost(R, t, pts)
         ctx.terrain = terrain
         ctx.R, ctx.t = R, t

@@ -2,7 +2,7 @@
 device memory while they run (deadline-bound scan-matching loops, processes
 that reserve their GPU memory at start-up): its results must equal those of
 rbf_soft_cost, through the C ABI, on consecutive calls that share its fixed
-scratch array.  This file is collected last on purpose."""
+scratch array (a large call followed by a small one).  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -29,11 +29,13 @@ def test_noalloc_soft_cost_matches_regular_entry_point():
     T = N.Terrain(rho=0.6, huber_delta=cfg["delta"])
     T.set_centers(torch.tensor(cfg["centers"], device="cuda"))
     T.set_weights(torch.tensor(cfg["w"], device="cuda"))
-    pts = torch.tensor(cfg["body"].astype(np.float32), device="cuda")
-    n = pts.shape[0]
+    pts_all = torch.tensor(cfg["body"].astype(np.float32), device="cuda")
     R = np.ascontiguousarray(cfg["R"], dtype=np.float64)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for call, dt in enumerate((0.0, 0.07)):
+    # a large call, then a much smaller one (a few blocks): the reduction of the
+    # second must read only its own blocks, not slots the first one left
+    for call, (dt, n) in enumerate(((0.0, pts_all.shape[0]), (0.07, 700))):
+        pts = pts_all[:n].contiguous()
         t = np.ascontiguousarray(cfg["t"] + np.array([0.0, dt, -dt]), dtype=np.float64)
         ref = torch.empty(7, dtype=torch.float64, device="cuda")
         ref_r = torch.empty(n, dtype=torch.float32, device="cuda")
