@@ -452,6 +452,7 @@ rbf_status build_center_grid(Ctx* c, cudaStream_t s) {
 rbf_status reset_update_state(Ctx* c) {
   c->a = 0;
   c->pg_on = false;
+  c->arena_used = 0;
   c->zi_valid = false;
   c->bw_lf = BW_DENSE;
   c->Hs.valid = false;
@@ -472,6 +473,8 @@ rbf_status install_centers(Ctx* c, const double* cxy, int64_t M, cudaStream_t s)
   RBF_CUDA(cudaMemsetAsync(c->g2l.p, 0xff, (size_t)M * sizeof(int32_t), s));
   RBF_TRY(c->departed.ensure((size_t)M * sizeof(int32_t)));
   RBF_CUDA(cudaMemsetAsync(c->departed.p, 0, (size_t)M * sizeof(int32_t), s));
+  RBF_TRY(c->blkref.ensure((size_t)M * sizeof(BlkRef)));
+  RBF_CUDA(cudaMemsetAsync(c->blkref.p, 0xff, (size_t)M * sizeof(BlkRef), s));  // base = -1: never left
   c->M = M;
   RBF_TRY(reset_update_state(c));
   rbf_status st = build_center_grid(c, s);
@@ -644,7 +647,7 @@ extern "C" rbf_status rbf_destroy(rbf_ctx* c) {
   cudaDeviceSynchronize();
   batch_destroy(x);
   Buf* bufs[] = {&x->c64, &x->w, &x->cell_start, &x->sorted_id, &x->sorted_xyw, &x->wlat, &x->lat_xs, &x->lat_ys, &x->wlat2, &x->lat_xhl, &x->lat_yhl,
-                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Hs.rp, &x->Hs.col, &x->Hs.val, &x->Hs_next.rp, &x->Hs_next.col, &x->Hs_next.val, &x->Pg, &x->departed, &x->dflag, &x->sync_flags, &x->df_flags};
+                 &x->A, &x->g2l, &x->H, &x->L, &x->Lf, &x->Zd, &x->Zi, &x->Hs.rp, &x->Hs.col, &x->Hs.val, &x->Hs_next.rp, &x->Hs_next.col, &x->Hs_next.val, &x->blkref, &x->arena, &x->departed, &x->dflag, &x->sync_flags, &x->df_flags};
   for (Buf* b : bufs) b->release();
   for (Buf& b : x->ws) b.release();
   for (auto& st : x->bs)

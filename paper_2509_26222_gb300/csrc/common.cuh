@@ -75,6 +75,14 @@ struct Lattice {
   int nx, ny;
 };
 
+// Where the covariance of a center outside the active block is stored: the
+// block of its latest departure starts at arena[base] (d x d, row-major) and
+// the center is its row pos; base < 0: the center never left a block.
+struct BlkRef {
+  long long base;
+  int d, pos;
+};
+
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
@@ -114,7 +122,7 @@ struct Ctx {
   cudaStream_t bs[2] = {};           // side streams of the block stage
   cudaEvent_t bev[3] = {};           // fork and joins of the block stage
   bool la_ok = true;                 // look-ahead factorization allowed
-  bool df_ok = false;                // one-launch dataflow factorization allowed
+  bool df_ok = true;                 // one-launch dataflow factorization allowed
   Buf df_flags;                      // its per-tile ready flags and abort word
   uint32_t df_epoch = 0;
   cudaStream_t la_stream = nullptr;  // side stream of the look-ahead factorization
@@ -124,9 +132,15 @@ struct Ctx {
   int64_t ldw = 0;
   int refine_sweeps = 3;      // float64 refinement sweeps of the weight solve (mixed precision)
   int refine_sweeps_cov = 2;  // ... of the covariance solves (leaving centers, rbf_get_cov)
-  Buf Pg;            // float64 M x M covariance of the centers outside the block
+  // Covariance of the centers outside the active block.  It is block
+  // diagonal: every departure stores its d x d block P_DD once, in an arena,
+  // and each center that left refers to the block of its latest departure
+  // (BlkRef); two centers are coupled only if they refer to the same block.
+  Buf blkref;        // BlkRef M
+  Buf arena;         // float64 blocks, arena_used entries in use
+  int64_t arena_used = 0;
   Buf departed;      // int32 M: 1 once a center has left an active block (its P may be coupled)
-  bool pg_on = false;
+  bool pg_on = false;  // some center has left a block
 
   // device status word + epoch counter for flag-based waits
   Buf dflag;         // int32[4]

@@ -367,13 +367,17 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
 // ---------------------------------------------------------------------------
 constexpr int DF_THREADS = 256;
 constexpr int DF_MAXOWN = 64;            // band tiles one CTA may own
+constexpr int DF_NACC = 8;               // owned tiles whose running sums stay in shared memory
+constexpr int64_t DF_NMAX = 4096;        // largest block factored by the dataflow launch
 constexpr long long DF_SPIN = 1LL << 22;
 // dynamic shared memory (floats): two k-major staged tiles, or the diagonal
-// factorization's T, Z (64 x 65), Y (32 x 33), 1 / L_jj and the column buffer
+// factorization's T, Z (64 x 65), Y (32 x 33), 1 / L_jj and the column buffer;
+// then DF_NACC tile accumulators (64 x 64, row-major); then the bitmap of the
+// ready flags this CTA has already seen
 constexpr int DF_STAGE_FLOATS = 2 * 64 * 64;
 constexpr int DF_DIAG_FLOATS = 2 * MB * MXS_LD + 32 * 33 + MB + 64;
-constexpr size_t DF_SMEM = (size_t)(DF_STAGE_FLOATS > DF_DIAG_FLOATS ? DF_STAGE_FLOATS : DF_DIAG_FLOATS) *
-                           sizeof(float);
+constexpr int DF_R0 = DF_STAGE_FLOATS > DF_DIAG_FLOATS ? DF_STAGE_FLOATS : DF_DIAG_FLOATS;
+constexpr size_t DF_SMEM_BASE = (size_t)(DF_R0 + DF_NACC * 64 * 64) * sizeof(float);
 
 struct DfParams {
   float* W;
@@ -399,6 +403,7 @@ __device__ __forceinline__ int df_colstart(int l, int nb, int bwb) {
 // element (r, kk) of a 64 x 64 row-major tile
 __device__ __forceinline__ int df_swz(int kk, int r) { return kk * 64 + (r ^ (((kk >> 2) & 7) << 2)); }
 
+// from global memory (rows < nr, columns < nc; zeros elsewhere)
 __device__ __forceinline__ void df_stage(float* S, const float* src, int64_t ld, int nr, int nc) {
   const int tid = threadIdx.x;
 #pragma unroll
@@ -422,6 +427,11 @@ __device__ __forceinline__ void df_stage(float* S, const float* src, int64_t ld,
   }
 }
 
+// from a row-major 64 x 64 accumulator in shared memory
+__device__ __forceinline__ void df_stage_smem(float* S, const float* A) {
+  for (int e = threadIdx.x; e < 64 * 64; e += DF_THREADS) S[df_swz(e & 63, e >> 6)] = A[e];
+}
+
 // acc[u][v] += sum_kk A(r, kk) B(c, kk), r = 4 ty + u, c = 4 tx + v
 __device__ __forceinline__ void df_mma(float (&acc)[4][4], const float* As, const float* Bs, int ty, int tx) {
 #pragma unroll 8
@@ -437,23 +447,32 @@ __device__ __forceinline__ void df_mma(float (&acc)[4][4], const float* As, cons
   }
 }
 
-// Bounded wait (thread 0) for flag idx; false if this or another CTA gave up.
-__device__ __forceinline__ bool df_wait(const DfParams& P, int idx, int* bail) {
-  if (threadIdx.x == 0) {
-    const int want = P.epoch ^ P.wait_xor;
-    long long it = 0;
-    while (ld_acq(P.flags + idx) != want) {
-      if (ld_acq(P.flags + P.ntiles) == P.epoch) {
-        *bail = 1;
-        break;
+// Bounded waits for the ready flags a and b (b < 0: none), thread 0 for a and
+// thread 32 for b; flags seen ready once are remembered in `seen`.  False if
+// this or another CTA gave up.
+__device__ __forceinline__ bool df_wait2(const DfParams& P, unsigned* seen, int a, int b, int* bail) {
+  const int tid = threadIdx.x;
+  if (tid == 0 || tid == 32) {
+    const int idx = tid == 0 ? a : b;
+    if (idx >= 0 && !(seen[idx >> 5] & (1u << (idx & 31)))) {
+      const int want = P.epoch ^ P.wait_xor;
+      long long it = 0;
+      bool ok = true;
+      while (ld_acq(P.flags + idx) != want) {
+        if (ld_acq(P.flags + P.ntiles) == P.epoch) {
+          ok = false;
+          break;
+        }
+        if (++it > P.spin) {
+          atomicOr(P.status, DEV_TIMEOUT);
+          st_rel(P.flags + P.ntiles, P.epoch);
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
       }
-      if (++it > P.spin) {
-        atomicOr(P.status, DEV_TIMEOUT);
-        st_rel(P.flags + P.ntiles, P.epoch);
-        *bail = 1;
-        break;
-      }
-      __nanosleep(32);
+      if (ok) atomicOr(seen + (idx >> 5), 1u << (idx & 31));
+      else *bail = 1;
     }
   }
   __syncthreads();
@@ -472,6 +491,9 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
   extern __shared__ float dfs[];
   __shared__ int own_i[DF_MAXOWN], own_l[DF_MAXOWN];
   __shared__ int bail;
+  float* R0 = dfs;
+  float* ACC = dfs + DF_R0;
+  unsigned* seen = reinterpret_cast<unsigned*>(ACC + DF_NACC * 64 * 64);
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int nb = P.nb, bwb = P.bwb;
   if (tid == 0) {
@@ -483,34 +505,61 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
       own_i[no] = l + (t - df_colstart(l, nb, bwb));
     }
   }
+  for (int e = tid; e < (P.ntiles + 31) / 32; e += DF_THREADS) seen[e] = 0u;
   __syncthreads();
   int nown = 0;
   for (int t = blockIdx.x; t < P.ntiles && nown < DF_MAXOWN; t += gridDim.x) ++nown;
-  float* As = dfs;
-  float* Bs = dfs + 64 * 64;
+  float* As = R0;
+  float* Bs = R0 + 64 * 64;
   auto rows_of = [&](int b) { return (int)min((int64_t)64, P.n - (int64_t)b * 64); };
   auto tile = [&](int i, int l) { return P.W + (int64_t)i * 64 * P.ldw + (int64_t)l * 64; };
   auto tid_of = [&](int i, int l) { return df_colstart(l, nb, bwb) + (i - l); };
+  // running sums of the first DF_NACC owned tiles live in shared memory
+  const int nacc = nown < DF_NACC ? nown : DF_NACC;
+  for (int q = 0; q < nacc; ++q) {
+    const int ri = rows_of(own_i[q]), rl = rows_of(own_l[q]);
+    const float* src = tile(own_i[q], own_l[q]);
+    float* A = ACC + q * 64 * 64;
+    for (int e = tid; e < 64 * 64; e += DF_THREADS) {
+      const int r = e >> 6, cc = e & 63;
+      A[e] = (r < ri && cc < rl) ? __ldcg(src + (int64_t)r * P.ldw + cc) : 0.f;
+    }
+  }
+  __syncthreads();
 
-  // U(i, l; k): W_il -= L_ik L_lk^T (the owner's tile in global memory)
-  auto update = [&](int i, int l, int k) -> bool {
-    if (!df_wait(P, tid_of(i, k), &bail)) return false;
-    if (i != l && !df_wait(P, tid_of(l, k), &bail)) return false;
+  // U(i, l; k): tile q -= L_ik L_lk^T
+  auto update = [&](int q, int k) -> bool {
+    const int i = own_i[q], l = own_l[q];
+    if (!df_wait2(P, seen, tid_of(i, k), i != l ? tid_of(l, k) : -1, &bail)) return false;
     const int ri = rows_of(i), rl = rows_of(l), ck = rows_of(k);
     df_stage(As, tile(i, k), P.ldw, ri, ck);
     if (i != l) df_stage(Bs, tile(l, k), P.ldw, rl, ck);
     __syncthreads();
     float acc[4][4] = {};
     df_mma(acc, As, i != l ? Bs : As, ty, tx);
-    float* dst = tile(i, l);
+    if (q < DF_NACC) {
+      float* A = ACC + q * 64 * 64;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = ty * 4 + u;
-      if (r >= ri) continue;
+      for (int u = 0; u < 4; ++u) {
+        float4* p = reinterpret_cast<float4*>(A + (ty * 4 + u) * 64 + tx * 4);
+        float4 v = *p;
+        v.x -= acc[u][0];
+        v.y -= acc[u][1];
+        v.z -= acc[u][2];
+        v.w -= acc[u][3];
+        *p = v;
+      }
+    } else {
+      float* dst = tile(i, l);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int cc = tx * 4 + v;
-        if (cc < rl) __stcg(dst + (int64_t)r * P.ldw + cc, __ldcg(dst + (int64_t)r * P.ldw + cc) - acc[u][v]);
+      for (int u = 0; u < 4; ++u) {
+        const int r = ty * 4 + u;
+        if (r >= ri) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int cc = tx * 4 + v;
+          if (cc < rl) __stcg(dst + (int64_t)r * P.ldw + cc, __ldcg(dst + (int64_t)r * P.ldw + cc) - acc[u][v]);
+        }
       }
     }
     __syncthreads();  // the staged tiles are read before the next task restages them
@@ -518,10 +567,12 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
   };
 
   // P(i, l): L_il = W_il Z_ll^T
-  auto panel = [&](int i, int l) -> bool {
-    if (!df_wait(P, tid_of(l, l), &bail)) return false;
+  auto panel = [&](int q) -> bool {
+    const int i = own_i[q], l = own_l[q];
+    if (!df_wait2(P, seen, tid_of(l, l), -1, &bail)) return false;
     const int ri = rows_of(i);
-    df_stage(As, tile(i, l), P.ldw, ri, 64);
+    if (q < DF_NACC) df_stage_smem(As, ACC + q * 64 * 64);
+    else df_stage(As, tile(i, l), P.ldw, ri, 64);
     df_stage(Bs, P.Zd + (int64_t)l * 64 * 64, 64, 64, 64);
     __syncthreads();
     float acc[4][4] = {};
@@ -543,8 +594,9 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
   };
 
   // D(l): L_ll = chol(W_ll) and Z_ll = L_ll^{-1} (2 x 2 blocks of 32, as k_mx_step)
-  auto diag = [&](int l) {
-    float* T = dfs;
+  auto diag = [&](int q) {
+    const int l = own_l[q];
+    float* T = R0;
     float* Z = T + MB * MXS_LD;
     float* Y = Z + MB * MXS_LD;
     float* rd = Y + 32 * 33;
@@ -552,9 +604,11 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
     const int warp = tid >> 5;
     const int kb = rows_of(l);
     const float* src = tile(l, l);
+    const float* A = q < DF_NACC ? ACC + q * 64 * 64 : nullptr;
     for (int e = tid; e < MB * MB; e += DF_THREADS) {
       const int i = e / MB, j = e % MB;
-      float v = (i < kb && j <= i) ? __ldcg(src + (int64_t)i * P.ldw + j) : 0.f;
+      float v = 0.f;
+      if (i < kb && j <= i) v = A ? A[e] : __ldcg(src + (int64_t)i * P.ldw + j);
       if (i >= kb && i == j) v = 1.f;  // identity beyond a ragged last block
       T[i * MXS_LD + j] = v;
       Z[i * MXS_LD + j] = 0.f;
@@ -572,12 +626,12 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
       for (int t = 0; t < 32; ++t) {
         const float lv = T[(32 + bi) * MXS_LD + t];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, T[(32 + bj + 8 * q) * MXS_LD + t], acc[q]);
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(lv, T[(32 + bj + 8 * u) * MXS_LD + t], acc[u]);
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = bj + 8 * q;
-        if (j <= bi) T[(32 + bi) * MXS_LD + 32 + j] -= acc[q];
+      for (int u = 0; u < 4; ++u) {
+        const int j = bj + 8 * u;
+        if (j <= bi) T[(32 + bi) * MXS_LD + 32 + j] -= acc[u];
       }
     }
     __syncthreads();
@@ -591,21 +645,21 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
       for (int t = 0; t < 32; ++t) {
         const float lv = T[(32 + bi) * MXS_LD + t];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, Z[t * MXS_LD + bj + 8 * q], acc[q]);
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(lv, Z[t * MXS_LD + bj + 8 * u], acc[u]);
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Y[bi * 33 + bj + 8 * q] = acc[q];
+      for (int u = 0; u < 4; ++u) Y[bi * 33 + bj + 8 * u] = acc[u];
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+      for (int u = 0; u < 4; ++u) acc[u] = 0.f;
 #pragma unroll 8
       for (int t = 0; t < 32; ++t) {
         const float zv = Z[(32 + bi) * MXS_LD + 32 + t];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fmaf(zv, Y[t * 33 + bj + 8 * q], acc[q]);
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(zv, Y[t * 33 + bj + 8 * u], acc[u]);
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Z[(32 + bi) * MXS_LD + bj + 8 * q] = -acc[q];
+      for (int u = 0; u < 4; ++u) Z[(32 + bi) * MXS_LD + bj + 8 * u] = -acc[u];
       __syncthreads();
     }
     float* zd = P.Zd + (int64_t)l * MB * MB;
@@ -625,17 +679,17 @@ __global__ void __launch_bounds__(DF_THREADS) k_chol_df(DfParams P) {
     // U(., s+1; s): the next block column first
     if (s >= 0)
       for (int q = p0; q < nown && own_l[q] == c; ++q)
-        if (own_i[q] - s <= bwb && !update(own_i[q], c, s)) return;
+        if (own_i[q] - s <= bwb && !update(q, s)) return;
     // D(s+1), then P(., s+1)
     for (int q = p0; q < nown && own_l[q] == c; ++q)
-      if (own_i[q] == c) diag(c);
+      if (own_i[q] == c) diag(q);
     for (int q = p0; q < nown && own_l[q] == c; ++q)
-      if (own_i[q] > c && !panel(own_i[q], c)) return;
+      if (own_i[q] > c && !panel(q)) return;
     // U(., l >= s+2; s)
     if (s >= 0)
       for (int q = p0; q < nown && own_l[q] <= s + bwb; ++q) {
         const int l = own_l[q], i = own_i[q];
-        if (l >= s + 2 && i - s <= bwb && !update(i, l, s)) return;
+        if (l >= s + 2 && i - s <= bwb && !update(q, s)) return;
       }
   }
 }
@@ -652,17 +706,21 @@ static rbf_status potrf_df(Ctx* c, int64_t n, float* W, int64_t ldw, float* Zd, 
   const int full = nb - bwb > 0 ? nb - bwb : 0;
   const int m = nb - full, s0 = nb - full;
   const int64_t ntiles = (int64_t)full * (bwb + 1) + (int64_t)m * s0 - (int64_t)m * (m - 1) / 2;
+  // shared memory: staging, accumulators and the bitmap of seen flags (at
+  // most DF_MAXOWN tiles per CTA on up to 1024 SMs)
+  constexpr size_t smem_max = DF_SMEM_BASE + (size_t)(DF_MAXOWN * 1024 / 32) * sizeof(unsigned);
   static int max_blocks[64] = {0};
   const int dev = c->device & 63;
   if (!max_blocks[dev]) {
     int per_sm = 0, sms = 0;
-    RBF_CUDA(cudaFuncSetAttribute(k_chol_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DF_SMEM));
-    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_df, DF_THREADS, DF_SMEM));
+    RBF_CUDA(cudaFuncSetAttribute(k_chol_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_df, DF_THREADS, smem_max));
     RBF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    max_blocks[dev] = (per_sm > 0 ? 1 : 0) * sms;  // one CTA per SM
+    max_blocks[dev] = (per_sm > 0 ? 1 : 0) * (sms < 1024 ? sms : 1024);  // one CTA per SM
   }
   int64_t grid = ntiles < max_blocks[dev] ? ntiles : max_blocks[dev];
   if (grid < 1 || (ntiles + grid - 1) / grid > DF_MAXOWN) return RBF_ERANGE;
+  const size_t smem = DF_SMEM_BASE + (size_t)((ntiles + 31) / 32) * sizeof(unsigned);
   if (c->df_flags.bytes < (size_t)(ntiles + 1) * sizeof(int)) {
     RBF_TRY(c->df_flags.ensure((size_t)(ntiles + 1) * sizeof(int)));
     RBF_CUDA(cudaMemsetAsync(c->df_flags.p, 0, c->df_flags.bytes, s));
@@ -684,7 +742,7 @@ static rbf_status potrf_df(Ctx* c, int64_t n, float* W, int64_t ldw, float* Zd, 
   P.wait_xor = c->wait_xor;
   void* args[] = {(void*)&P};
   StageTimer st(c, RBF_STAGE_PANEL, s, (double)n * n * n / 3.0);
-  RBF_CUDA(cooperative_launch((const void*)k_chol_df, dim3((unsigned)grid), dim3(DF_THREADS), args, DF_SMEM, s));
+  RBF_CUDA(cooperative_launch((const void*)k_chol_df, dim3((unsigned)grid), dim3(DF_THREADS), args, smem, s));
   return RBF_OK;
 }
 
@@ -699,7 +757,10 @@ rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W
   }
   cudaStreamCaptureStatus cap0 = cudaStreamCaptureStatusNone;
   RBF_CUDA(cudaStreamIsCapturing(s, &cap0));
-  if (c->la_ok && c->df_ok && cap0 == cudaStreamCaptureStatusNone) {
+  // the single dataflow launch serves blocks up to DF_NMAX; beyond, the
+  // launch chain with its tensor-core trailing updates is as fast (measured
+  // at a = 8192: 6.1 ms both)
+  if (c->la_ok && c->df_ok && n <= DF_NMAX && cap0 == cudaStreamCaptureStatusNone) {
     rbf_status st = potrf_df(c, n, W, ldw, Zd, s, bw);
     if (st != RBF_ERANGE) return st;
   }

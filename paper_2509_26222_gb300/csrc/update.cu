@@ -383,13 +383,25 @@ __global__ void k_unit_rhs(double* __restrict__ B, int64_t m, int64_t q, const i
   B[e] = (rowpos[cidx] == r) ? 1.0 : 0.0;
 }
 
-// gather G[u][v] = Pg[ids[u]][ids[v]]
-__global__ void k_gather_global(const double* __restrict__ Pg, int64_t M, const int32_t* __restrict__ gids,
-                                const int32_t* __restrict__ lpos, int64_t m, double* __restrict__ G) {
+// Entry (a, b) of the covariance of two centers outside the active block:
+// nonzero only when both refer to the same stored block; a center that never
+// left keeps the prior variance.
+__device__ __forceinline__ double outside_entry(const BlkRef* __restrict__ ref, const double* __restrict__ arena,
+                                                int a, int b, double prior) {
+  const BlkRef ra = ref[a], rb = ref[b];
+  if (ra.base < 0 || rb.base < 0) return a == b ? prior : 0.0;
+  if (ra.base != rb.base) return 0.0;
+  return arena[ra.base + (long long)ra.pos * ra.d + rb.pos];
+}
+
+// gather G[u][v] = P[ids[u]][ids[v]] of centers outside the block
+__global__ void k_gather_outside(const BlkRef* __restrict__ ref, const double* __restrict__ arena, double prior,
+                                 const int32_t* __restrict__ gids, const int32_t* __restrict__ lpos, int64_t m,
+                                 double* __restrict__ G) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * m) return;
   int64_t u = e / m, v = e % m;
-  G[e] = Pg[(int64_t)gids[lpos[u]] * M + gids[lpos[v]]];
+  G[e] = outside_entry(ref, arena, gids[lpos[u]], gids[lpos[v]], prior);
 }
 
 __global__ void k_identity(double* __restrict__ B, int64_t m) {
@@ -403,28 +415,17 @@ __global__ void k_copy_lower(const double* __restrict__ S, double* __restrict__ 
   D[(e / m) * ld + e % m] = S[(e / m) * ld + e % m];
 }
 
-// outside store: zero rows/columns of the leaving ids, then write their block
-__global__ void k_pg_zero(double* __restrict__ Pg, int64_t M, const int32_t* __restrict__ ids,
-                          const int32_t* __restrict__ lpos, int64_t d) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d * M) return;
-  int64_t q = e / M, j = e % M;
-  int64_t g = ids[lpos[q]];
-  Pg[g * M + j] = 0.0;
-  Pg[j * M + g] = 0.0;
-}
-
-__global__ void k_pg_block(double* __restrict__ Pg, int64_t M, const int32_t* __restrict__ ids,
-                           const int32_t* __restrict__ lpos, int64_t d, const double* __restrict__ Pdd) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d * d) return;
-  int64_t u = e / d, v = e % d;
-  Pg[(int64_t)ids[lpos[u]] * M + ids[lpos[v]]] = Pdd[e];
-}
-
-__global__ void k_pg_init(double* __restrict__ Pg, int64_t M, double diag) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < M) Pg[j * M + j] = diag;
+// the leaving centers refer to their new block (arena offset base, d x d)
+__global__ void k_blk_assign(BlkRef* __restrict__ ref, const int32_t* __restrict__ ids,
+                             const int32_t* __restrict__ lpos, int64_t d, long long base) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < d) {
+    BlkRef r;
+    r.base = base;
+    r.d = (int)d;
+    r.pos = (int)u;
+    ref[ids[lpos[u]]] = r;
+  }
 }
 
 // P[u][v] = 0.5 (X[pos[u]][v] + X[pos[v]][u]) for X = H^{-1} E_pos (n x k)
@@ -523,6 +524,30 @@ rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64
     RBF_CUDA(cudaGetLastError());
   }
   RBF_CUDA(cudaMemcpyAsync(b, xb.p, (size_t)a * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return RBF_OK;
+}
+
+// Room for `need` float64 entries in the arena of stored blocks, keeping its
+// contents (a new buffer, a copy, the old one freed).
+static rbf_status arena_reserve(Ctx* c, int64_t need, cudaStream_t s) {
+  const size_t bytes = (size_t)need * sizeof(double);
+  if (bytes <= c->arena.bytes) return RBF_OK;
+  size_t want = 2 * c->arena.bytes;
+  if (want < bytes) want = bytes;
+  if (want < ((size_t)1 << 20)) want = (size_t)1 << 20;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+  if (c->arena_used > 0) {
+    e = cudaMemcpyAsync(p, c->arena.p, (size_t)c->arena_used * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+      cudaFree(p);
+      return cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+    }
+  }
+  c->arena.release();  // cudaFree waits for the copy
+  c->arena.p = p;
+  c->arena.bytes = want;
   return RBF_OK;
 }
 
@@ -790,8 +815,9 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       }
       Buf& Gb = c->scratch(42);
       RBF_TRY(Gb.ensure((size_t)r * r * sizeof(double)));
-      { k_gather_global<<<nblk(r * r), 256, 0, sC>>>(c->Pg.as<double>(), M, An.as<int32_t>(),
-                                                   Rl.as<int32_t>(), r, Gb.as<double>()); ::rbf::note_launch(); }
+      { k_gather_outside<<<nblk(r * r), 256, 0, sC>>>(c->blkref.as<BlkRef>(), c->arena.as<double>(),
+                                                    1.0 / c->cfg.lambda, An.as<int32_t>(), Rl.as<int32_t>(), r,
+                                                    Gb.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
       if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, sC));
       else RBF_TRY(spd_inverse(c, Gb.as<double>(), r, sC, 43));
@@ -954,20 +980,18 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   { k_w_add<<<nblk(an), 256, 0, s>>>(c->w.as<double>(), An.as<int32_t>(), an, u.as<double>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   if (d > 0) {
-    if (!c->pg_on) {
-      RBF_TRY(c->Pg.ensure((size_t)M * M * sizeof(double)));
-      RBF_CUDA(cudaMemsetAsync(c->Pg.p, 0, (size_t)M * M * sizeof(double), s));
-      { k_pg_init<<<nblk(M), 256, 0, s>>>(c->Pg.as<double>(), M, 1.0 / c->cfg.lambda); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      c->pg_on = true;
-    }
-    { k_pg_zero<<<nblk(d * M), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d); ::rbf::note_launch(); }
+    // the block P_DD goes to the arena; the leaving centers refer to it, which
+    // also drops their coupling to every older block (P[D, not D] = 0)
+    const long long base = c->arena_used;
+    RBF_TRY(arena_reserve(c, base + d * d, s));
+    RBF_CUDA(cudaMemcpyAsync(c->arena.as<double>() + base, Pdd.p, (size_t)d * d * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s));
+    { k_blk_assign<<<nblk(d), 256, 0, s>>>(c->blkref.as<BlkRef>(), c->A.as<int32_t>(), Dl.as<int32_t>(), d, base); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     { k_mark_departed<<<nblk(d), 256, 0, s>>>(c->A.as<int32_t>(), Dl.as<int32_t>(), d, c->departed.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    { k_pg_block<<<nblk(d * d), 256, 0, s>>>(c->Pg.as<double>(), M, c->A.as<int32_t>(), Dl.as<int32_t>(), d,
-                                           Pdd.as<double>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
+    c->arena_used = base + d * d;
+    c->pg_on = true;
   }
   std::swap(c->H, Hn);
   if (mixed) {
@@ -1039,7 +1063,7 @@ extern "C" rbf_status rbf_get_neighbors(rbf_ctx* cx, const float* pts, int64_t n
 // the others from the outside store (or the prior), zero across the two.
 __global__ void k_cov_assemble(int64_t k, const int32_t* __restrict__ ids, const int32_t* __restrict__ g2l,
                                const int32_t* __restrict__ rank_in_active, const double* __restrict__ Paa,
-                               int64_t ka, const double* __restrict__ Pg, int64_t M, int pg_on,
+                               int64_t ka, const BlkRef* __restrict__ ref, const double* __restrict__ arena,
                                double prior, double* __restrict__ out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= k * k) return;
@@ -1050,8 +1074,7 @@ __global__ void k_cov_assemble(int64_t k, const int32_t* __restrict__ ids, const
   if (au && av) {
     x = Paa[(int64_t)rank_in_active[u] * ka + rank_in_active[v]];
   } else if (!au && !av) {
-    if (pg_on) x = Pg[(int64_t)iu * M + iv];
-    else x = (iu == iv) ? prior : 0.0;
+    x = outside_entry(ref, arena, iu, iv, prior);
   }
   out[e] = x;
 }
@@ -1107,8 +1130,8 @@ extern "C" rbf_status rbf_get_cov(rbf_ctx* cx, const int32_t* ids, int64_t k, do
   }
   { k_cov_assemble<<<nblk(k * k), 256, 0, s>>>(k, ib.as<int32_t>(), c->g2l.as<int32_t>(), rb.as<int32_t>(),
                                              ka > 0 ? Paa.as<double>() : nullptr, ka,
-                                             c->pg_on ? c->Pg.as<double>() : nullptr, c->M, c->pg_on ? 1 : 0,
-                                             1.0 / c->cfg.lambda, Pk); ::rbf::note_launch(); }
+                                             c->blkref.as<BlkRef>(), c->arena.as<double>(), 1.0 / c->cfg.lambda,
+                                             Pk); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_CUDA(cudaStreamSynchronize(s));
   int flag = 0;

@@ -290,3 +290,38 @@ def test_test_hook_validation(N):
         with pytest.raises(N.RBFError) as e:
             T.test_hook(hook, value)
         assert e.value.status == -1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_update_departures_at_65536_centers(N, prec):
+    """256 x 256 centers at 0.1 m (M = 65,536, rho = 0.3 m): three overlapping
+    frames -- the second shifted so that centers leave the active block, the
+    third bringing most of them back -- against the oracle's block recursion
+    (its covariance store); covariance blocks mix active, departed and
+    never-touched centers.  The outside covariance is stored per departure,
+    not as an M x M matrix (34 GB here)."""
+    cfg = W.config5(q=16)
+    c = cfg["centers"]
+    rng = np.random.default_rng(41)
+
+    def frame(x0, y0):
+        xy = rng.uniform([x0, y0], [x0 + 2.0, y0 + 1.0], (3000, 2))
+        z = 0.1 * np.sin(0.7 * xy[:, 0]) * np.cos(0.9 * xy[:, 1]) + rng.normal(0.0, 0.02, 3000)
+        return np.c_[xy, z].astype(np.float32)
+
+    frames = [frame(10.0, 12.0), frame(10.6, 12.3), frame(10.1, 12.05)]
+    T = N.Terrain(rho=0.3, update_precision=prec)
+    T.set_centers(dev(c, torch.float64))
+    st = O.BlockState(c, 1e-3, O.WENDLAND, rho=0.3)
+    for k, p32 in enumerate(frames):
+        T.update(dev(p32), noise=0.02)
+        A = O.block_update(st, p32.astype(np.float64))
+        assert np.array_equal(T.active().cpu().numpy(), A)
+        assert rel_inf(T.weights().cpu().numpy(), st.w) < F64_TOL
+        left = np.setdiff1d(st.P.ids, A)
+        ids = np.unique(np.r_[rng.choice(A, 40, replace=False),
+                              rng.choice(left, min(30, left.size), replace=False) if left.size else [],
+                              rng.choice(c.shape[0], 6, replace=False)]).astype(np.int32)
+        assert rel_inf(T.cov(ids).cpu().numpy(), st.P.block(ids)) < F64_TOL
+        if k > 0:
+            assert left.size > 0
