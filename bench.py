@@ -122,6 +122,33 @@ def raster_line(r, pk, pk_kind):
             "speedup_over_scattered_eval": r["scattered_eval_same_points_ms"] / r["ms"]}
 
 
+def pk_sm_ghz(pk):
+    return pk.get("sm_max_mhz", 2070.0) / 1e3
+
+
+def batch_work(sizes, rho=0.6, h=0.2):
+    """Algorithmic work of the 256-patch batch, from each patch's (M, nx, n, Q):
+    the Gram m~ m~^T and m~ z (K(K+1)/2 + K multiply-adds per point, K = pi
+    rho^2 / h^2 in-support centers), the banded Cholesky of the M x M
+    information matrix (M b^2 flops for half-bandwidth b = (2 ceil(rho/h) - 1)
+    (nx + 1) centers, b <= M), three refined solves (two triangular solves of
+    2 M b flops each, two float64 residuals of 2 M (2b + 1)), and the
+    evaluation (16 FP32 instructions per in-support center per query).
+    Bytes: 12 per point and 8 + 12 per query (in + out), 8 per weight."""
+    k = math.pi * rho * rho / (h * h)
+    rca = math.ceil(rho / h - 1e-9)
+    flops = 0.0
+    nbytes = 0.0
+    for M, nx, n, Q in sizes:
+        b = min((2 * rca - 1) * (nx + 1), M)
+        flops += n * (k * (k + 1) + 2 * k)                    # Gram, 2 flops per multiply-add
+        flops += M * b * b                                    # banded Cholesky
+        flops += 3 * 2 * (2 * M * b) + 2 * 2 * M * (2 * b + 1)  # solves and residuals
+        flops += Q * 16 * k                                   # evaluation
+        nbytes += 12 * n + 20 * Q + 8 * M
+    return flops, nbytes
+
+
 def eval_alu_line(qps, pk, rho=0.6, h=0.2):
     """ALU roofline of the evaluation: EVAL_INSTR_PER_NEIGHBOR FP32-pipe
     instructions per in-support neighbour, K = pi rho^2 / h^2 neighbours per
@@ -223,11 +250,10 @@ class Clocks:
 # DRAM bytes per query of the lattice evaluation kernel, from one ncu capture
 # (2^24 uniform queries on the 64x64 lattice: 134.31 MB read + 141.67 MB written).
 EVAL_DRAM_BYTES_PER_QUERY = (134.307840e6 + 141.672192e6) / (1 << 24)
-# DRAM bytes (read + write) per launch of k_mx_step, the mean over 400 launches
-# of the frame sequence (ncu dram__bytes_read.sum + dram__bytes_write.sum on
-# `bench.py --steps 2 --warmup 3 --no-cpu --eval-log2 20 --batch-patches 0
-# --c5-reps 0 --no-other`); the writes of the step stay in L2.
-MX_STEP_DRAM_BYTES_PER_LAUNCH = 537914.24 + 0.0
+# DRAM bytes (read + write) of one k_chol_df launch (the factorization of one
+# staircase frame, a = 1811), from one ncu capture; None until measured
+DF_DRAM_BYTES_PER_LAUNCH = None
+DF_TRAFFIC_SOURCE = "ncu dram__bytes_read+write of one k_chol_df launch (frame 5 of the sequence)"
 
 
 def frame_arrays(k):
@@ -627,10 +653,13 @@ def run_ours(args, ws, rank, local):
         arr = (N.RbfPatch * args.batch_patches)()
         keep = []
         npts = 0
+        sizes = []
+        pk = peaks()[0]
         for k in range(args.batch_patches):
             sp = W.config4_patch(k)
             M = sp["M"]
             gx = int(math.ceil(math.sqrt(M)))
+            sizes.append((M, gx, sp["points"].shape[0], sp["points"].shape[0]))
             pts = torch.tensor(sp["points"].astype(np.float32), device=dev)
             q = pts[:, :2].contiguous()
             w = torch.empty(M, dtype=torch.float64, device=dev)
@@ -657,10 +686,17 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize()
             bt.append(e0.elapsed_time(e1))
         bms = float(np.median(bt))
+        bflops, bbytes = batch_work(sizes)
+        fp32_peak = 152 * 128 * 2 * pk_sm_ghz(pk) * 1e9
         batch = {"workload": f"{args.batch_patches} patches: M log-uniform 64-4096, n log-uniform 500-50000; "
                              "update from the prior + h/grad h at the patch points, one graph launch",
                  "ms_per_batch": bms, "patches_per_s": args.batch_patches / (bms * 1e-3),
-                 "points_per_s": npts / (bms * 1e-3)}
+                 "points_per_s": npts / (bms * 1e-3),
+                 "roofline": {"bound": "alu", "algorithmic_gflop": bflops / 1e9, "algorithmic_mb": bbytes / 1e6,
+                              "achieved": bflops / (bms * 1e-3) / 1e12, "peak": fp32_peak / 1e12,
+                              "unit": "TFLOP/s", "frac": bflops / (bms * 1e-3) / fp32_peak,
+                              "hbm_frac": bbytes / (bms * 1e-3) / (pk["hbm_gbs"] * 1e9),
+                              "note": "latency-bound: chains of dependent steps per patch; FP32 CUDA-core peak"}}
         TB.close()
     # ----- one update at 65,536 centers with an 8192-center active block -----
     c5 = None
@@ -808,7 +844,7 @@ def main():
     cand = {"trsm32": ("k_trsm32", "alu", fp32_peak, fp32_note, 1.0),
             "invapply": ("k_inv_fwd_gemv+k_inv_bwd_gemv / k_inv_apply", "alu", fp32_peak, fp32_note, 1.0),
             "inverse": ("k_trtri_level", "alu", fp32_peak, fp32_note, 1.0),
-            "panel": ("k_mx_step", "alu", fp32_peak, fp32_note, 1.0),
+            "panel": ("k_chol_df", "alu", fp32_peak, fp32_note, 1.0),
             "trailing": ("k_syrk_tc", "tensor", pk["bf16_tflops_sustained"],
                          "bf16 sustained (" + pk_kind + "); the method's flops, run as 6 bf16 slice products", 1.0),
             "eval": ("k_eval_lattice_win", "hbm", pk["hbm_gbs"], pk_kind, 1.0)}
@@ -827,9 +863,8 @@ def main():
                 "frac": ach / peak, "traffic": None, "peak_kind": pkind, "launches": int(cnt),
                 "ms_per_launch": ms / max(cnt, 1), "work_per_launch": mult * work / max(cnt, 1)}
         if dom == "panel":
-            roof["traffic"] = MX_STEP_DRAM_BYTES_PER_LAUNCH
-            roof["traffic_source"] = ("ncu dram__bytes_read+write per k_mx_step launch, mean of 400 launches "
-                                      "of the same frame sequence")
+            roof["traffic"] = DF_DRAM_BYTES_PER_LAUNCH
+            roof["traffic_source"] = DF_TRAFFIC_SOURCE
     trail = prof["trailing"]
     roof_tc = None
     if trail[0] > 0:

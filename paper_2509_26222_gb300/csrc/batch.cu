@@ -176,6 +176,7 @@ __global__ void k_bp_eval(PatchGeom G, const double* __restrict__ w, const float
 // host side
 // ---------------------------------------------------------------------------
 struct BatchState {
+  void* persistent = nullptr;  // state of the mixed-precision path (bqueue.cu)
   std::vector<Ctx*> sub;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
@@ -320,6 +321,7 @@ void batch_destroy(Ctx* c) {
   for (cudaStream_t s : B->streams) cudaStreamDestroy(s);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   for (Ctx* sc : B->sub) free_sub(sc);
+  bq_destroy(B->persistent);
   delete B;
   c->batch = nullptr;
 }
@@ -425,6 +427,20 @@ extern "C" rbf_status rbf_batch_update_eval(rbf_ctx* cx, const rbf_patch* patche
   BatchState* B = reinterpret_cast<BatchState*>(c->batch);
   const int S = (int)B->sub.size();
   const bool allow_mixed = c->cfg.update_precision == RBF_UPDATE_MIXED;
+  if (allow_mixed && c->df_ok) {
+    // the persistent launches (bqueue.cu) serve the mixed-precision batch
+    bool handled = false;
+    RBF_TRY(bq_run(c, &B->persistent, patches, npatch, s, &handled));
+    if (handled) {
+      RBF_CUDA(cudaStreamSynchronize(s));
+      int f = 0;
+      RBF_TRY(read_dev_flag(c, s, &f));
+      if (f & DEV_BAD_INDEX) return fail(RBF_EINVAL, "a patch has a non-finite point");
+      if (f & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "a patch's information matrix is not SPD");
+      if (f & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "a bounded wait timed out");
+      return RBF_OK;
+    }
+  }
   // factorization path per patch (autotuned per size bucket)
   std::vector<char> mixed((size_t)npatch, 0);
   for (int32_t k = 0; k < npatch; ++k) {

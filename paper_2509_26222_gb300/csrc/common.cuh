@@ -323,6 +323,9 @@ rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
                       cudaStream_t s, int64_t bw = BW_DENSE);
 void batch_destroy(Ctx* c);
+// the mixed-precision batch in persistent launches (bqueue.cu)
+rbf_status bq_run(Ctx* c, void** state, const rbf_patch* patches, int32_t npatch, cudaStream_t s, bool* handled);
+void bq_destroy(void* state);
 // forget the cached device address of rbf_soft_cost_noalloc's scratch on `dev`
 void noalloc_forget(int dev);
 rbf_status symv_residual(const double* H, int64_t n, int64_t ld, const double* x,

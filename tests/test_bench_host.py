@@ -51,3 +51,14 @@ def test_eval_alu_line():
 
 def test_max_over_ranks_without_a_group_is_identity():
     assert bench.max_over_ranks(3.5, None) == 3.5
+
+
+def test_batch_work_by_hand():
+    # one patch: M = 64 centers on rows of nx = 8, n = Q = 100; K = 9 pi = 28.274
+    # in-support centers; half-bandwidth b = min(5 x 9, 64) = 45:
+    #   Gram 100 (28.274 x 29.274 + 2 x 28.274) = 88,426
+    #   Cholesky 64 x 45^2 = 129,600; solves 6 x 2 x 64 x 45 = 34,560;
+    #   residuals 4 x 64 x 91 = 23,296; evaluation 100 x 16 x 28.274 = 45,239
+    f, b = bench.batch_work([(64, 8, 100, 100)])
+    assert math.isclose(f, 88426 + 129600 + 34560 + 23296 + 45239, rel_tol=1e-4)
+    assert b == 12 * 100 + 20 * 100 + 8 * 64
