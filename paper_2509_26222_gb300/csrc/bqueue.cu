@@ -65,6 +65,7 @@ struct BqPatch {
   int nx, rows, nb, bwb;
   int ch, cx, cy, ntile;
   int gs, pad;
+  double inv_h;      // 1 / h
 };
 
 struct BqGeom {
@@ -93,8 +94,8 @@ __device__ __forceinline__ int bq_find(int np, long long g, F start) {
 // lattice cell of a point (node floor(u), clamped to the lattice)
 __device__ __forceinline__ void bq_cell(const BqPatch& p, float px, float py, int& ix, int& iy, double& pu,
                                         double& pv) {
-  pu = ((double)px - p.x0) / p.h - 0.5;
-  pv = ((double)py - p.y0) / p.h - 0.5;
+  pu = ((double)px - p.x0) * p.inv_h - 0.5;
+  pv = ((double)py - p.y0) * p.inv_h - 0.5;
   pu = fmin(fmax(pu, -1.0), (double)p.nx);
   pv = fmin(fmax(pv, -1.0), (double)p.rows);
   ix = (int)floor(pu);
@@ -158,6 +159,43 @@ __device__ __forceinline__ void bq_add_u128_words(unsigned long long* U, unsigne
   if (h != 0ull) atomicAdd(U + 1, h);
 }
 
+// Float-float arithmetic (a value as hi + lo, two float32): the regression
+// entries of the Wendland kernel are formed with it instead of float64, which
+// GB300 runs at a small fraction of the float32 rate.  Error-free transforms:
+// the sum by Knuth's TwoSum, the product by one fused multiply-add; the square
+// root by one Newton (Heron) correction of the float32 root.  About 2^-46
+// relative, against 2^-53 for float64.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  FF s = ff_two_sum(x.hi, y.hi);
+  return ff_fast_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi), e = fmaf(x.hi, y.hi, -p);
+  return ff_fast_sum(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ FF ff_sqrt(FF x) {
+  if (!(x.hi > 0.f)) return {0.f, 0.f};
+  const float y = __fsqrt_rn(x.hi);
+  const float p = __fmul_rn(y, y), pe = fmaf(y, y, -p);  // y^2 = p + pe exactly
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
+  return ff_fast_sum(y, __fdiv_rn(r, __fmul_rn(2.f, y)));
+}
+__device__ __forceinline__ FF ff_of(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+
 // Shared memory of the Gram: the band of the window as pairs of 32-bit words
 // (low, high) -- a 64-bit sum kept as two halves so that every update is a
 // native 32-bit shared-memory atomic (the carry of the low half goes to the
@@ -179,7 +217,9 @@ __global__ void __launch_bounds__(256) k_bq_gram(const BqPatch* __restrict__ P, 
   __shared__ int32_t sid[8][BQ_MAXK];
   __shared__ double smv[8][BQ_MAXK];
   __shared__ unsigned long long smq[8][BQ_MAXK];
+  __shared__ FF nodex[64], nodey[64];  // window node coordinates (float-float), W <= 64
   __shared__ long long cur;
+  const FF inv_rho = ff_of(G.inv_rho);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rca = G.rca, R2 = 2 * rca;
   const long long ibeg = istart[cbeg], iend = istart[cend];
@@ -205,6 +245,10 @@ __global__ void __launch_bounds__(256) k_bq_gram(const BqPatch* __restrict__ P, 
     unsigned* sG = reinterpret_cast<unsigned*>(sg);        // nG pairs of words
     unsigned long long* sU = sg + nG + (long long)wid * 2 * W * W;  // this warp's u sums
     for (int e = tid; e < nG + 16 * W * W; e += blockDim.x) sg[e] = 0ull;
+    if (tid < W) {
+      nodex[tid] = ff_of(bq_node(B.x0, wx0 + tid, B.h));
+      nodey[tid] = ff_of(bq_node(B.y0, wy0 + tid, B.h));
+    }
     __syncthreads();
     const int a0 = cstart[c] + (int)(item - istart[c]) * BQ_SLICE;
     const int a1 = a0 + BQ_SLICE < cstart[c + 1] ? a0 + BQ_SLICE : cstart[c + 1];
@@ -222,15 +266,30 @@ __global__ void __launch_bounds__(256) k_bq_gram(const BqPatch* __restrict__ P, 
         bool in = false;
         int li = 0;
         double m = 0.0;
+        unsigned long long mq = 0ull;
         if (t < R2 * R2) {
           const int i2 = ib + t % R2, j2 = jb + t / R2;
           if (i2 >= 0 && i2 < B.nx && j2 >= 0 && j2 < B.rows && (long long)j2 * B.nx + i2 < B.M) {
-            const double cx = bq_node(B.x0, i2, B.h), cy = bq_node(B.y0, j2, B.h);
-            if (d2_rn(px, py, (float)cx, (float)cy) < G.r2a) {
-              const double ex = (double)px - cx, ey = (double)py - cy;
-              m = row_value(G.kernel, ex * ex + ey * ey, G.inv_rho, G.g_scale, G.g_inv2s2);
+            const FF cx = nodex[i2 - wx0], cy = nodey[j2 - wy0];
+            if (d2_rn(px, py, cx.hi, cy.hi) < G.r2a) {  // cx.hi is the float32 rounding of the node
               li = (j2 - wy0) * W + (i2 - wx0);
               in = true;
+              if (G.kernel == RBF_KERNEL_WENDLAND) {
+                // m = (1 - s)^4 (4 s + 1), s = |p - c| / rho, in float-float
+                const FF dx = ff_two_sum(__fsub_rn(px, cx.hi), -cx.lo);  // px - cx.hi is exact
+                const FF dy = ff_two_sum(__fsub_rn(py, cy.hi), -cy.lo);
+                const FF sr = ff_mul(ff_sqrt(ff_add(ff_mul(dx, dx), ff_mul(dy, dy))), inv_rho);
+                const FF t = ff_add({1.f, 0.f}, {-sr.hi, -sr.lo});
+                const FF t2 = ff_mul(t, t);
+                const FF mm = ff_mul(ff_mul(t2, t2), ff_add({4.f * sr.hi, 4.f * sr.lo}, {1.f, 0.f}));
+                m = (double)mm.hi + (double)mm.lo;
+                mq = __float2ull_rn(ldexpf(mm.hi, 52)) + (unsigned long long)__float2ll_rn(ldexpf(mm.lo, 52));
+              } else {
+                const double ex = (double)px - ((double)cx.hi + (double)cx.lo);
+                const double ey = (double)py - ((double)cy.hi + (double)cy.lo);
+                m = row_value(G.kernel, ex * ex + ey * ey, G.inv_rho, G.g_scale, G.g_inv2s2);
+                mq = __double2ull_rn(ldexp(m, 52));
+              }
             }
           }
         }
@@ -239,7 +298,7 @@ __global__ void __launch_bounds__(256) k_bq_gram(const BqPatch* __restrict__ P, 
         if (in && pos < BQ_MAXK) {
           sid[wid][pos] = li;
           smv[wid][pos] = m;
-          smq[wid][pos] = __double2ull_rn(ldexp(m, 52));  // m in [0, 1] with 2^52 units per 1
+          smq[wid][pos] = mq;  // m in [0, 1] with 2^52 units per 1
         }
         K += __popc(mask);
       }
@@ -1007,6 +1066,7 @@ static rbf_status bq_plan(Ctx* c, BqState* S, const rbf_patch* patches, int32_t 
     B.gs = 62 - (int)ceil(log2((double)p.n + 1.0));
     if (B.gs > 52) B.gs = 52;
     B.gscale = ldexp(1.0, B.gs);
+    B.inv_h = 1.0 / p.spacing;
     const int bk = bq_bucket(p.M);
     L.bucket_of_pos[pos] = bk;
     B.ch = S->ch[bk] > 0 ? S->ch[bk] : 8;
@@ -1138,7 +1198,9 @@ rbf_status bq_run(Ctx* c, void** state, const rbf_patch* patches, int32_t npatch
     if (patches[k].spacing != h0 || patches[k].M > 65535 || patches[k].n >= (1 << 20) || npatch > (1 << 28))
       return RBF_OK;
   const BqGeom G = bq_geom(c->cfg, h0);
-  if (G.rca < 1 || (2 * G.rca) * (2 * G.rca) > BQ_MAXK || bq_gram_smem(4, G.rca) > 200 * 1024) return RBF_OK;
+  if (G.rca < 1 || (2 * G.rca) * (2 * G.rca) > BQ_MAXK || bq_gram_smem(4, G.rca) > 200 * 1024 ||
+      8 + 2 * G.rca - 1 > 64)
+    return RBF_OK;
   int sms = 0;
   RBF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   static bool attr_done[64] = {false};
