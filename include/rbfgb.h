@@ -78,7 +78,7 @@ typedef struct rbf_config {
                                covariance blocks; n > 0: n for both; 1 = no refinement) */
   int32_t inverse_max;      /* RBF_UPDATE_MIXED: largest active block for which the update forms
                                L^{-1} of the float32 factor and solves by two products with it
-                               (0 = default 3072; negative = never: blocked substitution only) */
+                               (0 = default 4096; negative = never: blocked substitution only) */
   int32_t exact;            /* 0: the paper's block recursion (Sec. III-C: only the rows touched by
                                   the frame are updated, P[A, not A] = 0 afterwards);
                                1: the exact recursion with the full covariance (Eq. kf_w_update and

@@ -116,13 +116,14 @@ struct Ctx {
   Buf Zd;            // float32 inverses of its 64 x 64 diagonal blocks
   Buf Zi;            // float32 L^{-1} of the whole factor (valid when zi_valid)
   bool zi_valid = false;
-  int64_t inv_max = 3072;  // form L^{-1} for active blocks up to this size
+  int64_t inv_max = 4096;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
   int64_t bw_lf = BW_DENSE_CTX;  // half-bandwidth of the float32 factor Lf
   cudaStream_t bs[2] = {};           // side streams of the block stage
   cudaEvent_t bev[3] = {};           // fork and joins of the block stage
   bool la_ok = true;                 // look-ahead factorization allowed
   bool df_ok = true;                 // one-launch dataflow factorization allowed
+  int8_t fchoice[64] = {};           // per size bucket of 256: 0 untimed, 1 launch chain, 2 dataflow
   Buf df_flags;                      // its per-tile ready flags and abort word
   uint32_t df_epoch = 0;
   cudaStream_t la_stream = nullptr;  // side stream of the look-ahead factorization
@@ -312,6 +313,11 @@ rbf_status build_csr(Ctx* c, const double* H, int64_t ld, int64_t n, SpH& out, c
 rbf_status csr_bandwidth(Ctx* c, int64_t n, int64_t* bw, cudaStream_t s);
 rbf_status dense_bandwidth(Ctx* c, const double* H, int64_t ld, int64_t n, int64_t* bw, cudaStream_t s);
 rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t m, double* R, cudaStream_t s);
+// float64 in and out, float-float arithmetic inside (ffgemm.cu)
+rbf_status gemm_ff(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                   const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s);
+rbf_status csr_residual_ff(Ctx* c, const SpH& A, const double* X, const double* B, int64_t m, double* R,
+                           cudaStream_t s, int slot);
 // explicit inverse of the float32 factor and solves with it (inverse.cu)
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
                        cudaStream_t s);

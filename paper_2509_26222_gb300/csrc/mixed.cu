@@ -550,24 +550,70 @@ static rbf_status potrf_df(Ctx* c, int64_t n, float* W, int64_t ldw, float* Zd, 
   return RBF_OK;
 }
 
+static rbf_status potrf_chain(Ctx* c, int64_t n, float* W, int64_t ldw, float* Zd, cudaStream_t s, int64_t bw);
+
+static rbf_status to_f32(const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, cudaStream_t s) {
+  int64_t tot = n * n;
+  { k_mx_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, ldh, n, W, ldw); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
+}
+
+// Float32 factor of H (with the diagonal-block inverses Zd) by the dataflow
+// launch or by the launch chain.  Which is faster depends on the size (the
+// chain's tensor-core trailing updates win for large blocks): the first
+// factorization of each size bucket of 256 runs both, timed, and the bucket
+// keeps the faster.  Stream capture, batched sub-contexts and blocks beyond
+// DF_NMAX use the chain.
 rbf_status potrf_mixed(Ctx* c, const double* H, int64_t ldh, int64_t n, float* W, int64_t ldw, float* Zd,
                        cudaStream_t s, int64_t bw) {
   if (n <= 0) return RBF_OK;
-  int* flag = c->dflag.as<int>();
-  {
-    int64_t tot = n * n;
-    { k_mx_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(H, ldh, n, W, ldw); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-  }
   cudaStreamCaptureStatus cap0 = cudaStreamCaptureStatusNone;
   RBF_CUDA(cudaStreamIsCapturing(s, &cap0));
-  // the single dataflow launch serves blocks up to DF_NMAX; beyond, the
-  // launch chain with its tensor-core trailing updates is as fast (measured
-  // at a = 8192: 6.1 ms both)
-  if (c->la_ok && c->df_ok && n <= DF_NMAX && cap0 == cudaStreamCaptureStatusNone) {
+  if (!(c->la_ok && c->df_ok && n <= DF_NMAX && cap0 == cudaStreamCaptureStatusNone)) {
+    RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
+    return potrf_chain(c, n, W, ldw, Zd, s, bw);
+  }
+  const int b = (int)(n / 256);
+  int8_t& pick = c->fchoice[b < 64 ? b : 63];
+  if (pick == 1) {
+    RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
+    return potrf_chain(c, n, W, ldw, Zd, s, bw);
+  }
+  if (pick == 2) {
+    RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
     rbf_status st = potrf_df(c, n, W, ldw, Zd, s, bw);
     if (st != RBF_ERANGE) return st;
+    RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
+    return potrf_chain(c, n, W, ldw, Zd, s, bw);
   }
+  // first block of this size: time both (the dataflow result is kept)
+  cudaEvent_t ev[3];
+  for (auto& e : ev) RBF_CUDA(cudaEventCreate(&e));
+  RBF_CUDA(cudaEventRecord(ev[0], s));
+  RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
+  RBF_TRY(potrf_chain(c, n, W, ldw, Zd, s, bw));
+  RBF_CUDA(cudaEventRecord(ev[1], s));
+  RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
+  rbf_status st = potrf_df(c, n, W, ldw, Zd, s, bw);
+  RBF_CUDA(cudaEventRecord(ev[2], s));
+  RBF_CUDA(cudaEventSynchronize(ev[2]));
+  float t_chain = 0.f, t_df = 0.f;
+  RBF_CUDA(cudaEventElapsedTime(&t_chain, ev[0], ev[1]));
+  RBF_CUDA(cudaEventElapsedTime(&t_df, ev[1], ev[2]));
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st == RBF_ERANGE) {
+    pick = 1;
+    RBF_TRY(to_f32(H, ldh, n, W, ldw, s));
+    return potrf_chain(c, n, W, ldw, Zd, s, bw);
+  }
+  RBF_TRY(st);
+  pick = t_df <= t_chain ? 2 : 1;
+  return RBF_OK;
+}
+
+static rbf_status potrf_chain(Ctx* c, int64_t n, float* W, int64_t ldw, float* Zd, cudaStream_t s, int64_t bw) {
+  int* flag = c->dflag.as<int>();
   // bf16 slices of the panel, two sets (panel k is read by the trailing
   // update of step k while step k + 1 writes the next one)
   const size_t slice = (size_t)(n + MB) * MB;

@@ -219,4 +219,52 @@ __device__ __forceinline__ void tile_chol_inv(float* T, float* Z, float* Y, floa
   }
 }
 
+// Float-float arithmetic (a value as hi + lo, two float32), used where a
+// result needs more than float32 but GB300's float64 rate (a small fraction of
+// its float32 rate) would bound the kernel.  Error-free transforms:
+// the sum by Knuth's TwoSum, the product by one fused multiply-add; the square
+// root by one Newton (Heron) correction of the float32 root.  About 2^-46
+// relative, against 2^-53 for float64.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  FF s = ff_two_sum(x.hi, y.hi);
+  return ff_fast_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi), e = fmaf(x.hi, y.hi, -p);
+  return ff_fast_sum(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ FF ff_sqrt(FF x) {
+  if (!(x.hi > 0.f)) return {0.f, 0.f};
+  const float y = __fsqrt_rn(x.hi);
+  const float p = __fmul_rn(y, y), pe = fmaf(y, y, -p);  // y^2 = p + pe exactly
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
+  return ff_fast_sum(y, __fdiv_rn(r, __fmul_rn(2.f, y)));
+}
+__device__ __forceinline__ FF ff_of(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+
+// x = hi + lo to about 2^-48 (one float64 subtraction)
+__device__ __forceinline__ FF ff_split(double v) { return ff_of(v); }
+// acc + x y
+__device__ __forceinline__ FF ff_mac(FF acc, FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+  const FF sum = ff_two_sum(acc.hi, p);
+  return ff_fast_sum(sum.hi, __fadd_rn(sum.lo, __fadd_rn(acc.lo, e)));
+}
+__device__ __forceinline__ double ff_to_double(FF x) { return (double)x.hi + (double)x.lo; }
+
 }  // namespace rbf
