@@ -153,7 +153,7 @@ struct Ctx {
   double diag_shift = 0.0;   // added to the diagonal of H' before it is factored
 
   // scratch buffers, addressed by slot (slots 48.. are used by the scans)
-  static constexpr int NSLOT = 96;
+  static constexpr int NSLOT = 100;
   Buf ws[NSLOT];
   Buf& scratch(int i) { return ws[i < NSLOT ? i : NSLOT - 1]; }
 
@@ -314,8 +314,9 @@ rbf_status csr_bandwidth(Ctx* c, int64_t n, int64_t* bw, cudaStream_t s);
 rbf_status dense_bandwidth(Ctx* c, const double* H, int64_t ld, int64_t n, int64_t* bw, cudaStream_t s);
 rbf_status csr_residual(const SpH& A, const double* X, const double* B, int64_t m, double* R, cudaStream_t s);
 // float64 in and out, float-float arithmetic inside (ffgemm.cu)
-rbf_status gemm_ff(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
-                   const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s);
+rbf_status gemm_ff(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s,
+                   int slot, bool lower = false);
 rbf_status csr_residual_ff(Ctx* c, const SpH& A, const double* X, const double* B, int64_t m, double* R,
                            cudaStream_t s, int slot);
 // explicit inverse of the float32 factor and solves with it (inverse.cu)

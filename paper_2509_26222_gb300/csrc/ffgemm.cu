@@ -18,20 +18,25 @@ constexpr int FT = 64;  // output tile
 constexpr int FK = 16;  // k chunk
 constexpr int FLD = FT + 4;
 
-// C = alpha op(A) op(B) + beta C, row-major; 256 threads, each a 4 x 4 block
-__global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
-                                                 const double* __restrict__ A, int64_t lda,
+// C = alpha op(A) op(B) + beta C, row-major; 256 threads, each a 4 x 4 block.
+// With part set, slice z of k ([z kc, (z + 1) kc)) writes its float64 partial
+// product to part[z][m][n] instead.  With lower set only the tiles on or below
+// the diagonal are computed (a symmetric result read from its lower triangle).
+__global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, bool lower, int64_t m, int64_t n, int64_t k,
+                                                 int64_t kc, double alpha, const double* __restrict__ A, int64_t lda,
                                                  const double* __restrict__ B, int64_t ldb, double beta,
-                                                 double* __restrict__ Cm, int64_t ldc) {
+                                                 double* __restrict__ Cm, int64_t ldc, double* __restrict__ part) {
+  if (lower && blockIdx.x > blockIdx.y) return;
   __shared__ __align__(16) float Ah[FK][FLD], Al[FK][FLD], Bh[FK][FLD], Bl[FK][FLD];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int64_t i0 = (int64_t)blockIdx.y * FT, j0 = (int64_t)blockIdx.x * FT;
+  const int64_t kb = (int64_t)blockIdx.z * kc, ke = kb + kc < k ? kb + kc : k;
   FF acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = {0.f, 0.f};
-  for (int64_t k0 = 0; k0 < k; k0 += FK) {
+  for (int64_t k0 = kb; k0 < ke; k0 += FK) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = tid + 256 * q;  // 0 .. 1023
@@ -41,7 +46,7 @@ __global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, int64_t m, in
       else { kk = e & 15; r = e >> 4; }
       const int64_t gi = i0 + r, gk = k0 + kk;
       double a = 0.0;
-      if (gi < m && gk < k) a = ta ? A[gk * lda + gi] : A[gi * lda + gk];
+      if (gi < m && gk < ke) a = ta ? A[gk * lda + gi] : A[gi * lda + gk];
       const FF af = ff_split(a);
       Ah[kk][r] = af.hi;
       Al[kk][r] = af.lo;
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, int64_t m, in
       else { cc = e & 63; kk = e >> 6; }
       const int64_t gj = j0 + cc, gk2 = k0 + kk;
       double b = 0.0;
-      if (gj < n && gk2 < k) b = tb ? B[gj * ldb + gk2] : B[gk2 * ldb + gj];
+      if (gj < n && gk2 < ke) b = tb ? B[gj * ldb + gk2] : B[gk2 * ldb + gj];
       const FF bf = ff_split(b);
       Bh[kk][cc] = bf.hi;
       Bl[kk][cc] = bf.lo;
@@ -79,10 +84,25 @@ __global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, int64_t m, in
     for (int v = 0; v < 4; ++v) {
       const int64_t j = j0 + tx * 4 + v;
       if (j >= n) continue;
-      const double prev = beta != 0.0 ? Cm[i * ldc + j] : 0.0;
-      Cm[i * ldc + j] = alpha * ff_to_double(acc[u][v]) + beta * prev;
+      if (part) {
+        part[((int64_t)blockIdx.z * m + i) * n + j] = ff_to_double(acc[u][v]);
+      } else {
+        const double prev = beta != 0.0 ? Cm[i * ldc + j] : 0.0;
+        Cm[i * ldc + j] = alpha * ff_to_double(acc[u][v]) + beta * prev;
+      }
     }
   }
+}
+
+__global__ void k_gemm_ff_reduce(int64_t m, int64_t n, int nsplit, const double* __restrict__ part, double alpha,
+                                 double beta, double* __restrict__ Cm, int64_t ldc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  double acc = 0.0;
+  for (int q = 0; q < nsplit; ++q) acc += part[(int64_t)q * m * n + e];
+  const int64_t i = e / n, j = e % n;
+  const double prev = beta != 0.0 ? Cm[i * ldc + j] : 0.0;
+  Cm[i * ldc + j] = alpha * acc + beta * prev;
 }
 
 // the float-float copy of X (n x m)
@@ -138,12 +158,36 @@ __global__ void __launch_bounds__(256) k_csr_resm_ff(int64_t n, int64_t m, int64
 
 }  // namespace
 
-rbf_status gemm_ff(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
-                   const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s) {
+rbf_status gemm_ff(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s,
+                   int slot, bool lower) {
   if (m <= 0 || n <= 0) return RBF_OK;
-  dim3 grid((unsigned)((n + FT - 1) / FT), (unsigned)((m + FT - 1) / FT));
-  { k_gemm_ff<<<grid, 256, 0, s>>>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc); ::rbf::note_launch(); }
+  const int64_t tiles = ((m + FT - 1) / FT) * ((n + FT - 1) / FT);
+  // outputs that do not fill the GPU twice split k into slices of >= 128
+  int64_t nsplit = 1;
+  if (!lower && tiles < 2 * 152 && k > 256) {
+    nsplit = (2 * 152 + tiles - 1) / tiles;
+    const int64_t most = k / 128;
+    if (nsplit > most) nsplit = most;
+  }
+  int64_t kc = (k + nsplit - 1) / nsplit;
+  kc = (kc + FK - 1) / FK * FK;
+  nsplit = (k + kc - 1) / kc;
+  double* part = nullptr;
+  if (nsplit > 1) {
+    Buf& pb = c->scratch(slot);
+    RBF_TRY(pb.ensure((size_t)nsplit * m * n * sizeof(double)));
+    part = pb.as<double>();
+  }
+  dim3 grid((unsigned)((n + FT - 1) / FT), (unsigned)((m + FT - 1) / FT), (unsigned)nsplit);
+  { k_gemm_ff<<<grid, 256, 0, s>>>(ta, tb, lower, m, n, k, kc, alpha, A, lda, B, ldb, beta, Cm, ldc, part); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
+  if (part) {
+    if (lower) return fail(RBF_EINVAL, "gemm_ff: lower with split k");
+    { k_gemm_ff_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, s>>>(m, n, (int)nsplit, part, alpha, beta, Cm,
+                                                                      ldc); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  }
   return RBF_OK;
 }
 

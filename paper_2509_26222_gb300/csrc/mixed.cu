@@ -919,8 +919,8 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, cons
 
 // Block P[D, D] = E_D^T H^{-1} E_D of the covariance for the columns B = E_D
 // (unit vectors at positions pos, overwritten).  X comes from sweeps - 1
-// refined solves; then one float64 residual R = E_D - H X gives the
-// second-order estimate
+// refined solves; then one residual R = E_D - H X (float-float products,
+// float64 result) gives the second-order estimate
 //   P = E_D^T X + X^T R    (error -(X - H^{-1}E_D)^T H (X - H^{-1}E_D)),
 // symmetrised.  With the float32 factor accurate to eps, one solve already
 // gives P to about eps^2, where one more refinement sweep would need a
@@ -970,8 +970,12 @@ rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const 
     RBF_TRY(mixed_solve(c, H, ldh, Hs, W, ldw, Zd, Zi, n, B, k, sweeps - 1, s, bw));
   }
   double* R = rr.as<double>();
-  if (Hs) {
-    RBF_TRY(csr_residual(*Hs, B, e0.as<double>(), k, R, s));
+  if (bw >= n) {
+    // H filled in by earlier departures: a tiled product over the dense H
+    RBF_CUDA(cudaMemcpyAsync(R, e0.p, (size_t)tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RBF_TRY(gemm_ff(c, false, false, n, k, n, -1.0, H, ldh, B, k, 1.0, R, k, s, 97));
+  } else if (Hs) {
+    RBF_TRY(csr_residual_ff(c, *Hs, B, e0.as<double>(), k, R, s, 97));
   } else {
     unsigned nw = (unsigned)((n * 32 + 255) / 256);
     { k_residual_multi<<<nw, 256, 0, s>>>(H, n, ldh, B, e0.as<double>(), k, R); ::rbf::note_launch(); }
@@ -979,7 +983,7 @@ rbf_status mixed_cov(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, const 
   }
   Buf& gq = c->scratch(86);
   RBF_TRY(gq.ensure((size_t)k * k * sizeof(double)));
-  RBF_TRY(gemm_f64(c, true, false, k, k, n, 1.0, B, k, R, k, 0.0, gq.as<double>(), k, s));
+  RBF_TRY(gemm_ff(c, true, false, k, k, n, 1.0, B, k, R, k, 0.0, gq.as<double>(), k, s, 96));
   { k_cov_second_order<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(B, k, pos, gq.as<double>(), P); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;

@@ -302,6 +302,14 @@ __global__ void k_gather_sym(const double* __restrict__ H, int64_t ldh, const in
   T[u * ldt + v] = H[(int64_t)perm[u] * ldh + perm[v]];
 }
 
+// D = S (m x m, leading dimension m) from the lower triangle of S
+__global__ void k_copy_lower_sym(const double* __restrict__ S, int64_t lds, int64_t m, double* __restrict__ D) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  int64_t u = e / m, v = e % m;
+  D[e] = (v <= u) ? S[u * lds + v] : S[v * lds + u];
+}
+
 // Hn[pos[u]][pos[v]] = S[u][v] using the lower triangle of S (symmetric)
 __global__ void k_scatter_sym(const double* __restrict__ S, int64_t lds, int64_t m,
                               const int32_t* __restrict__ pos, double* __restrict__ Hn, int64_t ldn) {
@@ -868,7 +876,30 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
         { k_gather_sym<<<nblk(t * t), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), t,
                                                  T.as<double>(), t); ::rbf::note_launch(); }
         RBF_CUDA(cudaGetLastError());
-        if (d <= SPD_SMALL_MAX) {
+        if (mixed) {
+          // Block elimination of D in chunks of at most SPD_SMALL_MAX: each
+          // chunk's Schur complement is taken in the block the previous
+          // chunks left, T[r, r] -= T[r, q] T[q, q]^{-1} T[r, q]^T, with the
+          // products in float-float arithmetic.  Only the lower triangle of T
+          // is kept current (the 64 x 64 tiles on or below the diagonal).
+          Buf& Gd = c->scratch(84);
+          Buf& Yb = c->scratch(85);
+          const int64_t nc = (d + SPD_SMALL_MAX - 1) / SPD_SMALL_MAX;
+          const int64_t cs = (d + nc - 1) / nc;
+          RBF_TRY(Gd.ensure((size_t)cs * cs * sizeof(double)));
+          RBF_TRY(Yb.ensure((size_t)cs * (t - 1) * sizeof(double)));
+          double* Tp = T.as<double>();
+          for (int64_t q0 = 0; q0 < d; q0 += cs) {
+            const int64_t dq = cs < d - q0 ? cs : d - q0, r0 = q0 + dq, rest = t - r0;
+            { k_copy_lower_sym<<<nblk(dq * dq), 256, 0, s>>>(Tp + q0 * t + q0, t, dq, Gd.as<double>()); ::rbf::note_launch(); }
+            RBF_CUDA(cudaGetLastError());
+            RBF_TRY(spd_inverse_small(c, Gd.as<double>(), dq, s));
+            RBF_TRY(gemm_ff(c, false, true, dq, rest, dq, 1.0, Gd.as<double>(), dq, Tp + r0 * t + q0, t, 0.0,
+                            Yb.as<double>(), rest, s, 87));
+            RBF_TRY(gemm_ff(c, false, false, rest, rest, dq, -1.0, Tp + r0 * t + q0, t, Yb.as<double>(), rest, 1.0,
+                            Tp + r0 * t + r0, t, s, 87, true));
+          }
+        } else if (d <= SPD_SMALL_MAX) {
           // H_NN -= H_ND (H_DD^{-1} H_DN), with H_DD^{-1} by the one-CTA inverse
           Buf& Gd = c->scratch(84);
           Buf& Yb = c->scratch(85);
