@@ -14,48 +14,64 @@
 namespace rbf {
 namespace {
 
-constexpr int FT = 64;  // output tile
 constexpr int FK = 16;  // k chunk
-constexpr int FLD = FT + 4;
 
-// C = alpha op(A) op(B) + beta C, row-major; 256 threads, each a 4 x 4 block.
-// With part set, slice z of k ([z kc, (z + 1) kc)) writes its float64 partial
-// product to part[z][m][n] instead.  With lower set only the tiles on or below
-// the diagonal are computed (a symmetric result read from its lower triangle).
-__global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, bool lower, int64_t m, int64_t n, int64_t k,
-                                                 int64_t kc, double alpha, const double* __restrict__ A, int64_t lda,
-                                                 const double* __restrict__ B, int64_t ldb, double beta,
-                                                 double* __restrict__ Cm, int64_t ldc, double* __restrict__ part) {
-  if (lower && blockIdx.x > blockIdx.y) return;
-  __shared__ __align__(16) float Ah[FK][FLD], Al[FK][FLD], Bh[FK][FLD], Bl[FK][FLD];
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const int64_t i0 = (int64_t)blockIdx.y * FT, j0 = (int64_t)blockIdx.x * FT;
+// s + t += x y, with x, y as hi + lo: the leading product's rounding error
+// and the cross terms go to t, which is only added into s at the end
+__device__ __forceinline__ void ff_acc(float& sacc, float& tacc, FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+  const FF sum = ff_two_sum(sacc, p);
+  sacc = sum.hi;
+  tacc = __fadd_rn(tacc, __fadd_rn(sum.lo, e));
+}
+
+// C = alpha op(A) op(B) + beta C, row-major; a TM x TN tile per CTA of
+// TM TN / 16 threads, each a 4 x 4 block.  With part set, slice z of k
+// ([z kc, (z + 1) kc)) writes its float64 partial product to part[z][m][n]
+// instead.  With lower set only the tiles that reach the diagonal or below it
+// are computed (a symmetric result read from its lower triangle).
+template <int TM, int TN>
+__global__ void __launch_bounds__(TM * TN / 16) k_gemm_ff(bool ta, bool tb, bool lower, int64_t m, int64_t n,
+                                                          int64_t k, int64_t kc, double alpha,
+                                                          const double* __restrict__ A, int64_t lda,
+                                                          const double* __restrict__ B, int64_t ldb, double beta,
+                                                          double* __restrict__ Cm, int64_t ldc,
+                                                          double* __restrict__ part) {
+  constexpr int NT = TM * TN / 16, CX = TN / 4;
+  const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TN;
+  if (lower && j0 > i0 + TM - 1) return;
+  __shared__ __align__(16) float Ah[FK][TM + 4], Al[FK][TM + 4], Bh[FK][TN + 4], Bl[FK][TN + 4];
+  const int tid = threadIdx.x, ty = tid / CX, tx = tid % CX;
   const int64_t kb = (int64_t)blockIdx.z * kc, ke = kb + kc < k ? kb + kc : k;
-  FF acc[4][4];
+  float sa[4][4], ta4[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = {0.f, 0.f};
+    for (int v = 0; v < 4; ++v) sa[u][v] = ta4[u][v] = 0.f;
   for (int64_t k0 = kb; k0 < ke; k0 += FK) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q;  // 0 .. 1023
-      // A: row r of the tile, k index kk
+    for (int q = 0; q < TM * FK / NT; ++q) {
+      const int e = tid + NT * q;
       int r, kk;
-      if (ta) { r = e & 63; kk = e >> 6; }
-      else { kk = e & 15; r = e >> 4; }
+      if (ta) { r = e % TM; kk = e / TM; }
+      else { kk = e % FK; r = e / FK; }
       const int64_t gi = i0 + r, gk = k0 + kk;
       double a = 0.0;
       if (gi < m && gk < ke) a = ta ? A[gk * lda + gi] : A[gi * lda + gk];
       const FF af = ff_split(a);
       Ah[kk][r] = af.hi;
       Al[kk][r] = af.lo;
-      int cc;
-      if (tb) { kk = e & 15; cc = e >> 4; }
-      else { cc = e & 63; kk = e >> 6; }
-      const int64_t gj = j0 + cc, gk2 = k0 + kk;
+    }
+#pragma unroll
+    for (int q = 0; q < TN * FK / NT; ++q) {
+      const int e = tid + NT * q;
+      int cc, kk;
+      if (tb) { kk = e % FK; cc = e / FK; }
+      else { cc = e % TN; kk = e / TN; }
+      const int64_t gj = j0 + cc, gk = k0 + kk;
       double b = 0.0;
-      if (gj < n && gk2 < ke) b = tb ? B[gj * ldb + gk2] : B[gk2 * ldb + gj];
+      if (gj < n && gk < ke) b = tb ? B[gj * ldb + gk] : B[gk * ldb + gj];
       const FF bf = ff_split(b);
       Bh[kk][cc] = bf.hi;
       Bl[kk][cc] = bf.lo;
@@ -72,7 +88,7 @@ __global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, bool lower, i
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = ff_mac(acc[u][v], av[u], bv[v]);
+        for (int v = 0; v < 4; ++v) ff_acc(sa[u][v], ta4[u][v], av[u], bv[v]);
     }
     __syncthreads();
   }
@@ -84,11 +100,12 @@ __global__ void __launch_bounds__(256) k_gemm_ff(bool ta, bool tb, bool lower, i
     for (int v = 0; v < 4; ++v) {
       const int64_t j = j0 + tx * 4 + v;
       if (j >= n) continue;
+      const double r = (double)sa[u][v] + (double)ta4[u][v];
       if (part) {
-        part[((int64_t)blockIdx.z * m + i) * n + j] = ff_to_double(acc[u][v]);
+        part[((int64_t)blockIdx.z * m + i) * n + j] = r;
       } else {
         const double prev = beta != 0.0 ? Cm[i * ldc + j] : 0.0;
-        Cm[i * ldc + j] = alpha * ff_to_double(acc[u][v]) + beta * prev;
+        Cm[i * ldc + j] = alpha * r + beta * prev;
       }
     }
   }
@@ -156,18 +173,19 @@ __global__ void __launch_bounds__(256) k_csr_resm_ff(int64_t n, int64_t m, int64
   }
 }
 
-}  // namespace
-
-rbf_status gemm_ff(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
-                   int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s,
-                   int slot, bool lower) {
-  if (m <= 0 || n <= 0) return RBF_OK;
-  const int64_t tiles = ((m + FT - 1) / FT) * ((n + FT - 1) / FT);
-  // outputs that do not fill the GPU twice split k into slices of >= 128
+template <int TM, int TN>
+rbf_status gemm_ff_tiles(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                         int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc,
+                         cudaStream_t s, int slot, bool lower) {
+  constexpr int NT = TM * TN / 16;
+  const int64_t tiles = ((m + TM - 1) / TM) * ((n + TN - 1) / TN);
+  // outputs that do not give every SM about 1024 threads split k into slices
+  // of at least 64
+  const int64_t want = 152 * (1024 / NT);
   int64_t nsplit = 1;
-  if (!lower && tiles < 2 * 152 && k > 256) {
-    nsplit = (2 * 152 + tiles - 1) / tiles;
-    const int64_t most = k / 128;
+  if (!lower && tiles < want && k >= 128) {
+    nsplit = (want + tiles - 1) / tiles;
+    const int64_t most = k / 64;
     if (nsplit > most) nsplit = most;
   }
   int64_t kc = (k + nsplit - 1) / nsplit;
@@ -179,16 +197,31 @@ rbf_status gemm_ff(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, do
     RBF_TRY(pb.ensure((size_t)nsplit * m * n * sizeof(double)));
     part = pb.as<double>();
   }
-  dim3 grid((unsigned)((n + FT - 1) / FT), (unsigned)((m + FT - 1) / FT), (unsigned)nsplit);
-  { k_gemm_ff<<<grid, 256, 0, s>>>(ta, tb, lower, m, n, k, kc, alpha, A, lda, B, ldb, beta, Cm, ldc, part); ::rbf::note_launch(); }
+  dim3 grid((unsigned)((n + TN - 1) / TN), (unsigned)((m + TM - 1) / TM), (unsigned)nsplit);
+  { k_gemm_ff<TM, TN><<<grid, NT, 0, s>>>(ta, tb, lower, m, n, k, kc, alpha, A, lda, B, ldb, beta, Cm, ldc, part); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   if (part) {
-    if (lower) return fail(RBF_EINVAL, "gemm_ff: lower with split k");
     { k_gemm_ff_reduce<<<(unsigned)((m * n + 255) / 256), 256, 0, s>>>(m, n, (int)nsplit, part, alpha, beta, Cm,
                                                                       ldc); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   return RBF_OK;
+}
+
+}  // namespace
+
+rbf_status gemm_ff(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc, cudaStream_t s,
+                   int slot, bool lower) {
+  if (m <= 0 || n <= 0) return RBF_OK;
+  // the tile follows the output's shape: small, tall, wide or square
+  if (!lower && m <= 32 && n <= 32)
+    return gemm_ff_tiles<32, 32>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, s, slot, lower);
+  if (!lower && n <= 32)
+    return gemm_ff_tiles<128, 32>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, s, slot, lower);
+  if (!lower && m <= 32)
+    return gemm_ff_tiles<32, 128>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, s, slot, lower);
+  return gemm_ff_tiles<64, 64>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, s, slot, lower);
 }
 
 rbf_status csr_residual_ff(Ctx* c, const SpH& A, const double* X, const double* B, int64_t m, double* R,
