@@ -41,48 +41,67 @@ __global__ void __launch_bounds__(TM * TN / 16) k_gemm_ff(bool ta, bool tb, bool
   constexpr int NT = TM * TN / 16, CX = TN / 4;
   const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TN;
   if (lower && j0 > i0 + TM - 1) return;
-  __shared__ __align__(16) float Ah[FK][TM + 4], Al[FK][TM + 4], Bh[FK][TN + 4], Bl[FK][TN + 4];
+  // two stages: the global loads of chunk c + 1 are in flight while chunk c
+  // is multiplied, then split into the other stage (one barrier per chunk)
+  __shared__ __align__(16) float Ah[2][FK][TM + 4], Al[2][FK][TM + 4], Bh[2][FK][TN + 4], Bl[2][FK][TN + 4];
   const int tid = threadIdx.x, ty = tid / CX, tx = tid % CX;
   const int64_t kb = (int64_t)blockIdx.z * kc, ke = kb + kc < k ? kb + kc : k;
+  constexpr int LA = TM * FK / NT, LB = TN * FK / NT;
+  double ra[LA], rb[LB];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + NT * q;
+      const int r = ta ? e % TM : e / FK, kk = ta ? e / TM : e % FK;
+      const int64_t gi = i0 + r, gk = k0 + kk;
+      ra[q] = (gi < m && gk < ke) ? (ta ? A[gk * lda + gi] : A[gi * lda + gk]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + NT * q;
+      const int cc = tb ? e / FK : e % TN, kk = tb ? e % FK : e / TN;
+      const int64_t gj = j0 + cc, gk = k0 + kk;
+      rb[q] = (gj < n && gk < ke) ? (tb ? B[gj * ldb + gk] : B[gk * ldb + gj]) : 0.0;
+    }
+  };
+  auto store = [&](int st) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + NT * q;
+      const int r = ta ? e % TM : e / FK, kk = ta ? e / TM : e % FK;
+      const FF f = ff_split(ra[q]);
+      Ah[st][kk][r] = f.hi;
+      Al[st][kk][r] = f.lo;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + NT * q;
+      const int cc = tb ? e / FK : e % TN, kk = tb ? e % FK : e / TN;
+      const FF f = ff_split(rb[q]);
+      Bh[st][kk][cc] = f.hi;
+      Bl[st][kk][cc] = f.lo;
+    }
+  };
   float sa[4][4], ta4[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) sa[u][v] = ta4[u][v] = 0.f;
-  for (int64_t k0 = kb; k0 < ke; k0 += FK) {
-#pragma unroll
-    for (int q = 0; q < TM * FK / NT; ++q) {
-      const int e = tid + NT * q;
-      int r, kk;
-      if (ta) { r = e % TM; kk = e / TM; }
-      else { kk = e % FK; r = e / FK; }
-      const int64_t gi = i0 + r, gk = k0 + kk;
-      double a = 0.0;
-      if (gi < m && gk < ke) a = ta ? A[gk * lda + gi] : A[gi * lda + gk];
-      const FF af = ff_split(a);
-      Ah[kk][r] = af.hi;
-      Al[kk][r] = af.lo;
-    }
-#pragma unroll
-    for (int q = 0; q < TN * FK / NT; ++q) {
-      const int e = tid + NT * q;
-      int cc, kk;
-      if (tb) { kk = e % FK; cc = e / FK; }
-      else { cc = e % TN; kk = e / TN; }
-      const int64_t gj = j0 + cc, gk = k0 + kk;
-      double b = 0.0;
-      if (gj < n && gk < ke) b = tb ? B[gj * ldb + gk] : B[gk * ldb + gj];
-      const FF bf = ff_split(b);
-      Bh[kk][cc] = bf.hi;
-      Bl[kk][cc] = bf.lo;
-    }
-    __syncthreads();
+  int st = 0;
+  if (kb < ke) {
+    load(kb);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t k0 = kb; k0 < ke; k0 += FK, st ^= 1) {
+    const bool more = k0 + FK < ke;
+    if (more) load(k0 + FK);
 #pragma unroll 4
     for (int kk = 0; kk < FK; ++kk) {
-      const float4 ah = *reinterpret_cast<const float4*>(&Ah[kk][ty * 4]);
-      const float4 al = *reinterpret_cast<const float4*>(&Al[kk][ty * 4]);
-      const float4 bh = *reinterpret_cast<const float4*>(&Bh[kk][tx * 4]);
-      const float4 bl = *reinterpret_cast<const float4*>(&Bl[kk][tx * 4]);
+      const float4 ah = *reinterpret_cast<const float4*>(&Ah[st][kk][ty * 4]);
+      const float4 al = *reinterpret_cast<const float4*>(&Al[st][kk][ty * 4]);
+      const float4 bh = *reinterpret_cast<const float4*>(&Bh[st][kk][tx * 4]);
+      const float4 bl = *reinterpret_cast<const float4*>(&Bl[st][kk][tx * 4]);
       const FF av[4] = {{ah.x, al.x}, {ah.y, al.y}, {ah.z, al.z}, {ah.w, al.w}};
       const FF bv[4] = {{bh.x, bl.x}, {bh.y, bl.y}, {bh.z, bl.z}, {bh.w, bl.w}};
 #pragma unroll
@@ -90,6 +109,7 @@ __global__ void __launch_bounds__(TM * TN / 16) k_gemm_ff(bool ta, bool tb, bool
 #pragma unroll
         for (int v = 0; v < 4; ++v) ff_acc(sa[u][v], ta4[u][v], av[u], bv[v]);
     }
+    if (more) store(st ^ 1);
     __syncthreads();
   }
 #pragma unroll
