@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_mx_step(float* __restrict__ W, int64_t 
 constexpr int DF_THREADS = 256;
 constexpr int DF_MAXOWN = 64;            // band tiles one CTA may own
 constexpr int DF_NACC = 8;               // owned tiles whose running sums stay in shared memory
-constexpr int64_t DF_NMAX = 4096;        // largest block factored by the dataflow launch
+constexpr int64_t DF_NMAX = 16384;       // largest block factored by the dataflow launch (64 size buckets of 256)
 constexpr long long DF_SPIN = 1LL << 22;
 // dynamic shared memory (floats): two k-major staged tiles, or the diagonal
 // factorization's T, Z (64 x 65), Y (32 x 33), 1 / L_jj and the column buffer;
