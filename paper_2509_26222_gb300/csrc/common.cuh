@@ -327,6 +327,8 @@ rbf_status inv_solve_unit(Ctx* c, const float* Z, int64_t ldz, int64_t n, const 
                           cudaStream_t s);
 constexpr int SPD_SMALL_MAX = 128;  // largest order of spd_inverse_small (one CTA, shared memory)
 rbf_status spd_inverse_small(Ctx* c, double* G, int64_t m, cudaStream_t s);
+// the same in float-float arithmetic (ffgemm.cu), for the mixed-precision update
+rbf_status spd_inverse_small_ff(Ctx* c, double* G, int64_t m, cudaStream_t s);
 rbf_status chol_solve(Ctx* c, const double* H, const double* L, int64_t a, int64_t ld, double* b, bool refine,
                       cudaStream_t s, int64_t bw = BW_DENSE);
 void batch_destroy(Ctx* c);

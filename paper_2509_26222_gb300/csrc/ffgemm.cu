@@ -193,6 +193,70 @@ __global__ void __launch_bounds__(256) k_csr_resm_ff(int64_t n, int64_t m, int64
   }
 }
 
+// 1 / p to about 2^-46: the float32 reciprocal and one Newton-Raphson step
+// r + r (1 - p r), with the residual 1 - p r formed in float-float
+__device__ __forceinline__ FF ff_recip(FF p) {
+  const float r = __frcp_rn(p.hi);
+  const FF pr = ff_mul(p, {r, 0.f});
+  const FF e = ff_add({1.f, 0.f}, {-pr.hi, -pr.lo});
+  return ff_add({r, 0.f}, ff_mul({r, 0.f}, e));
+}
+
+// Inverse of a small SPD matrix (m <= SPD_SMALL_MAX) in one CTA of 512
+// threads by Gauss-Jordan elimination without pivoting (the pivots are the
+// diagonals of successive Schur complements, positive for an SPD matrix), in
+// float-float arithmetic: each of the m steps is one parallel update of all
+// m^2 entries between two barriers.  In place, row-major float64 in and out,
+// symmetrised on output.
+__global__ void __launch_bounds__(512) k_spd_inverse_small_ff(double* __restrict__ G, int m, int* __restrict__ flag) {
+  extern __shared__ float gjf[];  // hi and lo of A (m x (m + 1)), then the pivot column and row (hi, lo)
+  const int ld = m + 1;
+  float* Ah = gjf;
+  float* Al = Ah + m * ld;
+  float* ch = Al + m * ld;
+  float* cl = ch + m;
+  float* rh = cl + m;
+  float* rl = rh + m;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const FF v = ff_split(G[e]);
+    Ah[(e / m) * ld + e % m] = v.hi;
+    Al[(e / m) * ld + e % m] = v.lo;
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (tid < m) {
+      ch[tid] = Ah[tid * ld + k];
+      cl[tid] = Al[tid * ld + k];
+      rh[tid] = Ah[k * ld + tid];
+      rl[tid] = Al[k * ld + tid];
+    }
+    __syncthreads();
+    FF p = {rh[k], rl[k]};
+    if (!(p.hi > 0.f)) {
+      if (tid == 0) atomicOr(flag, DEV_NOT_SPD);
+      p = {1.f, 0.f};
+    }
+    const FF rp = ff_recip(p);
+    for (int i = tid >> 5; i < m; i += 16) {  // 16 x 32 threads
+      const FF fi = ff_mul({-ch[i], -cl[i]}, rp);
+      for (int j = tid & 31; j < m; j += 32) {
+        const FF pj = {rh[j], rl[j]};
+        FF v;
+        if (i == k) v = (j == k) ? rp : ff_mul(pj, rp);
+        else v = (j == k) ? fi : ff_add(ff_mul(fi, pj), {Ah[i * ld + j], Al[i * ld + j]});
+        Ah[i * ld + j] = v.hi;
+        Al[i * ld + j] = v.lo;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    G[e] = 0.5 * (ff_to_double({Ah[i * ld + j], Al[i * ld + j]}) + ff_to_double({Ah[j * ld + i], Al[j * ld + i]}));
+  }
+}
+
 template <int TM, int TN>
 rbf_status gemm_ff_tiles(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
                          int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc,
@@ -242,6 +306,21 @@ rbf_status gemm_ff(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t k, do
   if (!lower && m <= 32)
     return gemm_ff_tiles<32, 128>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, s, slot, lower);
   return gemm_ff_tiles<64, 64>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, s, slot, lower);
+}
+
+rbf_status spd_inverse_small_ff(Ctx* c, double* G, int64_t m, cudaStream_t s) {
+  if (m <= 0 || m > SPD_SMALL_MAX)
+    return fail(RBF_EINVAL, "spd_inverse_small_ff: m must be in [1, %d]", SPD_SMALL_MAX);
+  const size_t smem = (size_t)(2 * m * (m + 1) + 4 * m) * sizeof(float);
+  static bool attr[64] = {false};
+  if (!attr[c->device & 63]) {
+    const size_t mx = (size_t)(2 * SPD_SMALL_MAX * (SPD_SMALL_MAX + 1) + 4 * SPD_SMALL_MAX) * sizeof(float);
+    RBF_CUDA(cudaFuncSetAttribute(k_spd_inverse_small_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+    attr[c->device & 63] = true;
+  }
+  { k_spd_inverse_small_ff<<<1, 512, smem, s>>>(G, (int)m, c->dflag.as<int>()); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  return RBF_OK;
 }
 
 rbf_status csr_residual_ff(Ctx* c, const SpH& A, const double* X, const double* B, int64_t m, double* R,

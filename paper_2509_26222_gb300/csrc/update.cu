@@ -827,7 +827,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
                                                     1.0 / c->cfg.lambda, An.as<int32_t>(), Rl.as<int32_t>(), r,
                                                     Gb.as<double>()); ::rbf::note_launch(); }
       RBF_CUDA(cudaGetLastError());
-      if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, sC));
+      if (r <= SPD_SMALL_MAX && mixed) RBF_TRY(spd_inverse_small_ff(c, Gb.as<double>(), r, sC));
+      else if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, sC));
       else RBF_TRY(spd_inverse(c, Gb.as<double>(), r, sC, 43));
       { k_scatter_sym<<<nblk(r * r), 256, 0, sC>>>(Gb.as<double>(), r, r, Rl.as<int32_t>(), Hn.as<double>(),
                                                 ld); ::rbf::note_launch(); }
@@ -880,7 +881,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
           // Block elimination of D in chunks of at most SPD_SMALL_MAX: each
           // chunk's Schur complement is taken in the block the previous
           // chunks left, T[r, r] -= T[r, q] T[q, q]^{-1} T[r, q]^T, with the
-          // products in float-float arithmetic.  Only the lower triangle of T
+          // inverse and the products in float-float arithmetic.  Only the lower triangle of T
           // is kept current (the 64 x 64 tiles on or below the diagonal).
           Buf& Gd = c->scratch(84);
           Buf& Yb = c->scratch(85);
@@ -893,7 +894,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
             const int64_t dq = cs < d - q0 ? cs : d - q0, r0 = q0 + dq, rest = t - r0;
             { k_copy_lower_sym<<<nblk(dq * dq), 256, 0, s>>>(Tp + q0 * t + q0, t, dq, Gd.as<double>()); ::rbf::note_launch(); }
             RBF_CUDA(cudaGetLastError());
-            RBF_TRY(spd_inverse_small(c, Gd.as<double>(), dq, s));
+            RBF_TRY(spd_inverse_small_ff(c, Gd.as<double>(), dq, s));
             RBF_TRY(gemm_ff(c, false, true, dq, rest, dq, 1.0, Gd.as<double>(), dq, Tp + r0 * t + q0, t, 0.0,
                             Yb.as<double>(), rest, s, 87));
             RBF_TRY(gemm_ff(c, false, false, rest, rest, dq, -1.0, Tp + r0 * t + q0, t, Yb.as<double>(), rest, 1.0,
