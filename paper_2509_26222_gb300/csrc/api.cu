@@ -153,11 +153,72 @@ __global__ void k_scan_total(const Tin* in, Tout* out, int64_t n) {
   if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = (n > 0) ? out[n - 1] + (Tout)in[n - 1] : (Tout)0;
 }
 
+// The whole scan in one CTA of 1024 threads for short inputs: chunks of
+// 1024 x 8 elements in turn, each scanned in the block and offset by the
+// running total of the chunks before it; out[n] = the total.
+constexpr int SCAN1_THREADS = 1024;
+constexpr int64_t SCAN1_MAX = 32 * SCAN1_THREADS * SCAN_PER_THREAD;
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_one(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                             int64_t n) {
+  __shared__ Tout warp_tot[SCAN1_THREADS / 32];
+  __shared__ Tout carry_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < n; c0 += (int64_t)SCAN1_THREADS * SCAN_PER_THREAD) {
+    const int64_t base = c0 + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+    const Tout carry = carry_s;  // read before warp 0 rewrites it (after the next barrier)
+    Tout v[SCAN_PER_THREAD];
+    Tout sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+      const int64_t i = base + k;
+      v[k] = (i < n) ? (Tout)in[i] : (Tout)0;
+      sum += v[k];
+    }
+    Tout inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Tout y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      const Tout t = warp_tot[lane];
+      Tout ti = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const Tout y = __shfl_up_sync(0xffffffffu, ti, o);
+        if (lane >= o) ti += y;
+      }
+      warp_tot[lane] = ti - t;  // exclusive
+      if (lane == 31) carry_s = carry + ti;
+    }
+    __syncthreads();
+    Tout run = carry + warp_tot[wid] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+      const int64_t i = base + k;
+      if (i < n) out[i] = run;
+      run += v[k];
+    }
+    __syncthreads();  // warp_tot and carry_s are rewritten by the next chunk
+  }
+  if (threadIdx.x == 0) out[n] = carry_s;
+}
+
 template <class Tin, class Tout>
 static rbf_status scan_impl(Ctx* c, const Tin* in, Tout* out, int64_t n, cudaStream_t s,
                             int slot) {
   if (n <= 0) {
     { k_scan_total<Tin, Tout><<<1, 1, 0, s>>>(in, out, 0); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    return RBF_OK;
+  }
+  if (n <= SCAN1_MAX) {
+    { k_scan_one<Tin, Tout><<<1, SCAN1_THREADS, 0, s>>>(in, out, n); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     return RBF_OK;
   }

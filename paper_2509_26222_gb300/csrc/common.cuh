@@ -119,8 +119,8 @@ struct Ctx {
   int64_t inv_max = 4096;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
   int64_t bw_lf = BW_DENSE_CTX;  // half-bandwidth of the float32 factor Lf
-  cudaStream_t bs[2] = {};           // side streams of the block stage
-  cudaEvent_t bev[3] = {};           // fork and joins of the block stage
+  cudaStream_t bs[3] = {};           // side streams of the block stage (bs[2]: high priority)
+  cudaEvent_t bev[4] = {};           // fork and joins of the block stage
   bool la_ok = true;                 // look-ahead factorization allowed
   bool df_ok = true;                 // one-launch dataflow factorization allowed
   int8_t fchoice[64] = {};           // per size bucket of 256: 0 untimed, 1 launch chain, 2 dataflow

@@ -742,17 +742,60 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       RBF_CUDA(cudaMemsetAsync(U0.p, 0, U0.bytes, s));
     }
   }
+  // Schur complement, first part (caller's stream, before the other streams
+  // are fed): H_SS moves over unchanged, the rows N of S coupled to some
+  // leaving center are listed, and their count goes to the host, so that the
+  // host reads it after the other streams' work has been issued.
+  Buf& cpl = c->scratch(74);
+  Buf& cpp = c->scratch(75);
+  Buf& perm = c->scratch(40);
+  Buf& Nn = c->scratch(76);
+  int32_t* h32 = (int32_t*)c->host_small;
+  if (d > 0 && sN > 0) {
+    StageTimer st_sc0(c, RBF_STAGE_SCHUR, s, 0.0);
+    { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(),
+                                             sN, Hn.as<double>(), ld); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    RBF_TRY(cpl.ensure((size_t)(sN + 1) * sizeof(int32_t)));
+    RBF_TRY(cpp.ensure((size_t)(sN + 1) * sizeof(int32_t)));
+    RBF_TRY(perm.ensure((size_t)(d + sN) * sizeof(int32_t)));
+    RBF_TRY(Nn.ensure((size_t)(sN + 1) * sizeof(int32_t)));
+    if (c->Hs.valid && c->Hs.n == ap) {
+      { k_coupled_csr<<<nblk(sN * 32), 256, 0, s>>>(c->Hs.rp.as<int32_t>(), c->Hs.col.as<int32_t>(),
+                                                   Sl.as<int32_t>(), sN, flD, cpl.as<int32_t>()); ::rbf::note_launch(); }
+    } else {
+      { k_coupled<<<nblk(sN * 32), 256, 0, s>>>(c->H.as<double>(), c->ldH, ap, Sl.as<int32_t>(), sN, flD,
+                                              cpl.as<int32_t>()); ::rbf::note_launch(); }
+    }
+    RBF_CUDA(cudaGetLastError());
+    RBF_TRY(scan_i32(c, cpl.as<int32_t>(), cpp.as<int32_t>(), sN, s, 77));
+    RBF_CUDA(cudaMemcpyAsync(perm.p, Dl.p, (size_t)d * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    { k_pick<<<nblk(sN), 256, 0, s>>>(cpl.as<int32_t>(), cpp.as<int32_t>(), sN, Sl.as<int32_t>(),
+                                    Sn.as<int32_t>(), perm.as<int32_t>() + d, Nn.as<int32_t>()); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    RBF_CUDA(cudaMemcpyAsync(h32 + 4, cpp.as<int32_t>() + sN, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  }
   const bool par = mixed && e_returning <= SPD_SMALL_MAX;
-  cudaStream_t sA = s, sC = s;
+  // The Schur chain is the longest of the block stage; its stream has the
+  // highest priority, so that its small kernels are not queued behind the
+  // second wave of the covariance block's product.
+  cudaStream_t sA = s, sB = s, sC = s;
   if (par) {
     for (int q = 0; q < 2; ++q)
       if (!c->bs[q]) RBF_CUDA(cudaStreamCreateWithFlags(&c->bs[q], cudaStreamNonBlocking));
+    if (!c->bs[2]) {
+      int least = 0, greatest = 0;
+      RBF_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      RBF_CUDA(cudaStreamCreateWithPriority(&c->bs[2], cudaStreamNonBlocking, greatest));
+    }
     for (auto& ev : c->bev)
       if (!ev) RBF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     sA = c->bs[0];
+    sB = c->bs[2];
     sC = c->bs[1];
     RBF_CUDA(cudaEventRecord(c->bev[0], s));
     RBF_CUDA(cudaStreamWaitEvent(sA, c->bev[0], 0));
+    RBF_CUDA(cudaStreamWaitEvent(sB, c->bev[0], 0));
     RBF_CUDA(cudaStreamWaitEvent(sC, c->bev[0], 0));
   }
   if (d > 0) {
@@ -773,6 +816,74 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
       RBF_TRY(gemm_f64(c, true, false, d, d, ap, 1.0, Y.as<double>(), d, Y.as<double>(), d, 0.0,
                        Pdd.as<double>(), d, s));
     }
+  }
+  // Schur complement, second part (stream sB), issued before the Gram
+  // and the entering centers: its chain is the longest of the block stage
+  if (d > 0) {
+    StageTimer st_sc(c, RBF_STAGE_SCHUR, sB, 0.0);
+    if (sN > 0) {
+      // H_S = H_SS - H_SD H_DD^{-1} H_DS.  H_SS moves over unchanged; only the
+      // rows N of S coupled to some leaving center change: T = H_prev on
+      // [D; N], and d steps of Cholesky leave the new H_NN in T[d:, d:].
+      // (the coupled rows N and their count were found before the fork)
+      RBF_CUDA(cudaStreamSynchronize(s));
+      const int64_t nN = h32[4];
+      if (nN > 0) {
+        const int64_t t = d + nN;
+        Buf& T = c->scratch(41);
+        RBF_TRY(T.ensure((size_t)t * t * sizeof(double)));
+        { k_gather_sym<<<nblk(t * t), 256, 0, sB>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), t,
+                                                 T.as<double>(), t); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+        if (mixed) {
+          // Block elimination of D in chunks of at most SPD_SMALL_MAX: each
+          // chunk's Schur complement is taken in the block the previous
+          // chunks left, T[r, r] -= T[r, q] T[q, q]^{-1} T[r, q]^T, with the
+          // inverse and the products in float-float arithmetic.  Only the lower triangle of T
+          // is kept current (the 64 x 64 tiles on or below the diagonal).
+          Buf& Gd = c->scratch(84);
+          Buf& Yb = c->scratch(85);
+          const int64_t nc = (d + SPD_SMALL_MAX - 1) / SPD_SMALL_MAX;
+          const int64_t cs = (d + nc - 1) / nc;
+          RBF_TRY(Gd.ensure((size_t)cs * cs * sizeof(double)));
+          RBF_TRY(Yb.ensure((size_t)cs * (t - 1) * sizeof(double)));
+          double* Tp = T.as<double>();
+          for (int64_t q0 = 0; q0 < d; q0 += cs) {
+            const int64_t dq = cs < d - q0 ? cs : d - q0, r0 = q0 + dq, rest = t - r0;
+            { k_copy_lower_sym<<<nblk(dq * dq), 256, 0, sB>>>(Tp + q0 * t + q0, t, dq, Gd.as<double>()); ::rbf::note_launch(); }
+            RBF_CUDA(cudaGetLastError());
+            RBF_TRY(spd_inverse_small_ff(c, Gd.as<double>(), dq, sB));
+            RBF_TRY(gemm_ff(c, false, true, dq, rest, dq, 1.0, Gd.as<double>(), dq, Tp + r0 * t + q0, t, 0.0,
+                            Yb.as<double>(), rest, sB, 87));
+            RBF_TRY(gemm_ff(c, false, false, rest, rest, dq, -1.0, Tp + r0 * t + q0, t, Yb.as<double>(), rest, 1.0,
+                            Tp + r0 * t + r0, t, sB, 87, true));
+          }
+        } else if (d <= SPD_SMALL_MAX) {
+          // H_NN -= H_ND (H_DD^{-1} H_DN), with H_DD^{-1} by the one-CTA inverse
+          Buf& Gd = c->scratch(84);
+          Buf& Yb = c->scratch(85);
+          RBF_TRY(Gd.ensure((size_t)d * d * sizeof(double)));
+          RBF_TRY(Yb.ensure((size_t)d * nN * sizeof(double)));
+          { k_copy_block<<<nblk(d * d), 256, 0, sB>>>(T.as<double>(), t, d, d, Gd.as<double>(), d); ::rbf::note_launch(); }
+          RBF_CUDA(cudaGetLastError());
+          RBF_TRY(spd_inverse_small(c, Gd.as<double>(), d, sB));
+          RBF_TRY(gemm_f64(c, false, false, d, nN, d, 1.0, Gd.as<double>(), d, T.as<double>() + d, t, 0.0,
+                           Yb.as<double>(), nN, sB, 87));
+          RBF_TRY(gemm_f64(c, false, false, nN, nN, d, -1.0, T.as<double>() + d * t, t, Yb.as<double>(), nN, 1.0,
+                           T.as<double>() + d * t + d, t, sB, 87));
+        } else {
+          RBF_TRY(potrf_lower(c, T.as<double>(), t, t, d, false, sB));
+        }
+        { k_scatter_sym<<<nblk(nN * nN), 256, 0, sB>>>(T.as<double>() + d * t + d, t, nN, Nn.as<int32_t>(),
+                                                    Hn.as<double>(), ld); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+      }
+    }
+  } else if (sN > 0) {
+    // nobody leaves: the staying block is the previous information matrix
+    { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(), sN,
+                                             Hn.as<double>(), ld); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
   }
   // m~ m~^T and m~ e: exact integer accumulation into cleared accumulators
   // (added to H' once the block stage has written it)
@@ -836,103 +947,14 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     }
   }
 
-  if (d > 0) {
-    StageTimer st_sc(c, RBF_STAGE_SCHUR, s, 0.0);
-    if (sN > 0) {
-      // H_S = H_SS - H_SD H_DD^{-1} H_DS.  H_SS moves over unchanged; only the
-      // rows N of S coupled to some leaving center change: T = H_prev on
-      // [D; N], and d steps of Cholesky leave the new H_NN in T[d:, d:].
-      { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(),
-                                               sN, Hn.as<double>(), ld); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      Buf& cpl = c->scratch(74);
-      Buf& cpp = c->scratch(75);
-      Buf& perm = c->scratch(40);
-      Buf& Nn = c->scratch(76);
-      RBF_TRY(cpl.ensure((size_t)(sN + 1) * sizeof(int32_t)));
-      RBF_TRY(cpp.ensure((size_t)(sN + 1) * sizeof(int32_t)));
-      RBF_TRY(perm.ensure((size_t)(d + sN) * sizeof(int32_t)));
-      RBF_TRY(Nn.ensure((size_t)(sN + 1) * sizeof(int32_t)));
-      if (c->Hs.valid && c->Hs.n == ap) {
-        { k_coupled_csr<<<nblk(sN * 32), 256, 0, s>>>(c->Hs.rp.as<int32_t>(), c->Hs.col.as<int32_t>(),
-                                                     Sl.as<int32_t>(), sN, flD, cpl.as<int32_t>()); ::rbf::note_launch(); }
-      } else {
-        { k_coupled<<<nblk(sN * 32), 256, 0, s>>>(c->H.as<double>(), c->ldH, ap, Sl.as<int32_t>(), sN, flD,
-                                                cpl.as<int32_t>()); ::rbf::note_launch(); }
-      }
-      RBF_CUDA(cudaGetLastError());
-      RBF_TRY(scan_i32(c, cpl.as<int32_t>(), cpp.as<int32_t>(), sN, s, 77));
-      RBF_CUDA(cudaMemcpyAsync(perm.p, Dl.p, (size_t)d * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-      { k_pick<<<nblk(sN), 256, 0, s>>>(cpl.as<int32_t>(), cpp.as<int32_t>(), sN, Sl.as<int32_t>(),
-                                      Sn.as<int32_t>(), perm.as<int32_t>() + d, Nn.as<int32_t>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      int32_t* h32 = (int32_t*)c->host_small;
-      RBF_CUDA(cudaMemcpyAsync(h32 + 4, cpp.as<int32_t>() + sN, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      RBF_CUDA(cudaStreamSynchronize(s));
-      const int64_t nN = h32[4];
-      if (nN > 0) {
-        const int64_t t = d + nN;
-        Buf& T = c->scratch(41);
-        RBF_TRY(T.ensure((size_t)t * t * sizeof(double)));
-        { k_gather_sym<<<nblk(t * t), 256, 0, s>>>(c->H.as<double>(), c->ldH, perm.as<int32_t>(), t,
-                                                 T.as<double>(), t); ::rbf::note_launch(); }
-        RBF_CUDA(cudaGetLastError());
-        if (mixed) {
-          // Block elimination of D in chunks of at most SPD_SMALL_MAX: each
-          // chunk's Schur complement is taken in the block the previous
-          // chunks left, T[r, r] -= T[r, q] T[q, q]^{-1} T[r, q]^T, with the
-          // inverse and the products in float-float arithmetic.  Only the lower triangle of T
-          // is kept current (the 64 x 64 tiles on or below the diagonal).
-          Buf& Gd = c->scratch(84);
-          Buf& Yb = c->scratch(85);
-          const int64_t nc = (d + SPD_SMALL_MAX - 1) / SPD_SMALL_MAX;
-          const int64_t cs = (d + nc - 1) / nc;
-          RBF_TRY(Gd.ensure((size_t)cs * cs * sizeof(double)));
-          RBF_TRY(Yb.ensure((size_t)cs * (t - 1) * sizeof(double)));
-          double* Tp = T.as<double>();
-          for (int64_t q0 = 0; q0 < d; q0 += cs) {
-            const int64_t dq = cs < d - q0 ? cs : d - q0, r0 = q0 + dq, rest = t - r0;
-            { k_copy_lower_sym<<<nblk(dq * dq), 256, 0, s>>>(Tp + q0 * t + q0, t, dq, Gd.as<double>()); ::rbf::note_launch(); }
-            RBF_CUDA(cudaGetLastError());
-            RBF_TRY(spd_inverse_small_ff(c, Gd.as<double>(), dq, s));
-            RBF_TRY(gemm_ff(c, false, true, dq, rest, dq, 1.0, Gd.as<double>(), dq, Tp + r0 * t + q0, t, 0.0,
-                            Yb.as<double>(), rest, s, 87));
-            RBF_TRY(gemm_ff(c, false, false, rest, rest, dq, -1.0, Tp + r0 * t + q0, t, Yb.as<double>(), rest, 1.0,
-                            Tp + r0 * t + r0, t, s, 87, true));
-          }
-        } else if (d <= SPD_SMALL_MAX) {
-          // H_NN -= H_ND (H_DD^{-1} H_DN), with H_DD^{-1} by the one-CTA inverse
-          Buf& Gd = c->scratch(84);
-          Buf& Yb = c->scratch(85);
-          RBF_TRY(Gd.ensure((size_t)d * d * sizeof(double)));
-          RBF_TRY(Yb.ensure((size_t)d * nN * sizeof(double)));
-          { k_copy_block<<<nblk(d * d), 256, 0, s>>>(T.as<double>(), t, d, d, Gd.as<double>(), d); ::rbf::note_launch(); }
-          RBF_CUDA(cudaGetLastError());
-          RBF_TRY(spd_inverse_small(c, Gd.as<double>(), d, s));
-          RBF_TRY(gemm_f64(c, false, false, d, nN, d, 1.0, Gd.as<double>(), d, T.as<double>() + d, t, 0.0,
-                           Yb.as<double>(), nN, s, 87));
-          RBF_TRY(gemm_f64(c, false, false, nN, nN, d, -1.0, T.as<double>() + d * t, t, Yb.as<double>(), nN, 1.0,
-                           T.as<double>() + d * t + d, t, s, 87));
-        } else {
-          RBF_TRY(potrf_lower(c, T.as<double>(), t, t, d, false, s));
-        }
-        { k_scatter_sym<<<nblk(nN * nN), 256, 0, s>>>(T.as<double>() + d * t + d, t, nN, Nn.as<int32_t>(),
-                                                    Hn.as<double>(), ld); ::rbf::note_launch(); }
-        RBF_CUDA(cudaGetLastError());
-      }
-    }
-  } else if (sN > 0) {
-    // nobody leaves: the staying block is the previous information matrix
-    { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(), sN,
-                                             Hn.as<double>(), ld); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-  }
 
   if (par) {
     RBF_CUDA(cudaEventRecord(c->bev[1], sA));
     RBF_CUDA(cudaEventRecord(c->bev[2], sC));
+    RBF_CUDA(cudaEventRecord(c->bev[3], sB));
     RBF_CUDA(cudaStreamWaitEvent(s, c->bev[1], 0));
     RBF_CUDA(cudaStreamWaitEvent(s, c->bev[2], 0));
+    RBF_CUDA(cudaStreamWaitEvent(s, c->bev[3], 0));
   }
   delete st_blk;
   // 7. + m~ m~^T and u = m~ e (accumulated above, beside the block stage)
