@@ -157,21 +157,6 @@ __global__ void k_compact(const int32_t* __restrict__ mark, const int32_t* __res
   }
 }
 
-// flag[l] = (other_g2l[ids[l]] >= 0) == want_member
-__global__ void k_member_flag(const int32_t* __restrict__ ids, int64_t a, const int32_t* __restrict__ other_g2l,
-                              int want_member, int32_t* __restrict__ flag) {
-  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= a) return;
-  int in = other_g2l[ids[l]] >= 0;
-  flag[l] = (in == want_member) ? 1 : 0;
-}
-
-__global__ void k_list_from_flags(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
-                                  int64_t a, int32_t* __restrict__ list) {
-  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l < a && flag[l]) list[pos[l]] = (int32_t)l;
-}
-
 // ---------------------------------------------------------------------------
 // m~ entries, innovation, transposed (center-major) lists
 // ---------------------------------------------------------------------------
@@ -437,19 +422,116 @@ __global__ void k_blk_assign(BlkRef* __restrict__ ref, const int32_t* __restrict
 }
 
 // P[u][v] = 0.5 (X[pos[u]][v] + X[pos[v]][u]) for X = H^{-1} E_pos (n x k)
-// Count the entering centers (lpos[0 .. *e_count)) that left some earlier block.
-// The list length is only known on the device here, so it is read from
-// e_count; both indirections are range-checked.
-__global__ void k_count_departed(const int32_t* __restrict__ ids, int64_t a, const int32_t* __restrict__ lpos,
-                                 const int32_t* __restrict__ e_count, const int32_t* __restrict__ departed,
-                                 int64_t M, int32_t* __restrict__ count) {
-  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= *e_count) return;
-  int32_t l = lpos[u];
-  if (l < 0 || l >= a) return;
-  int32_t id = ids[l];
-  if (id < 0 || id >= M) return;
-  if (departed[id]) atomicAdd(count, 1);
+// Exclusive scan of one int per thread over a CTA of SL_THREADS threads;
+// returns the total.  Ends with a barrier, so ws can be reused right away.
+constexpr int SL_THREADS = 1024;
+__device__ __forceinline__ int sl_block_scan(int v, int& excl, int* ws) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int t = ws[lane];
+    int ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    ws[lane] = ti - t;
+    if (lane == 31) ws[32] = ti;
+  }
+  __syncthreads();
+  excl = ws[wid] + inc - v;
+  const int tot = ws[32];
+  __syncthreads();
+  return tot;
+}
+
+// The leaving (D), staying (S) and entering (E) sets of one update in one
+// CTA: previous-local positions of D and S and new-local positions of E and
+// of the staying centers (Sn), each in ascending order, the leaving flags over
+// the previous block, and cnt = {|D|, |S|, |E|, entering centers that left
+// some earlier block}.
+__global__ void __launch_bounds__(SL_THREADS) k_set_lists(const int32_t* __restrict__ Ap, int64_t ap,
+                                                          const int32_t* __restrict__ An, int64_t an,
+                                                          const int32_t* __restrict__ g2l_new,
+                                                          const int32_t* __restrict__ g2l_prev,
+                                                          const int32_t* __restrict__ departed, int64_t M,
+                                                          int32_t* __restrict__ flD, int32_t* __restrict__ Dl,
+                                                          int32_t* __restrict__ Sl, int32_t* __restrict__ El,
+                                                          int32_t* __restrict__ Sn, int32_t* __restrict__ cnt) {
+  __shared__ int ws[33];
+  constexpr int PER = 8;
+  int nS = 0;  // staying centers seen so far (uniform)
+  for (int64_t c0 = 0; c0 < ap; c0 += (int64_t)SL_THREADS * PER) {
+    const int64_t b = c0 + (int64_t)threadIdx.x * PER;
+    int in[PER], k = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int64_t l = b + q;
+      int v = 0;
+      if (l < ap) {
+        const int32_t id = Ap[l];
+        v = (id >= 0 && id < M && g2l_new[id] >= 0) ? 1 : 0;
+      }
+      in[q] = v;
+      k += v;
+    }
+    int ex;
+    const int tot = sl_block_scan(k, ex, ws);
+    int ps = nS + ex;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int64_t l = b + q;
+      if (l >= ap) break;
+      flD[l] = 1 - in[q];
+      if (in[q]) Sl[ps++] = (int32_t)l;
+      else Dl[l - ps] = (int32_t)l;
+    }
+    nS += tot;
+  }
+  int nSn = 0, nret = 0;
+  for (int64_t c0 = 0; c0 < an; c0 += (int64_t)SL_THREADS * PER) {
+    const int64_t b = c0 + (int64_t)threadIdx.x * PER;
+    int in[PER], k = 0, r = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int64_t l = b + q;
+      int v = 0;
+      if (l < an) {
+        const int32_t id = An[l];
+        const bool ok = id >= 0 && id < M;
+        v = (ok && g2l_prev[id] >= 0) ? 1 : 0;
+        if (ok && !v && departed[id]) ++r;
+      }
+      in[q] = v;
+      k += v;
+    }
+    int ex, exr;
+    const int tot = sl_block_scan(k, ex, ws);
+    nret += sl_block_scan(r, exr, ws);
+    int ps = nSn + ex;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int64_t l = b + q;
+      if (l >= an) break;
+      if (in[q]) Sn[ps++] = (int32_t)l;
+      else El[l - ps] = (int32_t)l;
+    }
+    nSn += tot;
+  }
+  if (threadIdx.x == 0) {
+    cnt[0] = (int32_t)(ap - nS);
+    cnt[1] = nS;
+    cnt[2] = (int32_t)(an - nSn);
+    cnt[3] = nret;
+  }
 }
 
 // ret[q] = 1 if entering center q (new-local El[q]) left an earlier block
@@ -621,28 +703,17 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   // 3. relation to the previous block: S (stay), D (leave), E (enter)
   const int64_t ap = c->a;
   Buf& fl = c->scratch(6);
-  Buf& fpos = c->scratch(7);
   Buf& Dl = c->scratch(8);   // prev-local positions of leaving centers
   Buf& Sl = c->scratch(9);   // prev-local positions of staying centers
   Buf& El = c->scratch(11);  // new-local positions of entering centers
   Buf& Sn = c->scratch(12);  // new-local positions of staying centers
   int64_t amax = (ap > M ? ap : M);
   RBF_TRY(fl.ensure((size_t)(amax + 1) * sizeof(int32_t)));
-  RBF_TRY(fpos.ensure((size_t)(amax + 1) * sizeof(int32_t) * 4));
   RBF_TRY(Dl.ensure((size_t)(amax + 1) * sizeof(int32_t)));
   RBF_TRY(Sl.ensure((size_t)(amax + 1) * sizeof(int32_t)));
   RBF_TRY(El.ensure((size_t)(amax + 1) * sizeof(int32_t)));
   RBF_TRY(Sn.ensure((size_t)(amax + 1) * sizeof(int32_t)));
-  int32_t* fp = fpos.as<int32_t>();
-  int32_t* fpD = fp;                  // scan outputs, (ap+1) or (a+1) each
-  int32_t* fpS = fp + (amax + 1);
-  int32_t* fpE = fp + 2 * (amax + 1);
-  int32_t* fpSn = fp + 3 * (amax + 1);
-  Buf& fl2 = c->scratch(13);
-  RBF_TRY(fl2.ensure((size_t)(amax + 1) * sizeof(int32_t) * 2));
-  int32_t* flD = fl.as<int32_t>();
-  int32_t* flS = fl2.as<int32_t>();
-  int32_t* flE = fl2.as<int32_t>() + (amax + 1);
+  int32_t* flD = fl.as<int32_t>();  // leaving flags over the previous block
   // sizes to the host: a, d, s, e
   int64_t* hs = c->host_small;
   RBF_CUDA(cudaMemcpyAsync(hs + 0, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -651,37 +722,15 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   if (an == 0) return RBF_OK;
   int64_t d = 0, sN = 0, e = an, e_returning = 0;
   if (ap > 0) {
-    { k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 0, flD); ::rbf::note_launch(); }
-    { k_member_flag<<<nblk(ap), 256, 0, s>>>(c->A.as<int32_t>(), ap, g2ln.as<int32_t>(), 1, flS); ::rbf::note_launch(); }
-    { k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 0, flE); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-    RBF_TRY(scan_i32(c, flD, fpD, ap, s, 48));
-    RBF_TRY(scan_i32(c, flS, fpS, ap, s, 48));
-    RBF_TRY(scan_i32(c, flE, fpE, an, s, 48));
-    // staying centers in new-local positions: flag = member of the previous block
-    Buf& flSn = c->scratch(14);
-    RBF_TRY(flSn.ensure((size_t)(an + 1) * sizeof(int32_t)));
-    { k_member_flag<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, c->g2l.as<int32_t>(), 1,
-                                           flSn.as<int32_t>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-    RBF_TRY(scan_i32(c, flSn.as<int32_t>(), fpSn, an, s, 48));
-    { k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flD, fpD, ap, Dl.as<int32_t>()); ::rbf::note_launch(); }
-    { k_list_from_flags<<<nblk(ap), 256, 0, s>>>(flS, fpS, ap, Sl.as<int32_t>()); ::rbf::note_launch(); }
-    { k_list_from_flags<<<nblk(an), 256, 0, s>>>(flE, fpE, an, El.as<int32_t>()); ::rbf::note_launch(); }
-    { k_list_from_flags<<<nblk(an), 256, 0, s>>>(flSn.as<int32_t>(), fpSn, an, Sn.as<int32_t>()); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
     int32_t* h32 = (int32_t*)hs;
-    // entering centers that left some earlier block (their stored covariance may be coupled)
     Buf& cnt = c->scratch(53);
-    RBF_TRY(cnt.ensure(sizeof(int32_t)));
-    RBF_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
-    { k_count_departed<<<nblk(an), 256, 0, s>>>(An.as<int32_t>(), an, El.as<int32_t>(), fpE + an,
-                                                 c->departed.as<int32_t>(), M, cnt.as<int32_t>()); ::rbf::note_launch(); }
+    RBF_TRY(cnt.ensure(4 * sizeof(int32_t)));
+    { k_set_lists<<<1, SL_THREADS, 0, s>>>(c->A.as<int32_t>(), ap, An.as<int32_t>(), an, g2ln.as<int32_t>(),
+                                          c->g2l.as<int32_t>(), c->departed.as<int32_t>(), M, flD,
+                                          Dl.as<int32_t>(), Sl.as<int32_t>(), El.as<int32_t>(), Sn.as<int32_t>(),
+                                          cnt.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    RBF_CUDA(cudaMemcpyAsync(h32 + 0, fpD + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RBF_CUDA(cudaMemcpyAsync(h32 + 1, fpS + ap, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RBF_CUDA(cudaMemcpyAsync(h32 + 2, fpE + an, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RBF_CUDA(cudaMemcpyAsync(h32 + 3, cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaMemcpyAsync(h32, cnt.p, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaStreamSynchronize(s));
     d = h32[0];
     sN = h32[1];
@@ -690,9 +739,6 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     if (sN + e != an || sN + d != ap) return fail(RBF_ECUDA, "inconsistent active-set bookkeeping");
   } else {
     // every new center enters
-    Buf& flSn = c->scratch(14);
-    RBF_TRY(flSn.ensure((size_t)(an + 1) * sizeof(int32_t)));
-    RBF_CUDA(cudaMemsetAsync(flSn.p, 0, (size_t)(an + 1) * sizeof(int32_t), s));
     // El = 0..an-1
     std::vector<int32_t> iota((size_t)an);
     for (int64_t l = 0; l < an; ++l) iota[l] = (int32_t)l;
