@@ -83,9 +83,12 @@ double assembly_radius(const rbf_config& cfg, double noise) {
 }
 
 rbf_status read_dev_flag(Ctx* c, cudaStream_t s, int* flag) {
-  int h = 0;
-  RBF_CUDA(cudaMemcpyAsync(&h, c->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // the pinned word of a top-level context (sub-contexts of a batch have none)
+  int local = 0;
+  int32_t* hp = c->host_small ? (int32_t*)c->host_small + 20 : &local;
+  RBF_CUDA(cudaMemcpyAsync(hp, c->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBF_CUDA(cudaStreamSynchronize(s));
+  const int h = *hp;
   *flag = h;
   if (h) RBF_CUDA(cudaMemsetAsync(c->dflag.p, 0, sizeof(int), s));
   return RBF_OK;

@@ -323,6 +323,9 @@ rbf_status csr_residual_ff(Ctx* c, const SpH& A, const double* X, const double* 
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
                        cudaStream_t s);
 rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, int64_t m, cudaStream_t s);
+// X += Z^T (Z R), float64 R and X, at most 8 right-hand sides (inverse.cu)
+rbf_status inv_solve_acc(Ctx* c, const float* Z, int64_t ldz, int64_t n, const double* R, double* X, int64_t m,
+                         cudaStream_t s);
 rbf_status inv_solve_unit(Ctx* c, const float* Z, int64_t ldz, int64_t n, const int32_t* pos, int64_t m, float* F,
                           cudaStream_t s);
 constexpr int SPD_SMALL_MAX = 128;  // largest order of spd_inverse_small (one CTA, shared memory)

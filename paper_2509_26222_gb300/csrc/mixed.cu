@@ -890,16 +890,21 @@ rbf_status mixed_solve(Ctx* c, const double* H, int64_t ldh, const SpH* Hs, cons
   const double* R = B;  // first sweep: X = 0, so R = B
   unsigned nb = (unsigned)((tot + 255) / 256);
   for (int it = 0; it < sweeps; ++it) {
-    { k_f64_to_f32<<<nb, 256, 0, s>>>(R, F, tot); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
-    if (Zi) {
-      RBF_TRY(inv_solve(c, Zi, ldw, n, F, m, s));
+    if (Zi && m <= 8) {
+      // X += Z^T Z R, the roundings inside the two matrix-vector launches
+      RBF_TRY(inv_solve_acc(c, Zi, ldw, n, R, X, m, s));
     } else {
-      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, false, s, bw));
-      RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, true, s, bw));
+      { k_f64_to_f32<<<nb, 256, 0, s>>>(R, F, tot); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
+      if (Zi) {
+        RBF_TRY(inv_solve(c, Zi, ldw, n, F, m, s));
+      } else {
+        RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, false, s, bw));
+        RBF_TRY(trsm32(c, W, n, ldw, Zd, F, m, m, true, s, bw));
+      }
+      { k_add_f32_to_f64<<<nb, 256, 0, s>>>(X, F, tot); ::rbf::note_launch(); }
+      RBF_CUDA(cudaGetLastError());
     }
-    { k_add_f32_to_f64<<<nb, 256, 0, s>>>(X, F, tot); ::rbf::note_launch(); }
-    RBF_CUDA(cudaGetLastError());
     if (it + 1 < sweeps) {
       if (Hs) {
         RBF_TRY(csr_residual(*Hs, X, bb.as<double>(), m, Rr, s));
