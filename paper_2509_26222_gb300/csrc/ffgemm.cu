@@ -5,7 +5,7 @@
 // matrices of a few thousand rows by blocks of tens to hundreds of columns.
 // GB300 executes float64 at a small fraction of its float32 rate, so these
 // products take each operand as hi + lo (two float32, about 2^-48 relative),
-// multiply-accumulate with error-free transforms (about 14 float32
+// multiply-accumulate with error-free transforms (about 12 float32
 // operations per product term, accuracy about 2^-46 relative to the sum of
 // |terms|) and return float64.
 #include "common.cuh"
@@ -263,14 +263,32 @@ rbf_status gemm_ff_tiles(Ctx* c, bool ta, bool tb, int64_t m, int64_t n, int64_t
                          cudaStream_t s, int slot, bool lower) {
   constexpr int NT = TM * TN / 16;
   const int64_t tiles = ((m + TM - 1) / TM) * ((n + TN - 1) / TN);
-  // outputs that do not give every SM about 1024 threads split k into slices
-  // of at least 64
-  const int64_t want = 152 * (1024 / NT);
+  // Outputs with fewer tiles than co-resident CTAs split k into slices of at
+  // least 64, their number chosen to fill whole waves: a partial last wave
+  // costs a whole slice time for a few CTAs.
+  static int cap[64] = {0};
+  const int dev = c->device & 63;
+  if (!cap[dev]) {
+    int occ = 0, sms = 0;
+    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_ff<TM, TN>, NT, 0));
+    RBF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    cap[dev] = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
+  }
   int64_t nsplit = 1;
-  if (!lower && tiles < want && k >= 128) {
-    nsplit = (want + tiles - 1) / tiles;
+  if (!lower && tiles < cap[dev] && k >= 128) {
+    // the number of waves (1 to 4) whose slots the slices fill best
     const int64_t most = k / 64;
-    if (nsplit > most) nsplit = most;
+    double best = 0.0;
+    for (int w = 1; w <= 4; ++w) {
+      int64_t ns = (int64_t)w * cap[dev] / tiles;
+      if (ns > most) ns = most;
+      if (ns < 1) ns = 1;
+      const double eff = (double)(tiles * ns) / ((double)w * cap[dev]);
+      if (eff > best + 0.03) {
+        best = eff;
+        nsplit = ns;
+      }
+    }
   }
   int64_t kc = (k + nsplit - 1) / nsplit;
   kc = (kc + FK - 1) / FK * FK;
