@@ -32,7 +32,7 @@ __device__ __forceinline__ void ff_acc(float& sacc, float& tacc, FF x, FF y) {
 // instead.  With lower set only the tiles that reach the diagonal or below it
 // are computed (a symmetric result read from its lower triangle).
 template <int TM, int TN>
-__global__ void __launch_bounds__(TM * TN / 16) k_gemm_ff(bool ta, bool tb, bool lower, int64_t m, int64_t n,
+__global__ void __launch_bounds__(TM * TN / 16, 3) k_gemm_ff(bool ta, bool tb, bool lower, int64_t m, int64_t n,
                                                           int64_t k, int64_t kc, double alpha,
                                                           const double* __restrict__ A, int64_t lda,
                                                           const double* __restrict__ B, int64_t ldb, double beta,
