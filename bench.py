@@ -412,7 +412,8 @@ def full_sequence(args, N, prec, centers, flush, stream, eye, frames):
         line = {"frames_per_s": len(ts) / (sum(ts) * 1e-3), "ms_per_frame": sum(ts) / len(ts)}
         if name == "timed":
             line["regions"] = {r: {"frames": f"{a}..{b - 1}", "ms_per_frame": float(np.mean(ts[a:b])),
-                                   "max_ms": float(np.max(ts[a:b]))}
+                                   "median_ms": float(np.median(ts[a:b])),
+                                   "max_ms": float(np.max(ts[a:b])), "max_frame": int(a + np.argmax(ts[a:b]))}
                                for r, (a, b) in SEQ_REGIONS.items() if b <= len(ts)}
         out["fp64" if name == "fp64" else ("mixed" if prec == N.UPDATE_MIXED else "fp64_timed")] = line
     if prec == N.UPDATE_MIXED:
