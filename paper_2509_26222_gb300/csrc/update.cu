@@ -21,6 +21,7 @@
 #include <limits.h>
 #include <math.h>
 
+#include <algorithm>
 #include <utility>
 #include <vector>
 
@@ -395,6 +396,13 @@ __global__ void k_gather_outside(const BlkRef* __restrict__ ref, const double* _
   if (e >= m * m) return;
   int64_t u = e / m, v = e % m;
   G[e] = outside_entry(ref, arena, gids[lpos[u]], gids[lpos[v]], prior);
+}
+
+// base[q] = arena offset of the stored block of returning center q
+__global__ void k_ret_base(const BlkRef* __restrict__ ref, const int32_t* __restrict__ gids,
+                           const int32_t* __restrict__ lpos, int64_t r, long long* __restrict__ base) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < r) base[q] = ref[gids[lpos[q]]].base;
 }
 
 __global__ void k_identity(double* __restrict__ B, int64_t m) {
@@ -979,17 +987,51 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
         RBF_CUDA(cudaGetLastError());
       }
       Buf& Gb = c->scratch(42);
-      RBF_TRY(Gb.ensure((size_t)r * r * sizeof(double)));
-      { k_gather_outside<<<nblk(r * r), 256, 0, sC>>>(c->blkref.as<BlkRef>(), c->arena.as<double>(),
-                                                    1.0 / c->cfg.lambda, An.as<int32_t>(), Rl.as<int32_t>(), r,
-                                                    Gb.as<double>()); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
-      if (r <= SPD_SMALL_MAX && mixed) RBF_TRY(spd_inverse_small_ff(c, Gb.as<double>(), r, sC));
-      else if (r <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), r, sC));
-      else RBF_TRY(spd_inverse(c, Gb.as<double>(), r, sC, 43));
-      { k_scatter_sym<<<nblk(r * r), 256, 0, sC>>>(Gb.as<double>(), r, r, Rl.as<int32_t>(), Hn.as<double>(),
-                                                ld); ::rbf::note_launch(); }
-      RBF_CUDA(cudaGetLastError());
+      // P_RR is block-diagonal over the departures the centers came back from
+      // (P[A, not A] = 0 at each departure), so many returning centers are
+      // inverted block by block: their stored blocks' offsets go to the host,
+      // which groups them (the block stage runs on one stream in that case).
+      std::vector<int32_t> grp_list;
+      std::vector<int64_t> grp_start{0};
+      if (r > SPD_SMALL_MAX) {
+        Buf& bb = c->scratch(98);
+        RBF_TRY(bb.ensure((size_t)r * sizeof(long long)));
+        { k_ret_base<<<nblk(r), 256, 0, sC>>>(c->blkref.as<BlkRef>(), An.as<int32_t>(), Rl.as<int32_t>(), r,
+                                           bb.as<long long>()); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+        std::vector<long long> hb((size_t)r);
+        std::vector<int32_t> hr((size_t)r);
+        RBF_CUDA(cudaMemcpyAsync(hb.data(), bb.p, (size_t)r * sizeof(long long), cudaMemcpyDeviceToHost, sC));
+        RBF_CUDA(cudaMemcpyAsync(hr.data(), Rl.p, (size_t)r * sizeof(int32_t), cudaMemcpyDeviceToHost, sC));
+        RBF_CUDA(cudaStreamSynchronize(sC));
+        std::vector<int64_t> ord((size_t)r);
+        for (int64_t q = 0; q < r; ++q) ord[q] = q;
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return hb[x] < hb[y]; });
+        grp_list.resize((size_t)r);
+        for (int64_t q = 0; q < r; ++q) {
+          grp_list[q] = hr[ord[q]];
+          if (q > 0 && hb[ord[q]] != hb[ord[q - 1]]) grp_start.push_back(q);
+        }
+        RBF_CUDA(cudaMemcpyAsync(Rl.p, grp_list.data(), (size_t)r * sizeof(int32_t), cudaMemcpyHostToDevice, sC));
+        RBF_CUDA(cudaStreamSynchronize(sC));  // the host list is released at the end of this scope
+      }
+      grp_start.push_back(r);
+      int64_t kmax = 0;
+      for (size_t g = 0; g + 1 < grp_start.size(); ++g) kmax = std::max(kmax, grp_start[g + 1] - grp_start[g]);
+      RBF_TRY(Gb.ensure((size_t)kmax * kmax * sizeof(double)));
+      for (size_t g = 0; g + 1 < grp_start.size(); ++g) {
+        const int64_t q0 = grp_start[g], k = grp_start[g + 1] - q0;
+        const int32_t* lk = Rl.as<int32_t>() + q0;
+        { k_gather_outside<<<nblk(k * k), 256, 0, sC>>>(c->blkref.as<BlkRef>(), c->arena.as<double>(),
+                                                      1.0 / c->cfg.lambda, An.as<int32_t>(), lk, k,
+                                                      Gb.as<double>()); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+        if (k <= SPD_SMALL_MAX && mixed) RBF_TRY(spd_inverse_small_ff(c, Gb.as<double>(), k, sC));
+        else if (k <= SPD_SMALL_MAX) RBF_TRY(spd_inverse_small(c, Gb.as<double>(), k, sC));
+        else RBF_TRY(spd_inverse(c, Gb.as<double>(), k, sC, 43));
+        { k_scatter_sym<<<nblk(k * k), 256, 0, sC>>>(Gb.as<double>(), k, k, lk, Hn.as<double>(), ld); ::rbf::note_launch(); }
+        RBF_CUDA(cudaGetLastError());
+      }
     }
   }
 
