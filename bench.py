@@ -508,9 +508,15 @@ def run_ours(args, ws, rank, local):
             Tp.profile(True)
             Tp.profile_read(reset=True)
         g, b, s = dev_frames[k]
+        if k == args.profile_frame:  # the profiler range of `ncu --profile-from-start off`
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
         Tp.update(g, noise=NOISE)
         Tp.soft_cost(eye, s, b, out=out7)
         Tp.eval(g[:, :2], out_h=h[: g.shape[0]], out_grad=grad[: g.shape[0]])
+        if k == args.profile_frame:
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
     torch.cuda.synchronize()
     prof = Tp.profile_read(reset=True)
     Tp.profile(False)
@@ -814,6 +820,8 @@ def main():
     ap.add_argument("--no-other", action="store_true", help="skip the other update precision on the same frames")
     ap.add_argument("--c5-reps", type=int, default=3, help="timed updates at 65,536 centers per precision (0: skip)")
     ap.add_argument("--raster-reps", type=int, default=5, help="timed raster evaluations (0: skip)")
+    ap.add_argument("--profile-frame", type=int, default=-1,
+                    help="bracket this frame of the stage-timing pass with cudaProfilerStart/Stop (-1: none)")
     ap.add_argument("--no-full-sequence", dest="full_sequence", action="store_false",
                     help="skip the leg over all 200 frames of the sequence")
     args = ap.parse_args()
