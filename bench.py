@@ -252,8 +252,8 @@ class Clocks:
 EVAL_DRAM_BYTES_PER_QUERY = (134.307840e6 + 141.672192e6) / (1 << 24)
 # DRAM bytes (read + write) of one k_chol_df launch (the factorization of one
 # staircase frame, a = 1811), from one ncu capture; None until measured
-DF_DRAM_BYTES_PER_LAUNCH = 7_028_224  # read 7,028,224 B, written 0 B (the band stays in L2)
-DF_TRAFFIC_SOURCE = "ncu dram__bytes_read+write of one k_chol_df launch (frame 5 of the sequence)"
+DF_DRAM_BYTES_PER_LAUNCH = 6_289_920  # read 6,289,664 B, written 256 B (the band stays in L2)
+DF_TRAFFIC_SOURCE = "ncu dram__bytes_read+write of one k_chol_df launch (frame 20 of the sequence)"
 
 
 def frame_arrays(k):
