@@ -278,6 +278,25 @@ unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
 
+// K slices of the inverse apply: as many as fill the co-resident CTAs of
+// the GPU once (the tiles alone leave most SMs idle for a few right-hand
+// sides), at least 4 chunks of K each and at most 8.
+static int apply_split(Ctx* c, int64_t tiles, int64_t n) {
+  static int cap[64] = {0};
+  const int dev = c->device & 63;
+  if (!cap[dev]) {
+    int occ = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_inv_apply, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
+    cap[dev] = occ * sms;
+  }
+  int64_t ns = cap[dev] / (tiles > 0 ? tiles : 1);
+  const int64_t most = n / (4 * TK);
+  if (ns > most) ns = most;
+  if (ns > 8) ns = 8;
+  return ns < 1 ? 1 : (int)ns;
+}
+
 rbf_status trtri_mixed(Ctx* c, const float* W, int64_t ldw, int64_t n, const float* Zd, float* Z, int64_t ldz,
                        cudaStream_t s) {
   if (n <= 0) return RBF_OK;
@@ -321,9 +340,7 @@ rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, i
     return RBF_OK;
   }
   int64_t tiles = (int64_t)cdiv(n, TG) * cdiv(m, TG);
-  int nsplit = (int)(2 * 152 / tiles);
-  if (nsplit < 1) nsplit = 1;
-  if (nsplit > 8) nsplit = 8;
+  int nsplit = apply_split(c, tiles, n);
   Buf& pb = c->scratch(67);
   RBF_TRY(pb.ensure((size_t)nsplit * n * m * sizeof(float)));
   float* P = pb.as<float>();
@@ -377,9 +394,7 @@ rbf_status inv_solve_unit(Ctx* c, const float* Z, int64_t ldz, int64_t n, const 
     return RBF_OK;
   }
   int64_t tiles = (int64_t)cdiv(n, TG) * cdiv(m, TG);
-  int nsplit = (int)(2 * 152 / tiles);
-  if (nsplit < 1) nsplit = 1;
-  if (nsplit > 8) nsplit = 8;
+  int nsplit = apply_split(c, tiles, n);
   Buf& pb = c->scratch(67);
   RBF_TRY(pb.ensure((size_t)nsplit * n * m * sizeof(float)));
   float* P = pb.as<float>();
