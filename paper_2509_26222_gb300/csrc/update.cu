@@ -1065,16 +1065,12 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   // the solve on) are built on a side stream beside the factorization.
   int64_t bw = BW_DENSE;
   const bool band_probe = !c->pg_on && d == 0;
-  const bool csr_side = mixed && par && !band_probe;
+  // Once a center has left, H' carries Schur fill and soon holds about a^2
+  // nonzeros: its residuals then read the dense H' (8 bytes an entry against
+  // 12 for the compressed rows) and no compressed copy is built.
   if (mixed) {
-    if (csr_side) {
-      RBF_CUDA(cudaEventRecord(c->bev[0], s));
-      RBF_CUDA(cudaStreamWaitEvent(sA, c->bev[0], 0));
-      RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, sA));
-      RBF_CUDA(cudaEventRecord(c->bev[1], sA));
-    } else {
-      RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, s));
-    }
+    if (band_probe) RBF_TRY(build_csr(c, Hn.as<double>(), ld, an, c->Hs_next, s));
+    else c->Hs_next.valid = false;
   }
   if (band_probe) {
     if (mixed && c->Hs_next.valid) RBF_TRY(csr_bandwidth(c, an, &bw, s));
@@ -1102,7 +1098,6 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaMemcpyAsync(Ln.p, Hn.p, (size_t)an * an * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RBF_TRY(potrf_lower(c, Ln.as<double>(), an, ld, an, false, s, bw));
   }
-  if (csr_side) RBF_CUDA(cudaStreamWaitEvent(s, c->bev[1], 0));
   int flag = 0;
   {
     StageTimer st(c, RBF_STAGE_SOLVE, s, (mixed ? 2.0 * c->refine_sweeps + 2.0 * (c->refine_sweeps - 1) : 2.0) *
