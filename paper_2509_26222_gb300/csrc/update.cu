@@ -465,9 +465,10 @@ __device__ __forceinline__ int sl_block_scan(int v, int& excl, int* ws) {
 // CTA: previous-local positions of D and S and new-local positions of E and
 // of the staying centers (Sn), each in ascending order, the leaving flags over
 // the previous block, and cnt = {|D|, |S|, |E|, entering centers that left
-// some earlier block}.
+// some earlier block}.  The new block's size is read from the device.
 __global__ void __launch_bounds__(SL_THREADS) k_set_lists(const int32_t* __restrict__ Ap, int64_t ap,
-                                                          const int32_t* __restrict__ An, int64_t an,
+                                                          const int32_t* __restrict__ An,
+                                                          const int32_t* __restrict__ an_dev,
                                                           const int32_t* __restrict__ g2l_new,
                                                           const int32_t* __restrict__ g2l_prev,
                                                           const int32_t* __restrict__ departed, int64_t M,
@@ -476,6 +477,7 @@ __global__ void __launch_bounds__(SL_THREADS) k_set_lists(const int32_t* __restr
                                                           int32_t* __restrict__ Sn, int32_t* __restrict__ cnt) {
   __shared__ int ws[33];
   constexpr int PER = 8;
+  const int64_t an = *an_dev;  // size of the new block (the compaction's total)
   int nS = 0;  // staying centers seen so far (uniform)
   for (int64_t c0 = 0; c0 < ap; c0 += (int64_t)SL_THREADS * PER) {
     const int64_t b = c0 + (int64_t)threadIdx.x * PER;
@@ -722,32 +724,35 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   RBF_TRY(El.ensure((size_t)(amax + 1) * sizeof(int32_t)));
   RBF_TRY(Sn.ensure((size_t)(amax + 1) * sizeof(int32_t)));
   int32_t* flD = fl.as<int32_t>();  // leaving flags over the previous block
-  // sizes to the host: a, d, s, e
+  // sizes to the host: a, d, s, e (one read: the set lists take a from the device)
   int64_t* hs = c->host_small;
-  RBF_CUDA(cudaMemcpyAsync(hs + 0, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  RBF_CUDA(cudaStreamSynchronize(s));
-  const int64_t an = (int64_t)((int32_t*)hs)[0];
-  if (an == 0) return RBF_OK;
-  int64_t d = 0, sN = 0, e = an, e_returning = 0;
+  int32_t* h32 = (int32_t*)hs;
+  int64_t an = 0, d = 0, sN = 0, e = 0, e_returning = 0;
   if (ap > 0) {
-    int32_t* h32 = (int32_t*)hs;
     Buf& cnt = c->scratch(53);
     RBF_TRY(cnt.ensure(4 * sizeof(int32_t)));
-    { k_set_lists<<<1, SL_THREADS, 0, s>>>(c->A.as<int32_t>(), ap, An.as<int32_t>(), an, g2ln.as<int32_t>(),
-                                          c->g2l.as<int32_t>(), c->departed.as<int32_t>(), M, flD,
-                                          Dl.as<int32_t>(), Sl.as<int32_t>(), El.as<int32_t>(), Sn.as<int32_t>(),
-                                          cnt.as<int32_t>()); ::rbf::note_launch(); }
+    { k_set_lists<<<1, SL_THREADS, 0, s>>>(c->A.as<int32_t>(), ap, An.as<int32_t>(), pos.as<int32_t>() + M,
+                                          g2ln.as<int32_t>(), c->g2l.as<int32_t>(), c->departed.as<int32_t>(), M,
+                                          flD, Dl.as<int32_t>(), Sl.as<int32_t>(), El.as<int32_t>(),
+                                          Sn.as<int32_t>(), cnt.as<int32_t>()); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
     RBF_CUDA(cudaMemcpyAsync(h32, cnt.p, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaMemcpyAsync(h32 + 5, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaStreamSynchronize(s));
+    an = h32[5];
     d = h32[0];
     sN = h32[1];
     e = h32[2];
     e_returning = h32[3];
+    if (an == 0) return RBF_OK;
     if (sN + e != an || sN + d != ap) return fail(RBF_ECUDA, "inconsistent active-set bookkeeping");
   } else {
-    // every new center enters
-    // El = 0..an-1
+    RBF_CUDA(cudaMemcpyAsync(h32 + 5, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    an = h32[5];
+    if (an == 0) return RBF_OK;
+    e = an;
+    // every new center enters: El = 0..an-1
     std::vector<int32_t> iota((size_t)an);
     for (int64_t l = 0; l < an; ++l) iota[l] = (int32_t)l;
     RBF_CUDA(cudaMemcpyAsync(El.p, iota.data(), (size_t)an * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -804,7 +809,7 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   Buf& cpp = c->scratch(75);
   Buf& perm = c->scratch(40);
   Buf& Nn = c->scratch(76);
-  int32_t* h32 = (int32_t*)c->host_small;
+
   if (d > 0 && sN > 0) {
     StageTimer st_sc0(c, RBF_STAGE_SCHUR, s, 0.0);
     { k_move_sym<<<nblk(sN * sN), 256, 0, s>>>(c->H.as<double>(), c->ldH, Sl.as<int32_t>(), Sn.as<int32_t>(),
