@@ -417,8 +417,17 @@ __global__ void k_copy_lower(const double* __restrict__ S, double* __restrict__ 
 }
 
 // the leaving centers refer to their new block (arena offset base, d x d)
+// The commit kernels are issued before the host reads the device flags and
+// do nothing when the factorization or a solve failed (the state stays as it
+// was, as the failing update's contract requires).
+__device__ __forceinline__ bool update_failed(const int* __restrict__ flag) {
+  return (*flag & (DEV_NOT_SPD | DEV_TIMEOUT)) != 0;
+}
+
 __global__ void k_blk_assign(BlkRef* __restrict__ ref, const int32_t* __restrict__ ids,
-                             const int32_t* __restrict__ lpos, int64_t d, long long base) {
+                             const int32_t* __restrict__ lpos, int64_t d, long long base,
+                             const int* __restrict__ flag) {
+  if (update_failed(flag)) return;
   int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u < d) {
     BlkRef r;
@@ -562,15 +571,24 @@ __global__ void k_split_flags(const int32_t* __restrict__ flag, const int32_t* _
 }
 
 __global__ void k_mark_departed(const int32_t* __restrict__ ids, const int32_t* __restrict__ lpos, int64_t d,
-                                int32_t* __restrict__ departed) {
+                                int32_t* __restrict__ departed, const int* __restrict__ flag) {
+  if (update_failed(flag)) return;
   int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u < d) departed[ids[lpos[u]]] = 1;
 }
 
 __global__ void k_w_add(double* __restrict__ w, const int32_t* __restrict__ A, int64_t a,
-                        const double* __restrict__ delta) {
+                        const double* __restrict__ delta, const int* __restrict__ flag) {
+  if (update_failed(flag)) return;
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l < a) w[A[l]] += delta[l];
+}
+
+__global__ void k_copy_f64_guarded(double* __restrict__ dst, const double* __restrict__ src, int64_t n,
+                                   const int* __restrict__ flag) {
+  if (update_failed(flag)) return;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
 }
 
 // test hook: H'[l][l] += shift
@@ -1113,25 +1131,32 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     else
       RBF_TRY(chol_solve(c, Hn.as<double>(), Ln.as<double>(), an, ld, u.as<double>(), false, s, bw));
   }
-  // one read of the device flags covers the factorization and the solves
-  RBF_TRY(read_dev_flag(c, s, &flag));
-  if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
-  if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
-
-  // 9. commit
-  { k_w_add<<<nblk(an), 256, 0, s>>>(c->w.as<double>(), An.as<int32_t>(), an, u.as<double>()); ::rbf::note_launch(); }
+  // 9. commit, issued before the one read of the device flags that covers the
+  // factorization and the solves: the kernels skip their writes if it failed,
+  // and the host's bookkeeping below happens only after a clean read
+  const int* dflag = c->dflag.as<int>();
+  { k_w_add<<<nblk(an), 256, 0, s>>>(c->w.as<double>(), An.as<int32_t>(), an, u.as<double>(), dflag); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
+  const long long base = c->arena_used;
   if (d > 0) {
     // the block P_DD goes to the arena; the leaving centers refer to it, which
     // also drops their coupling to every older block (P[D, not D] = 0)
-    const long long base = c->arena_used;
     RBF_TRY(arena_reserve(c, base + d * d, s));
-    RBF_CUDA(cudaMemcpyAsync(c->arena.as<double>() + base, Pdd.p, (size_t)d * d * sizeof(double),
-                             cudaMemcpyDeviceToDevice, s));
-    { k_blk_assign<<<nblk(d), 256, 0, s>>>(c->blkref.as<BlkRef>(), c->A.as<int32_t>(), Dl.as<int32_t>(), d, base); ::rbf::note_launch(); }
+    { k_copy_f64_guarded<<<nblk(d * d), 256, 0, s>>>(c->arena.as<double>() + base, Pdd.as<double>(), d * d, dflag); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
-    { k_mark_departed<<<nblk(d), 256, 0, s>>>(c->A.as<int32_t>(), Dl.as<int32_t>(), d, c->departed.as<int32_t>()); ::rbf::note_launch(); }
+    { k_blk_assign<<<nblk(d), 256, 0, s>>>(c->blkref.as<BlkRef>(), c->A.as<int32_t>(), Dl.as<int32_t>(), d, base,
+                                         dflag); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
+    { k_mark_departed<<<nblk(d), 256, 0, s>>>(c->A.as<int32_t>(), Dl.as<int32_t>(), d, c->departed.as<int32_t>(),
+                                            dflag); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+  }
+  // the evaluation tables follow the weights (unchanged if the update failed)
+  RBF_TRY(refresh_center_weights(c, s));
+  RBF_TRY(read_dev_flag(c, s, &flag));
+  if (flag & DEV_NOT_SPD) return fail(RBF_ENOTSPD, "information matrix of the active block is not SPD");
+  if (flag & DEV_TIMEOUT) return fail(RBF_ETIMEOUT, "triangular solve wait timed out");
+  if (d > 0) {
     c->arena_used = base + d * d;
     c->pg_on = true;
   }
@@ -1152,7 +1177,6 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   std::swap(c->g2l, g2ln);
   c->a = an;
   c->ldH = ld;
-  RBF_TRY(refresh_center_weights(c, s));
   return RBF_OK;
 }
 
