@@ -205,13 +205,11 @@ __global__ void k_sum_partials(const float* __restrict__ P, int nsplit, int64_t 
 
 // Y = A F for m <= GEMV_M with A = Z (lower: row i over k <= i) or A = Z^T
 // stored transposed (upper: row i over k >= i): one warp per row, lanes over
-// the row, eight loads of A in flight per lane.  With Fd set, F is read as
-// float64 and rounded to float32; with Xd set, the result is added to the
-// float64 Xd instead of stored to Y.
+// the row, eight loads of A in flight per lane.  With Xd set, the result is
+// added to the float64 Xd instead of stored to Y.
 template <bool UPPER>
 __global__ void __launch_bounds__(256) k_inv_gemv(int64_t n, int m, const float* __restrict__ A, int64_t lda,
                                                   const float* __restrict__ F, float* __restrict__ Y,
-                                                  const double* __restrict__ Fd = nullptr,
                                                   double* __restrict__ Xd = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -229,7 +227,7 @@ __global__ void __launch_bounds__(256) k_inv_gemv(int64_t n, int m, const float*
       bool ok = k < hi;
       z[u] = ok ? ar[k] : 0.f;
 #pragma unroll
-      for (int j = 0; j < GEMV_M; ++j) f[u][j] = (ok && j < m) ? (Fd ? (float)Fd[k * m + j] : F[k * m + j]) : 0.f;
+      for (int j = 0; j < GEMV_M; ++j) f[u][j] = (ok && j < m) ? F[k * m + j] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
@@ -357,21 +355,30 @@ rbf_status inv_solve(Ctx* c, const float* Z, int64_t ldz, int64_t n, float* F, i
   return RBF_OK;
 }
 
-// X += Z^T (Z R) for m <= GEMV_M right-hand sides, R and X float64: the
-// rounding of R to float32 and the float64 accumulation happen inside the two
-// matrix-vector launches.
+// X += Z^T (Z R) for m <= GEMV_M right-hand sides, R and X float64: R is
+// rounded to float32 once (a float64 operand inside the matrix-vector loop
+// would convert it once per row, on GB300's narrow float64 pipe), and the
+// float64 accumulation happens in the second matrix-vector launch.
+__global__ void k_round_f32(const double* __restrict__ R, int64_t cnt, float* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) F[i] = (float)R[i];
+}
+
 rbf_status inv_solve_acc(Ctx* c, const float* Z, int64_t ldz, int64_t n, const double* R, double* X, int64_t m,
                          cudaStream_t s) {
   if (n <= 0 || m <= 0) return RBF_OK;
   if (m > GEMV_M) return fail(RBF_EINVAL, "inv_solve_acc: at most %d right-hand sides", GEMV_M);
   Buf& yb = c->scratch(66);
-  RBF_TRY(yb.ensure((size_t)n * m * sizeof(float)));
+  RBF_TRY(yb.ensure((size_t)2 * n * m * sizeof(float)));
   float* Y = yb.as<float>();
+  float* F = Y + n * m;
   StageTimer st(c, RBF_STAGE_INVAPPLY, s, 2.0 * (double)n * n * m);
   const float* Zt = Z + n * ldz;
-  { k_inv_gemv<false><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Z, ldz, nullptr, Y, R, nullptr); ::rbf::note_launch(); }
+  { k_round_f32<<<cdiv(n * m, 256), 256, 0, s>>>(R, n * m, F); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
-  { k_inv_gemv<true><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Zt, ldz, Y, nullptr, nullptr, X); ::rbf::note_launch(); }
+  { k_inv_gemv<false><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Z, ldz, F, Y); ::rbf::note_launch(); }
+  RBF_CUDA(cudaGetLastError());
+  { k_inv_gemv<true><<<cdiv(n * 32, 256), 256, 0, s>>>(n, (int)m, Zt, ldz, Y, nullptr, X); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   return RBF_OK;
 }
