@@ -119,6 +119,7 @@ struct Ctx {
   int64_t inv_max = 4096;  // form L^{-1} for active blocks up to this size
   bool gacc_dirty = false; // the Gram accumulators may hold values of an unfinished update
   int64_t bw_lf = BW_DENSE_CTX;  // half-bandwidth of the float32 factor Lf
+  int64_t nbr_cap = 0;           // neighbour-list capacity of rbf_update (0: read the total first)
   cudaStream_t bs[3] = {};           // side streams of the block stage (bs[2]: high priority)
   cudaEvent_t bev[4] = {};           // fork and joins of the block stage
   bool la_ok = true;                 // look-ahead factorization allowed
@@ -272,8 +273,10 @@ rbf_status install_centers(Ctx* c, const double* cxy_dev, int64_t M, cudaStream_
 rbf_status reset_update_state(Ctx* c);
 
 // neighbour lists (point-major CSR, ids ascending) under radius r
+// (defer_cap > 0: the total is not read; rows past defer_cap entries stay
+// unfilled and *nnz = -1, the caller reads row_ptr[n] and the flags later)
 rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride_floats, double radius,
-                          Buf& row_ptr, Buf& col, int64_t* nnz, cudaStream_t s);
+                          Buf& row_ptr, Buf& col, int64_t* nnz, cudaStream_t s, int64_t defer_cap = 0);
 
 rbf_status read_dev_flag(Ctx* c, cudaStream_t s, int* flag);
 

@@ -20,6 +20,7 @@
 // the same matrix the Woodbury form of Eq. H_inverse_update produces.
 #include <limits.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <utility>
@@ -78,12 +79,12 @@ __global__ void __launch_bounds__(256) k_nbr_fill(NbrParams P, const int32_t* __
                                                   const int32_t* __restrict__ sorted_id,
                                                   const float* __restrict__ pts, int stride, int64_t n,
                                                   const int64_t* __restrict__ row_ptr,
-                                                  int32_t* __restrict__ col) {
+                                                  int32_t* __restrict__ col, int64_t cap) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float x = pts[i * stride], y = pts[i * stride + 1];
   int64_t a = row_ptr[i], b = row_ptr[i + 1];
-  if (a == b) return;
+  if (a == b || b > cap) return;  // past the capacity: the caller sees the total and retries
   int64_t p = a;
   for_each_cand(P.g, cell_start, x, y, P.rc, [&](int s) {
     float4 cc = xyw[s];
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256) k_nbr_fill(NbrParams P, const int32_t* __
 }
 
 rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, double radius,
-                          Buf& row_ptr, Buf& col, int64_t* nnz, cudaStream_t s) {
+                          Buf& row_ptr, Buf& col, int64_t* nnz, cudaStream_t s, int64_t defer_cap) {
   NbrParams P;
   P.g = c->grid;
   float r32 = (float)radius;
@@ -116,6 +117,17 @@ rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, doubl
                                  stride, n, cnt.as<int32_t>(), c->dflag.as<int>()); ::rbf::note_launch(); }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32_to_i64(c, cnt.as<int32_t>(), row_ptr.as<int64_t>(), n, s, 48));
+  if (defer_cap > 0) {
+    // the total and the non-finite flag are read by the caller with its next
+    // host read; rows past the capacity are left unfilled
+    RBF_TRY(col.ensure((size_t)defer_cap * sizeof(int32_t)));
+    { k_nbr_fill<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(),
+                                  c->sorted_id.as<int32_t>(), pts, stride, n, row_ptr.as<int64_t>(),
+                                  col.as<int32_t>(), defer_cap); ::rbf::note_launch(); }
+    RBF_CUDA(cudaGetLastError());
+    *nnz = -1;
+    return RBF_OK;
+  }
   RBF_CUDA(cudaMemcpyAsync(c->host_small, row_ptr.as<int64_t>() + n, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s));
   int flag = 0;
@@ -126,7 +138,7 @@ rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, doubl
   if (*nnz > 0) {
     { k_nbr_fill<<<nb, 256, 0, s>>>(P, c->cell_start.as<int32_t>(), c->sorted_xyw.as<float4>(),
                                   c->sorted_id.as<int32_t>(), pts, stride, n, row_ptr.as<int64_t>(),
-                                  col.as<int32_t>()); ::rbf::note_launch(); }
+                                  col.as<int32_t>(), *nnz); ::rbf::note_launch(); }
     RBF_CUDA(cudaGetLastError());
   }
   return RBF_OK;
@@ -136,6 +148,15 @@ rbf_status neighbor_lists(Ctx* c, const float* pts, int64_t n, int stride, doubl
 // Active set and block bookkeeping
 // ---------------------------------------------------------------------------
 __global__ void k_mark(const int32_t* __restrict__ col, int64_t nnz, int32_t* __restrict__ mark) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) mark[col[k]] = 1;
+}
+
+// the same with the total read on the device (entries past cap were not filled)
+__global__ void k_mark_dev(const int32_t* __restrict__ col, const int64_t* __restrict__ nnz_dev, int64_t cap,
+                           int32_t* __restrict__ mark) {
+  const int64_t nnz = *nnz_dev;
+  if (nnz > cap) return;
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nnz) mark[col[k]] = 1;
 }
@@ -681,6 +702,33 @@ static rbf_status spd_inverse(Ctx* c, double* G, int64_t m, cudaStream_t s, int 
   return RBF_OK;
 }
 
+// The deferred neighbour total and the device flags, copied into the pinned
+// words 8..9 (total) and 10 (flags) with the caller's next host read.
+static rbf_status read_deferred_total(Ctx* c, const int64_t* total_dev, cudaStream_t s) {
+  int32_t* h32 = (int32_t*)c->host_small;
+  RBF_CUDA(cudaMemcpyAsync(h32 + 8, total_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  RBF_CUDA(cudaMemcpyAsync(h32 + 10, c->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return RBF_OK;
+}
+
+// After that read: EINVAL for a non-finite point (flag cleared), ERANGE with
+// the capacity raised when the lists did not fit.
+static rbf_status check_deferred_total(Ctx* c, int64_t cap, cudaStream_t s) {
+  int32_t* h32 = (int32_t*)c->host_small;
+  const int flag = h32[10];
+  int64_t total = 0;
+  memcpy(&total, h32 + 8, sizeof(int64_t));
+  if (flag & DEV_BAD_INDEX) {
+    RBF_CUDA(cudaMemsetAsync(c->dflag.p, 0, sizeof(int), s));
+    return fail(RBF_EINVAL, "a point has a non-finite coordinate");
+  }
+  if (total > cap) {
+    c->nbr_cap = 2 * total;
+    return RBF_ERANGE;
+  }
+  return RBF_OK;
+}
+
 }  // namespace rbf
 
 using namespace rbf;
@@ -696,15 +744,23 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   const int64_t M = c->M;
   const bool mixed = c->cfg.update_precision == RBF_UPDATE_MIXED;
 
-  // 1. neighbour lists
+  // 1. neighbour lists.  After the first update their total is not read
+  // here: the lists are filled up to a capacity (twice the largest total
+  // seen) and the total comes with the set sizes' host read below; a total
+  // past the capacity makes the update start over with the capacity raised.
   Buf& row_ptr = c->scratch(0);
   Buf& col = c->scratch(1);
   int64_t nnz = 0;
+  const int64_t cap = c->nbr_cap;
   {
     StageTimer st(c, RBF_STAGE_NEIGHBORS, s, 12.0 * (double)n);
-    RBF_TRY(neighbor_lists(c, pts, n, 3, assembly_radius(c->cfg, noise), row_ptr, col, &nnz, s));
+    RBF_TRY(neighbor_lists(c, pts, n, 3, assembly_radius(c->cfg, noise), row_ptr, col, &nnz, s, cap));
   }
-  if (nnz == 0) return RBF_OK;
+  if (cap == 0) {
+    if (nnz == 0) return RBF_OK;
+    c->nbr_cap = 2 * nnz;
+  }
+  const int64_t nnz_buf = cap > 0 ? cap : nnz;  // entries the lists may hold
 
   // 2. active set
   Buf& mark = c->scratch(2);
@@ -720,7 +776,11 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     { k_fill_i32<<<nblk(M), 256, 0, s>>>(mark.as<int32_t>(), M, 1); ::rbf::note_launch(); }
   } else {
     RBF_CUDA(cudaMemsetAsync(mark.p, 0, (size_t)M * sizeof(int32_t), s));
-    { k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>()); ::rbf::note_launch(); }
+    if (cap > 0) {
+      { k_mark_dev<<<nblk(cap), 256, 0, s>>>(col.as<int32_t>(), row_ptr.as<int64_t>() + n, cap, mark.as<int32_t>()); ::rbf::note_launch(); }
+    } else {
+      { k_mark<<<nblk(nnz), 256, 0, s>>>(col.as<int32_t>(), nnz, mark.as<int32_t>()); ::rbf::note_launch(); }
+    }
   }
   RBF_CUDA(cudaGetLastError());
   RBF_TRY(scan_i32(c, mark.as<int32_t>(), pos.as<int32_t>(), M, s, 48));
@@ -756,7 +816,13 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     RBF_CUDA(cudaGetLastError());
     RBF_CUDA(cudaMemcpyAsync(h32, cnt.p, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaMemcpyAsync(h32 + 5, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (cap > 0) RBF_TRY(read_deferred_total(c, row_ptr.as<int64_t>() + n, s));
     RBF_CUDA(cudaStreamSynchronize(s));
+    if (cap > 0) {
+      const rbf_status st = check_deferred_total(c, cap, s);
+      if (st == RBF_ERANGE) return rbf_update(cx, pts, n, noise, stream);  // lists past the capacity
+      RBF_TRY(st);
+    }
     an = h32[5];
     d = h32[0];
     sN = h32[1];
@@ -766,7 +832,13 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
     if (sN + e != an || sN + d != ap) return fail(RBF_ECUDA, "inconsistent active-set bookkeeping");
   } else {
     RBF_CUDA(cudaMemcpyAsync(h32 + 5, pos.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (cap > 0) RBF_TRY(read_deferred_total(c, row_ptr.as<int64_t>() + n, s));
     RBF_CUDA(cudaStreamSynchronize(s));
+    if (cap > 0) {
+      const rbf_status st = check_deferred_total(c, cap, s);
+      if (st == RBF_ERANGE) return rbf_update(cx, pts, n, noise, stream);  // lists past the capacity
+      RBF_TRY(st);
+    }
     an = h32[5];
     if (an == 0) return RBF_OK;
     e = an;
@@ -782,8 +854,8 @@ extern "C" rbf_status rbf_update(rbf_ctx* cx, const float* pts, int64_t n, doubl
   Buf& val = c->scratch(15);
   Buf& lcol = c->scratch(16);
   Buf& ev = c->scratch(17);
-  RBF_TRY(val.ensure((size_t)nnz * sizeof(double)));
-  RBF_TRY(lcol.ensure((size_t)nnz * sizeof(int32_t)));
+  RBF_TRY(val.ensure((size_t)nnz_buf * sizeof(double)));
+  RBF_TRY(lcol.ensure((size_t)nnz_buf * sizeof(int32_t)));
   RBF_TRY(ev.ensure((size_t)n * sizeof(double)));
   RowParams RP = row_params(c->cfg, noise);
   { k_rowvals<<<nblk(n * 32), 256, 0, s>>>(RP, pts, n, row_ptr.as<int64_t>(), col.as<int32_t>(),

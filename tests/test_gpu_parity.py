@@ -180,6 +180,25 @@ def test_update_config1_single_frame(N, prec):
     assert rel_inf(T.weights().cpu().numpy(), ref) < F64_TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_update_neighbour_lists_outgrow_capacity(N, prec):
+    """After its first update the library fills the neighbour lists up to a
+    capacity (twice the largest total seen) without reading the total first;
+    an update whose lists do not fit starts over with a larger capacity.  A
+    50-point batch followed by the full config-1 batch takes that path; both
+    updates must still equal the oracle's recursion."""
+    c1 = W.config1()
+    p32 = c1.points.astype(np.float32)
+    T = N.Terrain(rho=0.6, update_precision=prec)
+    T.set_centers(dev(c1.centers, torch.float64))
+    st = O.BlockState(c1.centers, 1e-3, O.WENDLAND, rho=0.6)
+    for batch in (p32[:50], p32[50:]):
+        T.update(dev(batch), noise=0.02)
+        A = O.block_update(st, batch.astype(np.float64))
+        assert np.array_equal(T.active().cpu().numpy(), A)
+        assert rel_inf(T.weights().cpu().numpy(), st.w) < F64_TOL
+
+
 @pytest.mark.parametrize("prec,inv", [(0, 0), (1, 0), (1, -1)])
 def test_update_config2_sequence_with_departures(N, prec, inv):
     """Frames 0, 1, 2, 40, 41 of the staircase sequence: the later frames
